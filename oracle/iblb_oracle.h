@@ -1,0 +1,101 @@
+/*
+ * iblb_oracle.h -- plain FP64 CPU oracle of the IBLB wetting time step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may include, link or
+ * call this file; only the tests, the smoke check and the benchmark's CPU
+ * baseline leg use it.  It shares no source with the CUDA library.
+ *
+ * What it computes (paper: Bellantoni et al., "On the hydrodynamic behaviour of
+ * the immersed boundary - lattice Boltzmann method for wetting problems",
+ * Sec. 2, "Wetting via immersed boundary - lattice Boltzmann method"):
+ *   - lattice Boltzmann equation with BGK relaxation and exact streaming (Eq. 1-2),
+ *   - second-order equilibrium (Eq. 3), Guo source term (Eq. 4),
+ *   - moments with the half-force correction (Eq. 5-6),
+ *   - IB velocity interpolation and force spreading (Eq. 7-8) with the
+ *     Peskin 4-point discrete delta,
+ *   - surface-tension force as the gradient of sigma * area (Eq. 9 with the
+ *     finite-element strain-energy reading), wetting potential Pi(d) (Eq. 10),
+ *     nodal wetting force -chi_j Pi(d_j) n_j / 3 (2D: / 2),
+ *   - A from theta_eq (Eq. 11), forward-Euler node advection.
+ * Readings where the paper is silent are listed with each function.
+ */
+#ifndef IBLB_ORACLE_H
+#define IBLB_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Simulation parameters.  Lattice units (dx = dt = 1). */
+typedef struct {
+    int lattice;          /* 9 = D2Q9 (2D), 19 = D3Q19 (3D) */
+    int nx, ny, nz;       /* lattice extent; nz = 1 in 2D */
+    int walls;            /* 1: the first and last layer along the wall axis
+                             (y in 2D, z in 3D) are solid, halfway bounce-back;
+                             0: every axis periodic */
+    int wetting;          /* 1: apply Pi(d) with d measured from the lower wall */
+    double tau;           /* BGK relaxation time */
+    double sigma;         /* surface tension */
+    double xi;            /* regularisation length of Pi */
+    double theta_eq_deg;  /* equilibrium contact angle (degrees) */
+    int pi_n, pi_m;       /* exponents of Pi, n > m > 1 */
+    double body_force[3]; /* uniform force density on every fluid cell */
+} or_params;
+
+/* Fixed-size observables block (every entry FP64). */
+typedef struct {
+    double mass;          /* sum of rho over fluid cells */
+    double volume;        /* enclosed area (2D) / volume (3D) of the interface */
+    double height;        /* max - min node coordinate along the wall axis */
+    double theta_deg;     /* apparent contact angle of the circle/sphere fit */
+    double r_cl;          /* contact-line half-width (2D) / radius (3D) */
+    double film;          /* mean wall distance of the nodes under the drop */
+    double d_min;         /* min wall distance over nodes */
+    double centre[3];     /* fitted circle/sphere centre */
+    double radius;        /* fitted radius */
+} or_obs;
+
+/* ---- pointwise pieces (for pins) ---- */
+int    or_lattice(int Q, int* c /*[Q][3]*/, double* w /*[Q]*/, int* opp /*[Q]*/);
+void   or_equilibrium(int Q, double rho, const double* u /*[3]*/, double* feq /*[Q]*/);
+void   or_guo_source(int Q, double tau, const double* u, const double* F, double* S /*[Q]*/);
+double or_delta4(double r);
+double or_wetting_A(double sigma, double xi, double theta_eq_deg, int n, int m);
+double or_wetting_Pi(double A, double xi, int n, int m, double d);
+
+/* Nodal forces of an interface (A1).  dim = 2: closed CCW ring, tri ignored;
+ * dim = 3: outward-oriented triangles.  Outputs are [N][dim]; any may be NULL.
+ * Returns 0, or 1 if a node lies at or below the wall plane. */
+int or_nodal_forces(int dim, int N, const double* q, int M, const int* tri,
+                    double sigma, int wetting, double A, double xi, int n, int m,
+                    double wall_plane,
+                    double* phi, double* phi_sigma, double* phi_pi,
+                    double* normal, double* chi);
+
+/* ---- a whole simulation ---- */
+typedef struct or_sim or_sim;
+
+or_sim* or_sim_create(const or_params* p);
+void    or_sim_destroy(or_sim* s);
+int     or_sim_set_interface(or_sim* s, int N, const double* q, int M, const int* tri);
+void    or_sim_set_populations(or_sim* s, const double* f /*[Q][cells]*/);
+void    or_sim_get_populations(const or_sim* s, double* f);
+/* Advance n steps; returns 0, 1 (node in wall) or 2 (non-finite population). */
+int     or_sim_step(or_sim* s, int n);
+/* rho [cells], u [3][cells] of the last moment evaluation, q [N][dim]. */
+void    or_sim_get_fields(const or_sim* s, double* rho, double* u, double* q);
+/* Spread the nodal forces of the current interface (plus the body force) to a
+ * dense force density F [3][cells]. */
+int     or_sim_force_field(or_sim* s, double* F);
+/* Interpolate a given velocity field u [3][cells] to the current nodes. */
+void    or_sim_interpolate(const or_sim* s, const double* u, double* qdot /*[N][dim]*/);
+/* Spread arbitrary nodal vectors phi [N][dim] at the current nodes. */
+void    or_sim_spread(const or_sim* s, const double* phi, double* F /*[3][cells]*/);
+int     or_sim_nodal_forces(const or_sim* s, double* phi, double* normal, double* chi);
+void    or_sim_observables(const or_sim* s, or_obs* o);
+double  or_sim_A(const or_sim* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

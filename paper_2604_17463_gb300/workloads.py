@@ -1,0 +1,257 @@
+"""Seeded synthetic inputs: initial interface shapes and workload sizes.
+
+This module holds no arithmetic of the method itself (no lattice Boltzmann,
+no forces, no delta kernel): only the geometry of the initial droplet shapes
+and the sizes and parameters of the droplet workloads.  Both the CUDA path and
+the CPU oracle take their inputs from here.
+
+Shapes follow the paper's workloads (Sec. 3-4): droplets of radius R_0
+resolved by a closed interface (a triangulated sphere in 3D; a closed ring in
+2D), placed just above a flat wall, with xi / R_0 = 0.05.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional, Tuple
+
+import numpy as np
+
+WALL_PLANE = 0.5  # lower wall plane with the first layer solid (halfway bounce-back)
+BASE_SEED = 20260417
+
+
+# ------------------------------------------------------------------ 2D rings
+def circle(n: int, radius: float, centre: Tuple[float, float]) -> np.ndarray:
+    """n nodes on a circle, counter-clockwise, node 0 at angle 0. [n, 2]"""
+    a = 2.0 * np.pi * np.arange(n) / n
+    return np.stack([centre[0] + radius * np.cos(a), centre[1] + radius * np.sin(a)], axis=1)
+
+
+def truncated_circle(n: int, radius: float, theta0_deg: float, base_y: float,
+                     centre_x: float) -> np.ndarray:
+    """Closed CCW ring: a circular arc of the given radius meeting the line
+    y = base_y at the angle theta0 (measured inside the drop), closed by the
+    flat base on that line.  Nodes are spread uniformly in arc length. [n, 2]"""
+    th = math.radians(theta0_deg)
+    yc = base_y - radius * math.cos(th)          # centre height
+    half = radius * math.sin(th)                 # half chord on the base line
+    arc_len = 2.0 * th * radius                  # arc above the base line
+    base_len = 2.0 * half
+    total = arc_len + base_len
+    s = (np.arange(n) + 0.5) * total / n
+    pts = np.zeros((n, 2))
+    # parametrise: start at the right end of the base, walk the arc CCW to the
+    # left end, then walk the base back left -> right.
+    a_start = -math.pi / 2 + th                  # angle of the right contact point
+    for k, sk in enumerate(s):
+        if sk < arc_len:
+            ang = a_start + sk / radius
+            pts[k] = (centre_x + radius * math.cos(ang), yc + radius * math.sin(ang))
+        else:
+            t = sk - arc_len
+            pts[k] = (centre_x - half + t, base_y)
+    return pts
+
+
+# ------------------------------------------------------------------ 3D mesh
+def icosphere(level: int, radius: float, centre: Tuple[float, float, float]):
+    """Icosahedron refined `level` times by 1 -> 4 midpoint subdivision with
+    every vertex projected to the sphere.  Faces are oriented outward.
+    Returns (nodes [10*4^level + 2, 3], faces [20*4^level, 3] int32)."""
+    g = (1.0 + math.sqrt(5.0)) / 2.0
+    v = []
+    for s1 in (-1.0, 1.0):
+        for s2 in (-1.0, 1.0):
+            v += [(0.0, s1, s2 * g), (s1, s2 * g, 0.0), (s2 * g, 0.0, s1)]
+    verts = np.array(v)
+    verts /= np.linalg.norm(verts, axis=1, keepdims=True)
+    # faces: triples of mutually adjacent vertices (edge = minimum distance)
+    d = np.linalg.norm(verts[:, None, :] - verts[None, :, :], axis=2)
+    edge = np.min(d[d > 1e-9])
+    adj = np.abs(d - edge) < 1e-6
+    faces = []
+    for a in range(12):
+        for b in range(a + 1, 12):
+            if not adj[a, b]:
+                continue
+            for c in range(b + 1, 12):
+                if adj[a, c] and adj[b, c]:
+                    n = np.cross(verts[b] - verts[a], verts[c] - verts[a])
+                    if np.dot(n, verts[a] + verts[b] + verts[c]) < 0:
+                        faces.append((a, c, b))
+                    else:
+                        faces.append((a, b, c))
+    verts = [tuple(x) for x in verts]
+    for _ in range(level):
+        cache = {}
+        new_faces = []
+
+        def mid(i, j):
+            key = (min(i, j), max(i, j))
+            if key not in cache:
+                p = np.add(verts[i], verts[j]) * 0.5
+                p /= np.linalg.norm(p)
+                cache[key] = len(verts)
+                verts.append(tuple(p))
+            return cache[key]
+
+        for a, b, c in faces:
+            ab, bc, ca = mid(a, b), mid(b, c), mid(c, a)
+            new_faces += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        faces = new_faces
+    nodes = np.asarray(verts) * radius + np.asarray(centre)[None, :]
+    return nodes, np.asarray(faces, dtype=np.int32)
+
+
+def icosphere_level_for(radius: float, max_edge: float = 1.5) -> int:
+    """Smallest subdivision level whose mean edge is at most max_edge lu."""
+    for lvl in range(0, 8):
+        nodes, faces = icosphere(lvl, radius, (0.0, 0.0, 0.0))
+        e = np.linalg.norm(nodes[faces[:, 0]] - nodes[faces[:, 1]], axis=1).mean()
+        if e <= max_edge:
+            return lvl
+    return 7
+
+
+# ------------------------------------------------------------------ workloads
+@dataclasses.dataclass
+class Workload:
+    """One droplet simulation: lattice, physical parameters, initial interface."""
+    name: str
+    lattice: int                 # 9 or 19
+    nx: int
+    ny: int
+    nz: int
+    tau: float
+    sigma: float
+    xi: float
+    theta_eq_deg: float
+    pi_n: int
+    pi_m: int
+    steps: int
+    nodes: np.ndarray            # [N, dim]
+    faces: Optional[np.ndarray]  # [M, 3] (3D) or None
+    walls: bool = True
+    wetting: bool = True
+
+    @property
+    def dim(self) -> int:
+        return 2 if self.lattice == 9 else 3
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def fluid_cells(self) -> int:
+        if not self.walls:
+            return self.cells
+        if self.dim == 2:
+            return self.nx * (self.ny - 2)
+        return self.nx * self.ny * (self.nz - 2)
+
+
+def config1() -> Workload:
+    """2D D2Q9 128x64, tau = 1, circle R = 20 with 200 nodes centred 22 lu
+    above the wall, sigma = 1e-3, theta_eq = 60 deg, xi = 0.05 R, 2000 steps."""
+    R = 20.0
+    nodes = circle(200, R, (64.0, WALL_PLANE + 22.0))
+    return Workload("c1_d2q9_128x64_fp64", 9, 128, 64, 1, 1.0, 1e-3, 0.05 * R, 60.0, 9, 3,
+                    2000, nodes, None)
+
+
+def config2(theta_eq_deg: float = 60.0, tau: float = 1.0, downscale: int = 1) -> Workload:
+    """2D D2Q9 2048x512 spreading, R = 200 with 2000 nodes, initial angle
+    150 deg; optional downscaled copy (lattice, R, nodes / downscale)."""
+    R = 200.0 / downscale
+    xi = 0.05 * R
+    n = 2000 // downscale
+    nx, ny = 2048 // downscale, 512 // downscale
+    nodes = truncated_circle(n, R, 150.0, WALL_PLANE + xi, nx / 2.0)
+    return Workload(f"c2_d2q9_{nx}x{ny}", 9, nx, ny, 1, tau, 1e-3, xi, theta_eq_deg, 9, 3,
+                    200000, nodes, None)
+
+
+def config3() -> Workload:
+    """3D D3Q19 256x256x128, icosphere R = 40 (20480 faces, 10242 nodes)
+    centred 42 lu above the wall, theta_eq = 75 deg, tau = 0.8."""
+    R = 40.0
+    nodes, faces = icosphere(5, R, (128.0, 128.0, WALL_PLANE + 42.0))
+    return Workload("c3_d3q19_256x256x128", 19, 256, 256, 128, 0.8, 1e-3, 0.05 * R, 75.0, 9, 3,
+                    50000, nodes, faces)
+
+
+def droplet_2d(width: int, theta_eq_deg: float, tau: float, steps: int,
+               name: str = "d2q9") -> Workload:
+    """Batched / served 2D member: height = width / 4, R = height / 3,
+    10 nodes per unit radius, xi = max(0.05 R, 1 lu)."""
+    ny = max(width // 4, 12)
+    R = ny / 3.0
+    xi = max(0.05 * R, 1.0)
+    n = int(round(10 * R))
+    nodes = circle(n, R, (width / 2.0, WALL_PLANE + R + 2.0 * xi))
+    return Workload(f"{name}_{width}x{ny}", 9, width, ny, 1, tau, 1e-3, xi, theta_eq_deg, 9, 3,
+                    steps, nodes, None)
+
+
+def droplet_3d(nx: int, ny: int, nz: int, theta_eq_deg: float, tau: float, steps: int,
+               name: str = "d3q19") -> Workload:
+    """Served 3D member: R = nz / 3, icosphere refined to mean edge <= 1.5 lu."""
+    R = nz / 3.0
+    xi = max(0.05 * R, 1.0)
+    lvl = icosphere_level_for(R)
+    nodes, faces = icosphere(lvl, R, (nx / 2.0, ny / 2.0, WALL_PLANE + R + 2.0 * xi))
+    return Workload(f"{name}_{nx}x{ny}x{nz}", 19, nx, ny, nz, tau, 1e-3, xi, theta_eq_deg, 9, 3,
+                    steps, nodes, faces)
+
+
+def config4(count: int = 256, seed: int = BASE_SEED + 4, steps_lo: int = 5000,
+            steps_hi: int = 50000) -> List[Workload]:
+    """256 uneven 2D droplets: width log-uniform in [64, 1024], theta_eq
+    uniform in [30, 150], tau uniform in [0.55, 1.5]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        w = int(round(math.exp(rng.uniform(math.log(64), math.log(1024)))))
+        th = float(rng.uniform(30.0, 150.0))
+        tau = float(rng.uniform(0.55, 1.5))
+        st = int(rng.integers(steps_lo, steps_hi + 1))
+        out.append(droplet_2d(w, th, tau, st, name=f"c4_{k:03d}"))
+    return out
+
+
+@dataclasses.dataclass
+class Request:
+    arrival_s: float
+    work: Workload
+
+
+def config5(count: int = 2000, rate_per_s: float = 50.0, seed: int = BASE_SEED + 5,
+            steps_lo: int = 5000, steps_hi: int = 50000, frac_3d: float = 0.2) -> List[Request]:
+    """Poisson stream of wetting requests: 80% 2D (sizes as in the batched
+    workload), 20% 3D D3Q19 between 64^3 and 192x192x96."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for k in range(count):
+        t += float(rng.exponential(1.0 / rate_per_s))
+        th = float(rng.uniform(30.0, 150.0))
+        tau = float(rng.uniform(0.55, 1.5))
+        st = int(rng.integers(steps_lo, steps_hi + 1))
+        if rng.uniform() < frac_3d:
+            s = float(rng.uniform(0.0, 1.0))
+            nx = int(round(64 + s * (192 - 64)))
+            nz = int(round(64 + s * (96 - 64)))
+            out.append(Request(t, droplet_3d(nx, nx, nz, th, tau, st, name=f"c5_{k:04d}")))
+        else:
+            w = int(round(math.exp(rng.uniform(math.log(64), math.log(1024)))))
+            out.append(Request(t, droplet_2d(w, th, tau, st, name=f"c5_{k:04d}")))
+    return out
+
+
+# ------------------------------------------------------------------ random data
+def random_perturbation(shape, seed: int, scale: float = 1.0) -> np.ndarray:
+    """Seeded uniform noise in [-scale, scale]."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-scale, scale, size=shape)
