@@ -1,0 +1,334 @@
+"""Throughput benchmark of the IBLB hot path on GB300.
+
+One "step" is one full IBLB time step of the 3D droplet workload
+(D3Q19, 256 x 256 x 128 lattice, FP32 deviation storage, icosphere drop of
+radius 40 with 10242 nodes / 20480 faces placed 42 lu above the wall,
+theta_eq = 75 deg, tau = 0.8): nodal forces, spread, fused stream-collide,
+interpolate + advect.  The population state (2 x 1.26 GB) is far larger than
+L2, so no L2 flush is needed between steps.
+
+Metric: MLUPS (million fluid-lattice-cell updates per second), whole job.
+Also reported: the HBM-roofline fraction of the stream-collide kernel, an
+end-to-end figure through the C-ABI with host buffers, and the FP64 CPU oracle
+timed on a bounded sample of the same workload.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD_NAME = "d3q19_256x256x128_icosphere_R40_fp32dev"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "stream_collide_d3q19_256x256x128_fp32.txt")
+LBM_SOURCE = os.path.join(ROOT, "paper_2604_17463_gb300", "csrc", "lbm.cu")
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS_FILE) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def source_digest(path):
+    with open(path, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def ncu_traffic():
+    """Per-launch DRAM bytes of the stream-collide kernel from the committed ncu
+    summary, valid only while the kernel source is unchanged since capture."""
+    try:
+        vals = {}
+        with open(TRAFFIC_FILE) as fh:
+            for line in fh:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    vals[k.strip()] = v.strip()
+        if vals.get("lbm.cu sha256[:16]") != source_digest(LBM_SOURCE):
+            return None
+        return float(vals["dram bytes per launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return None
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline_oracle(wl, steps):
+    """FP64 CPU oracle on `steps` full time steps of the workload (1 thread)."""
+    import oracle
+    s = oracle.Sim(wl.lattice, wl.nx, wl.ny, wl.nz, tau=wl.tau, walls=wl.walls, wetting=wl.wetting,
+                   sigma=wl.sigma, xi=wl.xi, theta_eq_deg=wl.theta_eq_deg, pi_n=wl.pi_n,
+                   pi_m=wl.pi_m)
+    s.set_interface(wl.nodes, wl.faces)
+    t0 = time.perf_counter()
+    rc = s.step(steps)
+    dt = time.perf_counter() - t0
+    s.close()
+    if rc != 0:
+        raise RuntimeError(f"oracle step failed: {rc}")
+    return wl.fluid_cells * steps / dt / 1e6, dt
+
+
+def run_reference(args, wl, budget_s=150.0):
+    """The oracle timed on the host cores on the same workload and metric.
+    A full 3D oracle step takes seconds, so at most as many steps as fit in
+    `budget_s` are run (the metric is a rate; the sample is stated)."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import oracle
+    s = oracle.Sim(wl.lattice, wl.nx, wl.ny, wl.nz, tau=wl.tau, walls=wl.walls, wetting=wl.wetting,
+                   sigma=wl.sigma, xi=wl.xi, theta_eq_deg=wl.theta_eq_deg, pi_n=wl.pi_n,
+                   pi_m=wl.pi_m)
+    s.set_interface(wl.nodes, wl.faces)
+    t0 = time.perf_counter()
+    s.step(1)                                   # one untimed step sizes the sample
+    per_step = time.perf_counter() - t0
+    fit = max(1, int(budget_s / max(per_step, 1e-3)))
+    warm = max(0, min(args.warmup, fit // 4) - 1)
+    timed = max(1, min(args.steps, fit - warm))
+    for _ in range(warm):
+        s.step(1)
+    t0 = time.perf_counter()
+    for _ in range(timed):
+        s.step(1)
+    dt = time.perf_counter() - t0
+    s.close()
+    v = wl.fluid_cells * timed / dt / 1e6
+    sample = (f"{timed} of {args.steps} requested full oracle time steps of the workload "
+              f"(FP64, single thread, {dt:.1f} s)")
+    line = {
+        "impl": "reference", "metric": "MLUPS", "value": v, "unit": "MLUPS", "n_gpus": world,
+        "steps": timed, "warmup": warm + 1, "ms_per_step": dt / timed * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "lattice": "D3Q19", "nx": wl.nx, "ny": wl.ny,
+                   "nz": wl.nz, "nodes": int(wl.nodes.shape[0]), "faces": int(wl.faces.shape[0]),
+                   "fluid_cells": wl.fluid_cells},
+        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, wl):
+    import torch
+    from paper_2604_17463_gb300 import iblb
+
+    world, rank, local = dist_setup()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device (the CUDA library has no CPU path)")
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    storage = {"fp32": iblb.FP32_DEV, "fp16": iblb.FP16_DEV, "fp64": iblb.FP64}[args.storage]
+    sim = iblb.Simulation.from_workload(wl, storage=storage, stream=stream.cuda_stream)
+    cells = sim.fluid_cells
+
+    # ---- device-resident throughput (value)
+    sim.step(args.warmup)
+    sim.sync()
+    n0 = iblb.iblb_kernel_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        sim.step(args.steps)
+        ev1.record(stream)
+        ev1.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    launches = iblb.iblb_kernel_launch_count() - n0
+    sim.sync()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * cells * args.steps / (ms / 1e3) / 1e6
+
+    # ---- per-kernel device times (CUDA events around each launch)
+    prof_steps = max(5, min(args.steps, 200))
+    kms = sim.step_profiled(prof_steps)
+    sc_ms = kms[iblb.K_STREAM_COLLIDE] / prof_steps
+    bytes_per_launch = sim.stream_bytes_per_step
+    achieved = bytes_per_launch / (sc_ms / 1e3) / 1e9
+    peak, peak_kind = hbm_peak()
+    kernel_share = {iblb.KERNEL_NAMES[k]: kms[k] / kms.sum() for k in range(iblb.K_COUNT)}
+    sim.close()
+
+    # ---- end to end through the C-ABI with pinned host buffers
+    xyz_host = torch.from_numpy(np.ascontiguousarray(wl.nodes)).pin_memory().numpy()
+    ncell = wl.cells
+    rho_out = torch.empty(ncell, dtype=torch.float64).pin_memory().numpy()
+    u_out = torch.empty(3 * ncell, dtype=torch.float64).pin_memory().numpy()
+    xyz_out = torch.empty(wl.nodes.size, dtype=torch.float64).pin_memory().numpy()
+    tri = np.ascontiguousarray(wl.faces, dtype=np.int32)
+    sim2 = iblb.Simulation(wl.lattice, wl.nx, wl.ny, wl.nz, stream=stream.cuda_stream,
+                           tau=wl.tau, walls=wl.walls, wetting=wl.wetting, sigma=wl.sigma,
+                           xi=wl.xi, theta_eq_deg=wl.theta_eq_deg, pi_n=wl.pi_n, pi_m=wl.pi_m,
+                           storage=storage)
+    sim2.set_interface(xyz_host, tri)
+    sim2.step(args.warmup)
+    sim2.sync()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    iblb.iblb_set_interface(sim2.h, xyz_host, tri)
+    iblb.iblb_step(sim2.h, args.steps)
+    iblb.iblb_read_fields(sim2.h, rho_out, u_out, xyz_out)
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    sim2.close()
+    e2e_value = world * cells * args.steps / e2e_s / 1e6
+    h2d = (xyz_host.nbytes + tri.nbytes) / args.steps
+    d2h = (rho_out.nbytes + u_out.nbytes + xyz_out.nbytes) / args.steps
+
+    if rank != 0:
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu_steps = 3
+        cv, cdt = cpu_baseline_oracle(wl, cpu_steps)
+        cpu = {"value": cv, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": f"{cpu_steps} full time steps of the same workload in the FP64 oracle "
+                         f"(single thread, {cdt:.1f} s)"}
+    clocks = clk.summary()
+    line = {
+        "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp16": "f32 (binary16 storage)", "fp64": "f64"}[args.storage],
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "lattice": "D3Q19", "nx": wl.nx, "ny": wl.ny,
+                   "nz": wl.nz, "storage": args.storage, "nodes": int(wl.nodes.shape[0]),
+                   "faces": int(wl.faces.shape[0]), "fluid_cells": cells,
+                   "l2": "state (2 x 1.26 GB) larger than L2; no flush",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "kernel": "stream_collide", "achieved": achieved,
+                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": ncu_traffic(),
+                     "bytes_per_launch": bytes_per_launch, "launch_ms": sc_ms,
+                     "kernel_share": kernel_share},
+        "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    from paper_2604_17463_gb300 import workloads as W
+    wl = W.config3()
+    if args.impl == "reference":
+        return run_reference(args, wl)
+    return run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,172 @@
+/*
+ * iblb.h -- C-ABI of the GB300 immersed boundary - lattice Boltzmann (IBLB)
+ * wetting library (libiblb.so).
+ *
+ * The library advances droplet simulations of the IBLB wetting method of
+ * Bellantoni et al., "On the hydrodynamic behaviour of the immersed boundary -
+ * lattice Boltzmann method for wetting problems", Sec. 2:
+ *   - lattice Boltzmann equation, BGK relaxation, exact streaming (Eq. 1-2),
+ *     second-order equilibrium (Eq. 3), Guo forcing (Eq. 4), moments with the
+ *     half-force correction (Eq. 5-6), on D2Q9 or D3Q19;
+ *   - halfway bounce-back at two flat solid walls normal to the last axis
+ *     (y in 2D, z in 3D), periodic along the other axes;
+ *   - a closed Lagrangian interface (ring in 2D, triangle mesh in 3D) carrying
+ *     surface tension plus the wetting potential Pi(d) (Eq. 9-11), spread to
+ *     the lattice and coupled back by velocity interpolation (Eq. 7-8) with
+ *     the Peskin 4-point delta, and advected by forward Euler.
+ *
+ * Conventions (all calls):
+ *   - Lattice units: dx = dt = 1.  Cell (x, y, z) has index x + nx*(y + ny*z);
+ *     nz = 1 in 2D.  The first and last layer along the wall axis are solid
+ *     (when walls != 0); the lower wall plane is at coordinate 0.5 and the
+ *     wall distance of a node is d = q_wall_axis - 0.5.
+ *   - Host arrays are FP64 unless stated otherwise; the caller owns them.
+ *     Populations are exchanged as f_i (not deviations), layout [Q][cells];
+ *     velocities as [dim][cells]; node positions as [N][dim].
+ *   - All device state is owned by the library.  Work is enqueued on the CUDA
+ *     stream given at creation; calls that return host data synchronise it.
+ *   - Every call returns an iblb_status; iblb_last_error() gives the text of
+ *     the last failure on a handle.  Faults detected on the device (a node at
+ *     or below the wall plane, a non-finite density) are latched in a device
+ *     flag and reported by the next synchronising call; they never trap.
+ *   - A handle is not thread-safe: use one handle per host thread / stream.
+ */
+#ifndef IBLB_H
+#define IBLB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    IBLB_OK = 0,
+    IBLB_EINVAL = 1,          /* bad argument or configuration */
+    IBLB_ENOMEM = 2,          /* device allocation failed / budget exceeded */
+    IBLB_ECUDA = 3,           /* a CUDA runtime call failed */
+    IBLB_ENODE_IN_WALL = 4,   /* an interface node reached d <= 0 */
+    IBLB_ENONFINITE = 5,      /* a density became NaN / Inf */
+    IBLB_ETIMEOUT = 6,        /* a bounded device wait gave up */
+    IBLB_EAGAIN = 7           /* batch: no room for this request right now */
+} iblb_status;
+
+typedef enum { IBLB_D2Q9 = 9, IBLB_D3Q19 = 19 } iblb_lattice;
+
+/* Population storage.  All forms hold deviations f_i - w_i from the rest
+ * state; arithmetic is FP64 for IBLB_FP64 and FP32 otherwise.  IBLB_FP16_DEV
+ * stores (f_i - w_i) * 2^fp16_scale_exp in binary16. */
+typedef enum { IBLB_FP64 = 0, IBLB_FP32_DEV = 1, IBLB_FP16_DEV = 2 } iblb_storage;
+
+typedef struct {
+    int lattice;            /* IBLB_D2Q9 or IBLB_D3Q19 */
+    int nx, ny, nz;         /* lattice extent (nz = 1 for D2Q9) */
+    int walls;              /* 1: solid first/last layer along the wall axis;
+                               0: periodic along every axis */
+    int wetting;            /* 1: apply Pi(d) (Eq. 10) to the interface nodes */
+    double tau;             /* BGK relaxation time, > 0.5 */
+    double sigma;           /* surface tension */
+    double xi;              /* regularisation length of Pi */
+    double theta_eq_deg;    /* equilibrium contact angle; sets A by Eq. 11 */
+    int pi_n, pi_m;         /* exponents of Pi, n > m > 1 */
+    double body_force[3];   /* uniform force density on every fluid cell */
+    int storage;            /* iblb_storage */
+    int fp16_scale_exp;     /* binary16 scale exponent (0 selects 16) */
+} iblb_config;
+
+typedef struct {
+    double mass;          /* sum of rho over fluid cells (FP64) */
+    double volume;        /* enclosed area (2D) / volume (3D) of the interface */
+    double height;        /* max - min node coordinate along the wall axis */
+    double theta_deg;     /* apparent contact angle of the circle/sphere fit */
+    double r_cl;          /* contact-line half-width (2D) / radius (3D) */
+    double film;          /* mean wall distance of the nodes under the drop */
+    double d_min;         /* minimum node wall distance */
+    double centre[3];     /* fitted circle / sphere centre */
+    double radius;        /* fitted radius */
+} iblb_obs;
+
+typedef struct iblb_sim* iblb_handle;
+
+/* Create a simulation at rest (rho = 1, u = 0) on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  Allocates the device
+ * state: two population buffers, the moments, the force density and the
+ * band flags.  Returns IBLB_EINVAL for a bad config, IBLB_ENOMEM if the
+ * device cannot hold it. */
+iblb_status iblb_create(const iblb_config* cfg, void* cuda_stream, iblb_handle* out);
+void        iblb_destroy(iblb_handle h);
+const char* iblb_last_error(iblb_handle h);
+const char* iblb_status_string(iblb_status s);
+
+/* Set the interface (Sec. 2: N Lagrangian nodes, fixed connectivity).
+ * xyz [n_nodes][dim] host FP64.  2D: the nodes form a closed ring in
+ * counter-clockwise order and `tri` must be NULL.  3D: tri [n_faces][3]
+ * host int32, outward-oriented.  n_nodes = 0 removes the interface. */
+iblb_status iblb_set_interface(iblb_handle h, const double* xyz, int n_nodes,
+                               const int* tri, int n_faces);
+
+/* Advance n_steps time steps (asynchronous on the stream).  Each step:
+ * nodal forces at q(t) -> spread F(t) -> fused stream-collide with Guo
+ * forcing -> interpolate u(t) at q(t) -> Euler.  The last step of a call
+ * also stores rho and u of every cell for iblb_read_fields. */
+iblb_status iblb_step(iblb_handle h, int n_steps);
+
+/* Synchronise the stream and report any latched device fault. */
+iblb_status iblb_sync(iblb_handle h);
+
+/* rho [cells], u [dim][cells] of the last moment evaluation (zero on solid
+ * cells) and node positions xyz [N][dim]; any pointer may be NULL.
+ * Synchronises. */
+iblb_status iblb_read_fields(iblb_handle h, double* rho, double* u, double* xyz);
+
+/* Replace / read the populations f_i, host FP64 [Q][cells]. */
+iblb_status iblb_set_populations(iblb_handle h, const double* f);
+iblb_status iblb_get_populations(iblb_handle h, double* f);
+
+/* FP64 observables (A7): mass, volume, height, fitted contact angle,
+ * contact-line position, film thickness.  Synchronises. */
+iblb_status iblb_observables(iblb_handle h, iblb_obs* out);
+
+/* ---- single-stage entry points (each runs one kernel of the step) ---- */
+
+/* Nodal forces phi [N][dim], normals [N][dim] and 1-ring measures chi [N]
+ * at the current interface (any pointer may be NULL). Synchronises. */
+iblb_status iblb_nodal_forces(iblb_handle h, double* phi, double* normal, double* chi);
+
+/* Spread the current nodal forces plus the body force: F [dim][cells].
+ * Leaves the device force buffer cleared.  Synchronises. */
+iblb_status iblb_force_field(iblb_handle h, double* F);
+
+/* Interpolate a given velocity field u [dim][cells] to the current nodes:
+ * qdot [N][dim].  Does not move the nodes.  Synchronises. */
+iblb_status iblb_interpolate(iblb_handle h, const double* u, double* qdot);
+
+/* ---- measurement ---- */
+
+/* Kernel ids for iblb_step_profiled. */
+enum {
+    IBLB_K_FORCES = 0,
+    IBLB_K_SPREAD = 1,
+    IBLB_K_STREAM_COLLIDE = 2,
+    IBLB_K_INTERP_ADVECT = 3,
+    IBLB_K_COUNT = 4
+};
+
+/* Run n_steps outside any CUDA graph with a CUDA event pair around every
+ * kernel launch; kernel_ms[IBLB_K_COUNT] receives the summed device time of
+ * each kernel (ms).  Synchronises. */
+iblb_status iblb_step_profiled(iblb_handle h, int n_steps, double* kernel_ms);
+
+/* Algorithmic HBM bytes of one stream-collide launch: populations read once
+ * and written once per fluid cell. */
+double iblb_stream_bytes_per_step(iblb_handle h);
+long long iblb_fluid_cells(iblb_handle h);
+
+/* Number of kernels this library has launched since load (counting every
+ * launch, including those inside CUDA graphs). */
+long long iblb_kernel_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,143 @@
+// common.cuh -- internal declarations shared by the CUDA translation units of
+// libiblb (lattice stencils, kernel parameter blocks, launchers).
+//
+// Lattice: D2Q9 and D3Q19 (the paper uses D3Q19, Sec. 2; D2Q9 is its 2D
+// analogue).  The weights are the standard ones for these stencils; the paper
+// does not print them.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace iblb {
+
+// ------------------------------------------------------------------ stencils
+// Velocity order (shared with the host-visible population layout):
+//   D2Q9 : rest, +x, +y, -x, -y, (+x+y), (-x+y), (-x-y), (+x-y)
+//   D3Q19: rest, +x, -x, +y, -y, +z, -z, then the 12 edge directions in
+//          opposite pairs (2k+1, 2k+2).
+template <int Q> struct Stencil;
+
+template <> struct Stencil<9> {
+    static constexpr int D = 2;
+    __host__ __device__ static constexpr int cx(int i) {
+        constexpr int t[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+        return t[i];
+    }
+    __host__ __device__ static constexpr int cy(int i) {
+        constexpr int t[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+        return t[i];
+    }
+    __host__ __device__ static constexpr int cz(int) { return 0; }
+    __host__ __device__ static constexpr int opp(int i) {
+        constexpr int t[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+        return t[i];
+    }
+    __host__ __device__ static constexpr double w(int i) {
+        return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+    }
+};
+
+template <> struct Stencil<19> {
+    static constexpr int D = 3;
+    __host__ __device__ static constexpr int cx(int i) {
+        constexpr int t[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 0, 0, 1, -1, 1, -1, 0, 0};
+        return t[i];
+    }
+    __host__ __device__ static constexpr int cy(int i) {
+        constexpr int t[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 1, -1};
+        return t[i];
+    }
+    __host__ __device__ static constexpr int cz(int i) {
+        constexpr int t[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 1, -1, 1, -1, 0, 0, -1, 1, -1, 1};
+        return t[i];
+    }
+    __host__ __device__ static constexpr int opp(int i) {
+        return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1);
+    }
+    __host__ __device__ static constexpr double w(int i) {
+        return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+    }
+};
+
+// Device error flags (bitwise OR).
+enum : int { ERR_NODE_IN_WALL = 1, ERR_NONFINITE = 2, ERR_TIMEOUT = 4 };
+
+// ------------------------------------------------------------------ params
+struct GridParams {
+    int nx, ny, nz;        // extent (nz = 1 in 2D)
+    int dim;               // 2 or 3
+    int walls;             // solid first/last layer along the wall axis
+    int nseg_x;            // 32-cell band segments per x row
+    long long ncell;       // nx * ny * nz
+};
+
+struct StreamParams {
+    GridParams g;
+    double omega;          // 1 / tau
+    double body[3];        // uniform force density
+    float scale, inv_scale;  // binary16 storage scale (1 for other storage)
+    int* err;
+};
+
+struct ForceParams {
+    double sigma;
+    double A, xi;          // wetting amplitude (Eq. 11) and length
+    int n, m;              // exponents of Pi
+    int wetting;
+    double wall_plane;     // 0.5
+};
+
+// ------------------------------------------------------------------ launchers
+// Storage ids match iblb_storage.
+enum Storage : int { ST_FP64 = 0, ST_FP32 = 1, ST_FP16 = 2 };
+
+// One fused stream-collide step over every fluid cell (pull, halfway
+// bounce-back, Guo forcing).  fin/fout: population deviations [Q][ncell];
+// moments: drho [ncell] then u [dim][ncell] (compute precision); F: force
+// density [dim][ncell], read and cleared only in flagged band segments.
+void launch_stream_collide(int Q, int storage, bool write_all, const void* fin, void* fout,
+                           void* moments, void* F, uint8_t* flags, const StreamParams& p,
+                           cudaStream_t s);
+
+// Host FP64 <-> device storage conversion of populations ([Q][ncell], f_i).
+void launch_pack_populations(int Q, int storage, const double* f, void* dst, long long ncell,
+                             float scale, cudaStream_t s);
+void launch_unpack_populations(int Q, int storage, const void* src, double* f, long long ncell,
+                               float inv_scale, cudaStream_t s);
+// Moments (compute precision) -> FP64 rho [ncell] and u [dim][ncell].
+void launch_unpack_moments(int storage, const GridParams& g, const void* moments, double* rho,
+                           double* u, cudaStream_t s);
+// Initialise moments to the rest state (drho = 0 on fluid, -1 on solid).
+void launch_init_moments(int storage, const GridParams& g, void* moments, cudaStream_t s);
+// Dense FP64 u [dim][ncell] -> moments' u part (compute precision).
+void launch_load_velocity(int storage, int dim, const double* u, void* moments, long long ncell,
+                          cudaStream_t s);
+// F [dim][ncell] (compute precision) plus body force on fluid cells -> FP64.
+void launch_unpack_force(int storage, const GridParams& g, const void* F, const double* body,
+                         double* out, cudaStream_t s);
+void launch_clear_flags(uint8_t* flags, long long n, cudaStream_t s);
+void launch_set_all_flags(uint8_t* flags, long long n, cudaStream_t s);
+// Mass of the populations: per-block FP64 partial sums into `partial`
+// (length mass_partial_blocks(g)); sum them in order afterwards.
+int mass_partial_blocks(const GridParams& g);
+void launch_mass_partials(int Q, int storage, const void* f, const GridParams& g, float inv_scale,
+                          double* partial, cudaStream_t s);
+
+// IB kernels.  q, phi: [N][dim] FP64.
+void launch_forces(int dim, const double* q, int N, const int* tri, const int* csr_ptr,
+                   const int* csr_ent, const ForceParams& fp, double* phi, double* normal,
+                   double* chi, int* err, cudaStream_t s);
+void launch_spread(int storage, int dim, const double* q, const double* phi, int N, void* F,
+                   uint8_t* flags, const GridParams& g, cudaStream_t s);
+// qdot [N][dim] = sum u Delta; if advect, q += qdot.
+void launch_interp(int storage, int dim, double* q, const void* moments, int N, double* qdot,
+                   bool advect, const GridParams& g, cudaStream_t s);
+
+// Observables (single block, deterministic).  out: 12 doubles, layout of iblb_obs.
+void launch_observables(int dim, const double* q, int N, const int* tri, int M,
+                        const double* mass_partial, int n_partial, double xi, double wall_plane,
+                        double* out, cudaStream_t s);
+
+}  // namespace iblb

@@ -1,0 +1,593 @@
+// engine.cu -- one simulation's device state and the C-ABI of libiblb
+// (include/iblb.h): creation, interface upload, the per-step kernel sequence
+// replayed as CUDA graphs, field read-back and observables.
+//
+// Step t -> t+1 (paper Sec. 2; order: forces at q(t), spread F(t), moments
+// with F(t), interpolate u(t) at q(t), forward Euler):
+//   A1 nodal forces  ->  A2/A3 spread + band flags  ->  A4 stream-collide
+//   ->  A5/A6 interpolate + advect.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/iblb.h"
+#include "common.cuh"
+
+using namespace iblb;
+
+namespace {
+std::atomic<long long> g_launches{0};
+}
+
+struct iblb_sim {
+    iblb_config cfg{};
+    int Q = 9, dim = 2, storage = 0;
+    size_t elt = 8;            // storage element size
+    size_t relt = 8;           // compute-precision element size
+    GridParams g{};
+    StreamParams sp{};
+    ForceParams fp{};
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;  // private stream used only for graph capture
+    void* f[2] = {nullptr, nullptr};
+    int cur = 0;
+    void* mom = nullptr;       // drho [ncell], u [dim][ncell]
+    void* F = nullptr;         // [dim][ncell]
+    uint8_t* flags = nullptr;
+    long long nflags = 0;
+    int* err = nullptr;
+    double* partial = nullptr;
+    int npartial = 0;
+    double* obs = nullptr;     // 12 doubles
+    // interface
+    int N = 0, M = 0;
+    double* q = nullptr;
+    double* phi = nullptr;
+    int* tri = nullptr;
+    int* csr_ptr = nullptr;
+    int* csr_ent = nullptr;
+    std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;  // (parity, steps, last)
+    std::string msg;
+};
+
+namespace {
+
+iblb_status fail(iblb_sim* h, iblb_status st, const std::string& m)
+{
+    if (h) h->msg = m;
+    return st;
+}
+
+iblb_status cuda_fail(iblb_sim* h, cudaError_t e, const char* where)
+{
+    return fail(h, IBLB_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(h, call)                                       \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+    } while (0)
+
+template <typename T>
+void free_dev(T*& p)
+{
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+void clear_graphs(iblb_sim* h)
+{
+    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+}
+
+int kernels_per_step(const iblb_sim* h) { return h->N > 0 ? 4 : 1; }
+
+// Enqueue one time step on stream s (buffers by the current parity).
+void enqueue_step(iblb_sim* h, cudaStream_t s, bool write_all)
+{
+    if (h->N > 0) {
+        launch_forces(h->dim, h->q, h->N, h->tri, h->csr_ptr, h->csr_ent, h->fp, h->phi, nullptr,
+                      nullptr, h->err, s);
+        launch_spread(h->storage, h->dim, h->q, h->phi, h->N, h->F, h->flags, h->g, s);
+    }
+    launch_stream_collide(h->Q, h->storage, write_all, h->f[h->cur], h->f[h->cur ^ 1], h->mom,
+                          h->F, h->flags, h->sp, s);
+    if (h->N > 0)
+        launch_interp(h->storage, h->dim, h->q, h->mom, h->N, nullptr, true, h->g, s);
+    h->cur ^= 1;
+}
+
+iblb_status get_graph(iblb_sim* h, int steps, bool last, cudaGraphExec_t* out)
+{
+    auto key = std::make_tuple(h->cur, steps, last ? 1 : 0);
+    auto it = h->graphs.find(key);
+    if (it != h->graphs.end()) {
+        *out = it->second;
+        return IBLB_OK;
+    }
+    const int cur0 = h->cur;
+    CK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < steps; k++) enqueue_step(h, h->cap, last && k == steps - 1);
+    cudaGraph_t graph;
+    cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
+    h->cur = cur0;
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    cudaGraphExec_t exec;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+    h->graphs[key] = exec;
+    *out = exec;
+    return IBLB_OK;
+}
+
+iblb_status check_device_flag(iblb_sim* h)
+{
+    int e = 0;
+    CK(h, cudaMemcpyAsync(&e, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (e & ERR_NODE_IN_WALL)
+        return fail(h, IBLB_ENODE_IN_WALL, "an interface node reached the wall (d <= 0)");
+    if (e & ERR_NONFINITE) return fail(h, IBLB_ENONFINITE, "non-finite density");
+    if (e & ERR_TIMEOUT) return fail(h, IBLB_ETIMEOUT, "a bounded device wait gave up");
+    return IBLB_OK;
+}
+
+double wetting_amplitude(const iblb_config& c)
+{
+    // Eq. 11: A = sigma (m-1)(n-1) / ((n-m) xi) (1 + cos theta_eq)
+    const double th = c.theta_eq_deg * (M_PI / 180.0);
+    return c.sigma * ((double)(c.pi_m - 1) * (double)(c.pi_n - 1)) /
+           ((double)(c.pi_n - c.pi_m) * c.xi) * (1.0 + std::cos(th));
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* iblb_status_string(iblb_status s)
+{
+    switch (s) {
+        case IBLB_OK: return "ok";
+        case IBLB_EINVAL: return "invalid argument";
+        case IBLB_ENOMEM: return "out of device memory";
+        case IBLB_ECUDA: return "CUDA error";
+        case IBLB_ENODE_IN_WALL: return "interface node in the wall";
+        case IBLB_ENONFINITE: return "non-finite density";
+        case IBLB_ETIMEOUT: return "device wait timed out";
+        case IBLB_EAGAIN: return "no room, try again";
+    }
+    return "unknown status";
+}
+
+const char* iblb_last_error(iblb_handle h) { return h ? h->msg.c_str() : "null handle"; }
+
+long long iblb_kernel_launch_count(void) { return g_launches.load(); }
+
+iblb_status iblb_create(const iblb_config* cfg, void* cuda_stream, iblb_handle* out)
+{
+    if (!cfg || !out) return IBLB_EINVAL;
+    *out = nullptr;
+    const iblb_config& c = *cfg;
+    if (c.lattice != IBLB_D2Q9 && c.lattice != IBLB_D3Q19) return IBLB_EINVAL;
+    const int dim = c.lattice == IBLB_D2Q9 ? 2 : 3;
+    const int nz = dim == 2 ? 1 : c.nz;
+    if (c.nx < 1 || c.ny < 1 || nz < 1) return IBLB_EINVAL;
+    const int Lw = dim == 2 ? c.ny : nz;
+    if (c.walls && Lw < 3) return IBLB_EINVAL;
+    if (!(c.tau > 0.5) || !std::isfinite(c.tau)) return IBLB_EINVAL;
+    if (c.storage < IBLB_FP64 || c.storage > IBLB_FP16_DEV) return IBLB_EINVAL;
+    if (c.wetting && (!c.walls || !(c.xi > 0.0) || !(c.pi_n > c.pi_m) || c.pi_m < 2))
+        return IBLB_EINVAL;
+    if (dim == 3 && (c.ny > 65535 || nz > 65535)) return IBLB_EINVAL;
+    if (dim == 2 && c.ny > 65535) return IBLB_EINVAL;
+    if (c.fp16_scale_exp < 0 || c.fp16_scale_exp > 24) return IBLB_EINVAL;
+
+    iblb_sim* h = new iblb_sim();
+    h->cfg = c;
+    h->cfg.nz = nz;
+    h->Q = c.lattice;
+    h->dim = dim;
+    h->storage = c.storage;
+    h->elt = c.storage == IBLB_FP64 ? 8 : (c.storage == IBLB_FP32_DEV ? 4 : 2);
+    h->relt = c.storage == IBLB_FP64 ? 8 : 4;
+    h->stream = (cudaStream_t)cuda_stream;
+    GridParams& g = h->g;
+    g.nx = c.nx;
+    g.ny = c.ny;
+    g.nz = nz;
+    g.dim = dim;
+    g.walls = c.walls ? 1 : 0;
+    g.nseg_x = (c.nx + 31) / 32;
+    g.ncell = (long long)c.nx * c.ny * nz;
+    h->nflags = (long long)c.ny * nz * g.nseg_x;
+    StreamParams& sp = h->sp;
+    sp.g = g;
+    sp.omega = 1.0 / c.tau;
+    for (int k = 0; k < 3; k++) sp.body[k] = (k < dim) ? c.body_force[k] : 0.0;
+    const int sexp = c.fp16_scale_exp ? c.fp16_scale_exp : 16;
+    sp.scale = c.storage == IBLB_FP16_DEV ? std::ldexp(1.0f, sexp) : 1.0f;
+    sp.inv_scale = 1.0f / sp.scale;
+    ForceParams& fp = h->fp;
+    fp.sigma = c.sigma;
+    fp.xi = c.xi;
+    fp.n = c.pi_n;
+    fp.m = c.pi_m;
+    fp.wetting = c.wetting ? 1 : 0;
+    fp.A = c.wetting ? wetting_amplitude(c) : 0.0;
+    fp.wall_plane = 0.5;
+
+    auto bail = [&](cudaError_t e, const char* where) {
+        iblb_destroy(h);
+        (void)where;
+        return e == cudaErrorMemoryAllocation ? IBLB_ENOMEM : IBLB_ECUDA;
+    };
+    cudaError_t e;
+    const size_t pop_bytes = (size_t)h->Q * g.ncell * h->elt;
+    for (int b = 0; b < 2; b++)
+        if ((e = cudaMalloc(&h->f[b], pop_bytes)) != cudaSuccess) return bail(e, "populations");
+    if ((e = cudaMalloc(&h->mom, (size_t)(1 + dim) * g.ncell * h->relt)) != cudaSuccess)
+        return bail(e, "moments");
+    if ((e = cudaMalloc(&h->F, (size_t)dim * g.ncell * h->relt)) != cudaSuccess)
+        return bail(e, "force");
+    if ((e = cudaMalloc(&h->flags, (size_t)h->nflags)) != cudaSuccess) return bail(e, "flags");
+    if ((e = cudaMalloc(&h->err, sizeof(int))) != cudaSuccess) return bail(e, "err");
+    h->npartial = mass_partial_blocks(g);
+    if ((e = cudaMalloc(&h->partial, sizeof(double) * h->npartial)) != cudaSuccess)
+        return bail(e, "partial");
+    if ((e = cudaMalloc(&h->obs, sizeof(double) * 12)) != cudaSuccess) return bail(e, "obs");
+    if ((e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(e, "stream");
+    // rest state: deviations are zero in every storage form
+    cudaMemsetAsync(h->f[0], 0, pop_bytes, h->stream);
+    cudaMemsetAsync(h->f[1], 0, pop_bytes, h->stream);
+    cudaMemsetAsync(h->F, 0, (size_t)dim * g.ncell * h->relt, h->stream);
+    cudaMemsetAsync(h->flags, 0, (size_t)h->nflags, h->stream);
+    cudaMemsetAsync(h->err, 0, sizeof(int), h->stream);
+    launch_init_moments(h->storage, g, h->mom, h->stream);
+    g_launches++;
+    sp.err = h->err;
+    if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "init");
+    *out = h;
+    return IBLB_OK;
+}
+
+void iblb_destroy(iblb_handle h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    clear_graphs(h);
+    free_dev(h->f[0]);
+    free_dev(h->f[1]);
+    free_dev(h->mom);
+    free_dev(h->F);
+    free_dev(h->flags);
+    free_dev(h->err);
+    free_dev(h->partial);
+    free_dev(h->obs);
+    free_dev(h->q);
+    free_dev(h->phi);
+    free_dev(h->tri);
+    free_dev(h->csr_ptr);
+    free_dev(h->csr_ent);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    delete h;
+}
+
+iblb_status iblb_set_interface(iblb_handle h, const double* xyz, int n_nodes, const int* tri,
+                               int n_faces)
+{
+    if (!h) return IBLB_EINVAL;
+    if (n_nodes < 0 || (n_nodes > 0 && !xyz)) return fail(h, IBLB_EINVAL, "bad node array");
+    if (n_nodes > 0 && n_nodes < 3) return fail(h, IBLB_EINVAL, "an interface needs >= 3 nodes");
+    if (h->dim == 2 && tri) return fail(h, IBLB_EINVAL, "2D interfaces are rings: tri must be NULL");
+    if (h->dim == 3 && n_nodes > 0 && (!tri || n_faces < 1))
+        return fail(h, IBLB_EINVAL, "3D interfaces need triangles");
+    const int dim = h->dim;
+    for (long long k = 0; k < (long long)n_nodes * dim; k++)
+        if (!std::isfinite(xyz[k])) return fail(h, IBLB_EINVAL, "non-finite node coordinate");
+    if (h->fp.wetting)
+        for (int j = 0; j < n_nodes; j++)
+            if (!(xyz[dim * j + dim - 1] - h->fp.wall_plane > 0.0))
+                return fail(h, IBLB_ENODE_IN_WALL, "a node lies at or below the wall plane");
+    std::vector<int> ptr, ent;
+    if (dim == 3 && n_nodes > 0) {
+        for (long long k = 0; k < 3LL * n_faces; k++)
+            if (tri[k] < 0 || tri[k] >= n_nodes)
+                return fail(h, IBLB_EINVAL, "triangle index out of range");
+        // node -> (face, corner) list, faces in increasing order per node
+        ptr.assign(n_nodes + 1, 0);
+        for (long long k = 0; k < 3LL * n_faces; k++) ptr[tri[k] + 1]++;
+        for (int j = 0; j < n_nodes; j++) ptr[j + 1] += ptr[j];
+        ent.resize(3LL * n_faces);
+        std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+        for (int f = 0; f < n_faces; f++)
+            for (int v = 0; v < 3; v++) ent[fill[tri[3 * f + v]]++] = 3 * f + v;
+        for (int j = 0; j < n_nodes; j++)
+            if (ptr[j + 1] == ptr[j]) return fail(h, IBLB_EINVAL, "a node belongs to no face");
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    clear_graphs(h);
+    free_dev(h->q);
+    free_dev(h->phi);
+    free_dev(h->tri);
+    free_dev(h->csr_ptr);
+    free_dev(h->csr_ent);
+    h->N = n_nodes;
+    h->M = dim == 2 ? n_nodes : n_faces;
+    if (n_nodes == 0) return IBLB_OK;
+    const size_t qb = sizeof(double) * (size_t)n_nodes * dim;
+    CK(h, cudaMalloc(&h->q, qb));
+    CK(h, cudaMalloc(&h->phi, qb));
+    CK(h, cudaMemcpyAsync(h->q, xyz, qb, cudaMemcpyHostToDevice, h->stream));
+    if (dim == 3) {
+        CK(h, cudaMalloc(&h->tri, sizeof(int) * 3 * (size_t)n_faces));
+        CK(h, cudaMalloc(&h->csr_ptr, sizeof(int) * (n_nodes + 1)));
+        CK(h, cudaMalloc(&h->csr_ent, sizeof(int) * ent.size()));
+        CK(h, cudaMemcpyAsync(h->tri, tri, sizeof(int) * 3 * (size_t)n_faces,
+                              cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaMemcpyAsync(h->csr_ptr, ptr.data(), sizeof(int) * ptr.size(),
+                              cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaMemcpyAsync(h->csr_ent, ent.data(), sizeof(int) * ent.size(),
+                              cudaMemcpyHostToDevice, h->stream));
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    return IBLB_OK;
+}
+
+iblb_status iblb_step(iblb_handle h, int n_steps)
+{
+    if (!h || n_steps < 0) return h ? fail(h, IBLB_EINVAL, "negative step count") : IBLB_EINVAL;
+    const int CHUNK = 32;
+    int left = n_steps;
+    while (left > 0) {
+        const int k = std::min(left, CHUNK);
+        const bool last = (k == left);
+        cudaGraphExec_t ge;
+        iblb_status st = get_graph(h, k, last, &ge);
+        if (st != IBLB_OK) return st;
+        CK(h, cudaGraphLaunch(ge, h->stream));
+        g_launches += (long long)k * kernels_per_step(h);
+        h->cur ^= (k & 1);
+        left -= k;
+    }
+    return IBLB_OK;
+}
+
+iblb_status iblb_sync(iblb_handle h)
+{
+    if (!h) return IBLB_EINVAL;
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaGetLastError());
+    return check_device_flag(h);
+}
+
+iblb_status iblb_read_fields(iblb_handle h, double* rho, double* u, double* xyz)
+{
+    if (!h) return IBLB_EINVAL;
+    const long long nc = h->g.ncell;
+    if (rho || u) {
+        double* tmp = nullptr;
+        CK(h, cudaMalloc(&tmp, sizeof(double) * (size_t)(1 + h->dim) * nc));
+        launch_unpack_moments(h->storage, h->g, h->mom, tmp, tmp + nc, h->stream);
+        g_launches++;
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess && rho)
+            e = cudaMemcpyAsync(rho, tmp, sizeof(double) * nc, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess && u)
+            e = cudaMemcpyAsync(u, tmp + nc, sizeof(double) * h->dim * nc, cudaMemcpyDeviceToHost,
+                                h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        cudaFree(tmp);
+        if (e != cudaSuccess) return cuda_fail(h, e, "read_fields");
+    }
+    if (xyz && h->N > 0)
+        CK(h, cudaMemcpyAsync(xyz, h->q, sizeof(double) * h->N * h->dim, cudaMemcpyDeviceToHost,
+                              h->stream));
+    return iblb_sync(h);
+}
+
+iblb_status iblb_set_populations(iblb_handle h, const double* f)
+{
+    if (!h || !f) return IBLB_EINVAL;
+    const size_t n = (size_t)h->Q * h->g.ncell;
+    double* tmp = nullptr;
+    CK(h, cudaMalloc(&tmp, sizeof(double) * n));
+    cudaError_t e = cudaMemcpyAsync(tmp, f, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) {
+        launch_pack_populations(h->Q, h->storage, tmp, h->f[h->cur], h->g.ncell, h->sp.scale,
+                                h->stream);
+        g_launches++;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_populations");
+    return IBLB_OK;
+}
+
+iblb_status iblb_get_populations(iblb_handle h, double* f)
+{
+    if (!h || !f) return IBLB_EINVAL;
+    const size_t n = (size_t)h->Q * h->g.ncell;
+    double* tmp = nullptr;
+    CK(h, cudaMalloc(&tmp, sizeof(double) * n));
+    launch_unpack_populations(h->Q, h->storage, h->f[h->cur], tmp, h->g.ncell, h->sp.inv_scale,
+                              h->stream);
+    g_launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(f, tmp, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(h, e, "get_populations");
+    return iblb_sync(h);
+}
+
+iblb_status iblb_observables(iblb_handle h, iblb_obs* out)
+{
+    if (!h || !out) return IBLB_EINVAL;
+    launch_mass_partials(h->Q, h->storage, h->f[h->cur], h->g, h->sp.inv_scale, h->partial,
+                         h->stream);
+    launch_observables(h->dim, h->q, h->N, h->tri, h->M, h->partial, h->npartial, h->cfg.xi, 0.5,
+                       h->obs, h->stream);
+    g_launches += 2;
+    CK(h, cudaGetLastError());
+    double v[12];
+    CK(h, cudaMemcpyAsync(v, h->obs, sizeof(v), cudaMemcpyDeviceToHost, h->stream));
+    iblb_status st = iblb_sync(h);
+    out->mass = v[0];
+    out->volume = v[1];
+    out->height = v[2];
+    out->theta_deg = v[3];
+    out->r_cl = v[4];
+    out->film = v[5];
+    out->d_min = v[6];
+    out->centre[0] = v[7];
+    out->centre[1] = v[8];
+    out->centre[2] = v[9];
+    out->radius = v[10];
+    return st;
+}
+
+iblb_status iblb_nodal_forces(iblb_handle h, double* phi, double* normal, double* chi)
+{
+    if (!h) return IBLB_EINVAL;
+    if (h->N == 0) return IBLB_OK;
+    const size_t nb = sizeof(double) * h->N * h->dim;
+    double *dn = nullptr, *dc = nullptr;
+    CK(h, cudaMalloc(&dn, nb));
+    CK(h, cudaMalloc(&dc, sizeof(double) * h->N));
+    launch_forces(h->dim, h->q, h->N, h->tri, h->csr_ptr, h->csr_ent, h->fp, h->phi, dn, dc,
+                  h->err, h->stream);
+    g_launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && phi)
+        e = cudaMemcpyAsync(phi, h->phi, nb, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && normal)
+        e = cudaMemcpyAsync(normal, dn, nb, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && chi)
+        e = cudaMemcpyAsync(chi, dc, sizeof(double) * h->N, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(dn);
+    cudaFree(dc);
+    if (e != cudaSuccess) return cuda_fail(h, e, "nodal_forces");
+    return iblb_sync(h);
+}
+
+iblb_status iblb_force_field(iblb_handle h, double* F)
+{
+    if (!h || !F) return IBLB_EINVAL;
+    const long long nc = h->g.ncell;
+    double* tmp = nullptr;
+    CK(h, cudaMalloc(&tmp, sizeof(double) * h->dim * nc));
+    if (h->N > 0) {
+        launch_forces(h->dim, h->q, h->N, h->tri, h->csr_ptr, h->csr_ent, h->fp, h->phi, nullptr,
+                      nullptr, h->err, h->stream);
+        launch_spread(h->storage, h->dim, h->q, h->phi, h->N, h->F, h->flags, h->g, h->stream);
+        g_launches += 2;
+    }
+    launch_unpack_force(h->storage, h->g, h->F, h->sp.body, tmp, h->stream);
+    g_launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(F, tmp, sizeof(double) * h->dim * nc, cudaMemcpyDeviceToHost,
+                            h->stream);
+    // leave the force buffer and the band flags cleared for the next step
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->F, 0, h->relt * h->dim * nc, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->flags, 0, (size_t)h->nflags, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(h, e, "force_field");
+    return iblb_sync(h);
+}
+
+iblb_status iblb_interpolate(iblb_handle h, const double* u, double* qdot)
+{
+    if (!h || !u || !qdot) return IBLB_EINVAL;
+    if (h->N == 0) return IBLB_OK;
+    const long long nc = h->g.ncell;
+    double* du = nullptr;
+    void* mtmp = nullptr;
+    double* dq = nullptr;
+    CK(h, cudaMalloc(&du, sizeof(double) * h->dim * nc));
+    CK(h, cudaMalloc(&mtmp, h->relt * (1 + h->dim) * nc));
+    CK(h, cudaMalloc(&dq, sizeof(double) * h->N * h->dim));
+    cudaError_t e =
+        cudaMemcpyAsync(du, u, sizeof(double) * h->dim * nc, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) {
+        launch_load_velocity(h->storage, h->dim, du, mtmp, nc, h->stream);
+        launch_interp(h->storage, h->dim, h->q, mtmp, h->N, dq, false, h->g, h->stream);
+        g_launches += 2;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(qdot, dq, sizeof(double) * h->N * h->dim, cudaMemcpyDeviceToHost,
+                            h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(du);
+    cudaFree(mtmp);
+    cudaFree(dq);
+    if (e != cudaSuccess) return cuda_fail(h, e, "interpolate");
+    return IBLB_OK;
+}
+
+iblb_status iblb_step_profiled(iblb_handle h, int n_steps, double* kernel_ms)
+{
+    if (!h || !kernel_ms || n_steps < 0) return IBLB_EINVAL;
+    for (int k = 0; k < IBLB_K_COUNT; k++) kernel_ms[k] = 0.0;
+    cudaEvent_t ev[IBLB_K_COUNT + 1];
+    for (auto& e : ev) CK(h, cudaEventCreate(&e));
+    for (int t = 0; t < n_steps; t++) {
+        const bool last = (t == n_steps - 1);
+        const bool ib = h->N > 0;
+        cudaEventRecord(ev[0], h->stream);
+        if (ib)
+            launch_forces(h->dim, h->q, h->N, h->tri, h->csr_ptr, h->csr_ent, h->fp, h->phi,
+                          nullptr, nullptr, h->err, h->stream);
+        cudaEventRecord(ev[1], h->stream);
+        if (ib) launch_spread(h->storage, h->dim, h->q, h->phi, h->N, h->F, h->flags, h->g, h->stream);
+        cudaEventRecord(ev[2], h->stream);
+        launch_stream_collide(h->Q, h->storage, last, h->f[h->cur], h->f[h->cur ^ 1], h->mom,
+                              h->F, h->flags, h->sp, h->stream);
+        cudaEventRecord(ev[3], h->stream);
+        if (ib) launch_interp(h->storage, h->dim, h->q, h->mom, h->N, nullptr, true, h->g, h->stream);
+        cudaEventRecord(ev[4], h->stream);
+        h->cur ^= 1;
+        g_launches += kernels_per_step(h);
+        CK(h, cudaEventSynchronize(ev[4]));
+        for (int k = 0; k < IBLB_K_COUNT; k++) {
+            float ms = 0.f;
+            CK(h, cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+            kernel_ms[k] += ms;
+        }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    CK(h, cudaGetLastError());
+    return check_device_flag(h);
+}
+
+double iblb_stream_bytes_per_step(iblb_handle h)
+{
+    if (!h) return 0.0;
+    return 2.0 * (double)h->Q * (double)h->elt * (double)iblb_fluid_cells(h);
+}
+
+long long iblb_fluid_cells(iblb_handle h)
+{
+    if (!h) return 0;
+    const GridParams& g = h->g;
+    if (!g.walls) return g.ncell;
+    if (g.dim == 2) return (long long)g.nx * (g.ny - 2);
+    return (long long)g.nx * g.ny * (g.nz - 2);
+}
+
+}  // extern "C"

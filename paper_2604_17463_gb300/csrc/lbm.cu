@@ -1,0 +1,441 @@
+// lbm.cu -- fused lattice Boltzmann stream-collide kernel (A4) and the
+// population / moment conversion kernels of libiblb.
+//
+// One time step of the lattice Boltzmann equation (Eq. 1) in pull form:
+//   f_i(x, t+1)  = f*_i(x - c_i, t)                 (exact streaming)
+//                  f*_opp(i)(x, t)  if x - c_i is a solid layer (halfway
+//                                   bounce-back at the flat walls)
+//   rho = sum_i f_i,  u = (sum_i c_i f_i + F/2) / rho          (Eq. 5-6)
+//   f*_i(x, t+1) = f_i - (f_i - f_i^eq(rho, u)) / tau + S_i(u, F)
+// with the second-order equilibrium (Eq. 3) and the Guo source (Eq. 4).
+//
+// Populations are stored as deviations from the rest state, g_i = f_i - w_i,
+// in FP64, FP32 or scaled binary16; the collision is written for deviations:
+//   g_i^eq = w_i (drho + rho (3 c.u + 9/2 (c.u)^2 - 3/2 u.u)),  drho = sum g_i
+//   g*_i   = g_i + omega (g_i^eq - g_i) + (1 - omega/2) w_i (3 (c_i - u).F + 9 (c_i.u)(c_i.F))
+// which is algebraically the same update as above (sum w_i = 1, sum w_i c_i = 0).
+//
+// Layout: structure of arrays, plane i at offset i * ncell, x fastest, so a
+// warp reads and writes 32 consecutive cells of one row per plane.  The force
+// density F is read (and cleared) only in 32-cell row segments flagged by the
+// spread kernel; elsewhere F is the uniform body force.  The moments are
+// written only in flagged segments (for the interpolation) or everywhere on
+// the last step of a call.
+#include "common.cuh"
+
+namespace iblb {
+
+template <int ST> struct StorageT;
+
+template <> struct StorageT<ST_FP64> {
+    using S = double;
+    using R = double;
+    __device__ __forceinline__ static R load(const S* p, long long i, float) { return p[i]; }
+    __device__ __forceinline__ static void store(S* p, long long i, R v, float) { p[i] = v; }
+};
+
+template <> struct StorageT<ST_FP32> {
+    using S = float;
+    using R = float;
+    __device__ __forceinline__ static R load(const S* p, long long i, float) { return p[i]; }
+    __device__ __forceinline__ static void store(S* p, long long i, R v, float) { p[i] = v; }
+};
+
+template <> struct StorageT<ST_FP16> {
+    using S = __half;
+    using R = float;
+    __device__ __forceinline__ static R load(const S* p, long long i, float inv_scale) {
+        return __half2float(p[i]) * inv_scale;
+    }
+    __device__ __forceinline__ static void store(S* p, long long i, R v, float scale) {
+        p[i] = __float2half_rn(v * scale);
+    }
+};
+
+constexpr int SC_BLOCK = 128;
+
+template <int Q, int ST, bool WRITE_ALL>
+__global__ void __launch_bounds__(SC_BLOCK)
+k_stream_collide(const typename StorageT<ST>::S* __restrict__ fin,
+                 typename StorageT<ST>::S* __restrict__ fout,
+                 typename StorageT<ST>::R* __restrict__ mom,
+                 typename StorageT<ST>::R* __restrict__ F,
+                 uint8_t* __restrict__ flags, const StreamParams p)
+{
+    using T = StorageT<ST>;
+    using R = typename T::R;
+    using L = Stencil<Q>;
+    constexpr int D = L::D;
+    const int nx = p.g.nx, ny = p.g.ny;
+    const long long nc = p.g.ncell;
+    const int walls = p.g.walls;
+    const int woff = walls ? 1 : 0;
+
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y, z;
+    if (D == 2) {
+        y = blockIdx.y + woff;
+        z = 0;
+    } else {
+        y = blockIdx.y;
+        z = blockIdx.z + woff;
+    }
+    const int lane = threadIdx.x & 31;
+    const long long row = (long long)z * ny + y;
+    const long long seg = row * p.g.nseg_x + (x >> 5);
+    int band = 0;
+    if (lane == 0 && (x >> 5) < p.g.nseg_x) band = flags[seg];
+    band = __shfl_sync(0xffffffffu, band, 0);
+    if (x >= nx) return;
+    const long long cell = row * nx + x;
+
+    // neighbours: periodic along x (and y in 3D); the wall axis (y in 2D,
+    // z in 3D) has solid first/last layers when walls != 0
+    const int xm = (x == 0) ? nx - 1 : x - 1;
+    const int xp = (x == nx - 1) ? 0 : x + 1;
+    const int Lw = (D == 2) ? ny : p.g.nz;
+    const int a = (D == 2) ? y : z;
+    int am = a - 1, ap = a + 1;
+    bool solid_m = false, solid_p = false;
+    if (walls) {
+        solid_m = (am == 0);
+        solid_p = (ap == Lw - 1);
+    } else {
+        if (am < 0) am = Lw - 1;
+        if (ap >= Lw) ap = 0;
+    }
+    int ym = y, yp = y;
+    if (D == 3) {
+        ym = (y == 0) ? ny - 1 : y - 1;
+        yp = (y == ny - 1) ? 0 : y + 1;
+    }
+
+    R g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+        const int sx = cx == 0 ? x : (cx > 0 ? xm : xp);
+        const int cw = (D == 2) ? cy : cz;  // velocity along the wall axis
+        const int sa = cw == 0 ? a : (cw > 0 ? am : ap);
+        const bool solid = cw == 0 ? false : (cw > 0 ? solid_m : solid_p);
+        long long src;
+        if (D == 2) {
+            src = (long long)sa * nx + sx;
+        } else {
+            const int sy = cy == 0 ? y : (cy > 0 ? ym : yp);
+            src = ((long long)sa * ny + sy) * nx + sx;
+        }
+        if (solid)
+            g[i] = T::load(fin, (long long)L::opp(i) * nc + cell, p.inv_scale);
+        else
+            g[i] = T::load(fin, (long long)i * nc + src, p.inv_scale);
+    }
+
+    // moments of the deviations
+    R drho = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        drho += g[i];
+        if (L::cx(i) > 0) jx += g[i];
+        if (L::cx(i) < 0) jx -= g[i];
+        if (L::cy(i) > 0) jy += g[i];
+        if (L::cy(i) < 0) jy -= g[i];
+        if (D == 3) {
+            if (L::cz(i) > 0) jz += g[i];
+            if (L::cz(i) < 0) jz -= g[i];
+        }
+    }
+    R Fx = (R)p.body[0], Fy = (R)p.body[1], Fz = (R)p.body[2];
+    if (band) {
+        Fx += F[cell];
+        Fy += F[nc + cell];
+        F[cell] = 0;
+        F[nc + cell] = 0;
+        if (D == 3) {
+            Fz += F[2 * nc + cell];
+            F[2 * nc + cell] = 0;
+        }
+    }
+    const R rho = R(1) + drho;
+    const R inv_rho = R(1) / rho;
+    const R ux = (jx + R(0.5) * Fx) * inv_rho;
+    const R uy = (jy + R(0.5) * Fy) * inv_rho;
+    const R uz = (D == 3) ? (jz + R(0.5) * Fz) * inv_rho : R(0);
+    const R usq15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
+    const R omega = (R)p.omega;
+    const R pref = R(1) - R(0.5) * omega;
+    const R uF = ux * Fx + uy * Fy + uz * Fz;
+
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        const R cx = (R)L::cx(i), cy = (R)L::cy(i), cz = (R)L::cz(i);
+        const R w = (R)L::w(i);
+        const R cu = cx * ux + cy * uy + (D == 3 ? cz * uz : R(0));
+        const R cF = cx * Fx + cy * Fy + (D == 3 ? cz * Fz : R(0));
+        const R geq = w * (drho + rho * (R(3) * cu + R(4.5) * cu * cu - usq15));
+        const R src = pref * w * (R(3) * (cF - uF) + R(9) * cu * cF);
+        const R gn = g[i] + omega * (geq - g[i]) + src;
+        T::store(fout, (long long)i * nc + cell, gn, p.scale);
+    }
+
+    if (WRITE_ALL || band) {
+        mom[cell] = drho;
+        mom[nc + cell] = ux;
+        mom[2 * nc + cell] = uy;
+        if (D == 3) mom[3 * nc + cell] = uz;
+    }
+    if (!isfinite(drho)) atomicOr(p.err, ERR_NONFINITE);
+    if (lane == 0 && band) flags[seg] = 0;
+}
+
+template <int Q, int ST>
+static void launch_sc_t(bool write_all, const void* fin, void* fout, void* mom, void* F,
+                        uint8_t* flags, const StreamParams& p, cudaStream_t s)
+{
+    using T = StorageT<ST>;
+    const int woff = p.g.walls ? 1 : 0;
+    dim3 block(SC_BLOCK);
+    dim3 grid((p.g.nx + SC_BLOCK - 1) / SC_BLOCK, 1, 1);
+    if (Q == 9) {
+        grid.y = p.g.ny - 2 * woff;
+    } else {
+        grid.y = p.g.ny;
+        grid.z = p.g.nz - 2 * woff;
+    }
+    auto* a = (const typename T::S*)fin;
+    auto* b = (typename T::S*)fout;
+    auto* m = (typename T::R*)mom;
+    auto* f = (typename T::R*)F;
+    if (write_all)
+        k_stream_collide<Q, ST, true><<<grid, block, 0, s>>>(a, b, m, f, flags, p);
+    else
+        k_stream_collide<Q, ST, false><<<grid, block, 0, s>>>(a, b, m, f, flags, p);
+}
+
+void launch_stream_collide(int Q, int storage, bool write_all, const void* fin, void* fout,
+                           void* moments, void* F, uint8_t* flags, const StreamParams& p,
+                           cudaStream_t s)
+{
+    if (Q == 9) {
+        if (storage == ST_FP64) launch_sc_t<9, ST_FP64>(write_all, fin, fout, moments, F, flags, p, s);
+        else if (storage == ST_FP32) launch_sc_t<9, ST_FP32>(write_all, fin, fout, moments, F, flags, p, s);
+        else launch_sc_t<9, ST_FP16>(write_all, fin, fout, moments, F, flags, p, s);
+    } else {
+        if (storage == ST_FP64) launch_sc_t<19, ST_FP64>(write_all, fin, fout, moments, F, flags, p, s);
+        else if (storage == ST_FP32) launch_sc_t<19, ST_FP32>(write_all, fin, fout, moments, F, flags, p, s);
+        else launch_sc_t<19, ST_FP16>(write_all, fin, fout, moments, F, flags, p, s);
+    }
+}
+
+// ------------------------------------------------------------------ conversions
+__device__ double weight_q(int Q, int i)
+{
+    return Q == 9 ? Stencil<9>::w(i) : Stencil<19>::w(i);
+}
+
+template <int ST>
+__global__ void k_pack(int Q, const double* __restrict__ f, typename StorageT<ST>::S* dst,
+                       long long ncell, float scale)
+{
+    const long long n = (long long)Q * ncell;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t / ncell);
+        const double dev = f[t] - weight_q(Q, i);
+        StorageT<ST>::store(dst, t, (typename StorageT<ST>::R)dev, scale);
+    }
+}
+
+template <int ST>
+__global__ void k_unpack(int Q, const typename StorageT<ST>::S* src, double* __restrict__ f,
+                         long long ncell, float inv_scale)
+{
+    const long long n = (long long)Q * ncell;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t / ncell);
+        f[t] = weight_q(Q, i) + (double)StorageT<ST>::load(src, t, inv_scale);
+    }
+}
+
+static int grid_for(long long n, int block = 256)
+{
+    long long b = (n + block - 1) / block;
+    if (b > 152 * 32) b = 152 * 32;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+void launch_pack_populations(int Q, int storage, const double* f, void* dst, long long ncell,
+                             float scale, cudaStream_t s)
+{
+    const int gb = grid_for((long long)Q * ncell);
+    if (storage == ST_FP64) k_pack<ST_FP64><<<gb, 256, 0, s>>>(Q, f, (double*)dst, ncell, scale);
+    else if (storage == ST_FP32) k_pack<ST_FP32><<<gb, 256, 0, s>>>(Q, f, (float*)dst, ncell, scale);
+    else k_pack<ST_FP16><<<gb, 256, 0, s>>>(Q, f, (__half*)dst, ncell, scale);
+}
+
+void launch_unpack_populations(int Q, int storage, const void* src, double* f, long long ncell,
+                               float inv_scale, cudaStream_t s)
+{
+    const int gb = grid_for((long long)Q * ncell);
+    if (storage == ST_FP64) k_unpack<ST_FP64><<<gb, 256, 0, s>>>(Q, (const double*)src, f, ncell, inv_scale);
+    else if (storage == ST_FP32) k_unpack<ST_FP32><<<gb, 256, 0, s>>>(Q, (const float*)src, f, ncell, inv_scale);
+    else k_unpack<ST_FP16><<<gb, 256, 0, s>>>(Q, (const __half*)src, f, ncell, inv_scale);
+}
+
+__device__ __forceinline__ bool is_solid_cell(const GridParams& g, long long c)
+{
+    if (!g.walls) return false;
+    const long long plane = (long long)g.nx * g.ny;
+    const int a = (g.dim == 2) ? (int)((c / g.nx) % g.ny) : (int)(c / plane);
+    const int Lw = (g.dim == 2) ? g.ny : g.nz;
+    return a == 0 || a == Lw - 1;
+}
+
+template <typename R>
+__global__ void k_unpack_moments(GridParams g, const R* __restrict__ mom, double* rho, double* u)
+{
+    const long long ncell = g.ncell;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+         c += (long long)gridDim.x * blockDim.x) {
+        const bool solid = is_solid_cell(g, c);
+        if (rho) rho[c] = solid ? 0.0 : 1.0 + (double)mom[c];
+        if (u)
+            for (int k = 0; k < g.dim; k++)
+                u[k * ncell + c] = solid ? 0.0 : (double)mom[(k + 1) * ncell + c];
+    }
+}
+
+void launch_unpack_moments(int storage, const GridParams& g, const void* moments, double* rho,
+                           double* u, cudaStream_t s)
+{
+    const int gb = grid_for(g.ncell);
+    if (storage == ST_FP64)
+        k_unpack_moments<double><<<gb, 256, 0, s>>>(g, (const double*)moments, rho, u);
+    else
+        k_unpack_moments<float><<<gb, 256, 0, s>>>(g, (const float*)moments, rho, u);
+}
+
+template <typename R>
+__global__ void k_init_moments(GridParams g, R* mom)
+{
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
+         c += (long long)gridDim.x * blockDim.x) {
+        mom[c] = is_solid_cell(g, c) ? R(-1) : R(0);
+        for (int k = 0; k < g.dim; k++) mom[(k + 1) * g.ncell + c] = R(0);
+    }
+}
+
+void launch_init_moments(int storage, const GridParams& g, void* moments, cudaStream_t s)
+{
+    const int gb = grid_for(g.ncell);
+    if (storage == ST_FP64) k_init_moments<double><<<gb, 256, 0, s>>>(g, (double*)moments);
+    else k_init_moments<float><<<gb, 256, 0, s>>>(g, (float*)moments);
+}
+
+template <typename R>
+__global__ void k_load_velocity(int dim, const double* __restrict__ u, R* mom, long long ncell)
+{
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+         c += (long long)gridDim.x * blockDim.x)
+        for (int k = 0; k < dim; k++) mom[(k + 1) * ncell + c] = (R)u[k * ncell + c];
+}
+
+void launch_load_velocity(int storage, int dim, const double* u, void* moments, long long ncell,
+                          cudaStream_t s)
+{
+    const int gb = grid_for(ncell);
+    if (storage == ST_FP64) k_load_velocity<double><<<gb, 256, 0, s>>>(dim, u, (double*)moments, ncell);
+    else k_load_velocity<float><<<gb, 256, 0, s>>>(dim, u, (float*)moments, ncell);
+}
+
+template <typename R>
+__global__ void k_unpack_force(GridParams g, const R* __restrict__ F, double b0, double b1,
+                               double b2, double* out)
+{
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
+         c += (long long)gridDim.x * blockDim.x) {
+        const bool solid = is_solid_cell(g, c);
+        const double body[3] = {b0, b1, b2};
+        for (int k = 0; k < g.dim; k++)
+            out[k * g.ncell + c] = solid ? 0.0 : (double)F[k * g.ncell + c] + body[k];
+    }
+}
+
+void launch_unpack_force(int storage, const GridParams& g, const void* F, const double* body,
+                         double* out, cudaStream_t s)
+{
+    const int gb = grid_for(g.ncell);
+    if (storage == ST_FP64)
+        k_unpack_force<double><<<gb, 256, 0, s>>>(g, (const double*)F, body[0], body[1], body[2], out);
+    else
+        k_unpack_force<float><<<gb, 256, 0, s>>>(g, (const float*)F, body[0], body[1], body[2], out);
+}
+
+__global__ void k_fill_flags(uint8_t* flags, long long n, uint8_t v)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x)
+        flags[t] = v;
+}
+
+void launch_clear_flags(uint8_t* flags, long long n, cudaStream_t s)
+{
+    k_fill_flags<<<grid_for(n), 256, 0, s>>>(flags, n, 0);
+}
+
+void launch_set_all_flags(uint8_t* flags, long long n, cudaStream_t s)
+{
+    k_fill_flags<<<grid_for(n), 256, 0, s>>>(flags, n, 1);
+}
+
+// ------------------------------------------------------------------ mass
+constexpr int MASS_BLOCK = 256;
+
+int mass_partial_blocks(const GridParams& g)
+{
+    long long b = (g.ncell + MASS_BLOCK - 1) / MASS_BLOCK;
+    if (b > 1024) b = 1024;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+template <int ST>
+__global__ void __launch_bounds__(MASS_BLOCK)
+k_mass_partials(int Q, const typename StorageT<ST>::S* __restrict__ f, GridParams g,
+                float inv_scale, double* partial)
+{
+    double acc = 0.0;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
+         c += (long long)gridDim.x * blockDim.x) {
+        if (is_solid_cell(g, c)) continue;
+        double dev = 0.0;
+        for (int i = 0; i < Q; i++)
+            dev += (double)StorageT<ST>::load(f, (long long)i * g.ncell + c, inv_scale);
+        acc += 1.0 + dev;
+    }
+    __shared__ double red[MASS_BLOCK / 32];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < MASS_BLOCK / 32; k++) t += red[k];
+        partial[blockIdx.x] = t;
+    }
+}
+
+void launch_mass_partials(int Q, int storage, const void* f, const GridParams& g, float inv_scale,
+                          double* partial, cudaStream_t s)
+{
+    const int nb = mass_partial_blocks(g);
+    if (storage == ST_FP64)
+        k_mass_partials<ST_FP64><<<nb, MASS_BLOCK, 0, s>>>(Q, (const double*)f, g, inv_scale, partial);
+    else if (storage == ST_FP32)
+        k_mass_partials<ST_FP32><<<nb, MASS_BLOCK, 0, s>>>(Q, (const float*)f, g, inv_scale, partial);
+    else
+        k_mass_partials<ST_FP16><<<nb, MASS_BLOCK, 0, s>>>(Q, (const __half*)f, g, inv_scale, partial);
+}
+
+}  // namespace iblb

@@ -1,0 +1,242 @@
+"""CUDA path (through the C-ABI) against the FP64 oracle, element by element.
+
+Tolerances: FP64 storage, relative L2 <= 1e-10 on density and velocity (and
+per-kernel comparisons at round-off level); FP32 deviation storage,
+relative L2 <= 1e-5 on velocity and on rho - 1.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_17463_gb300 import iblb
+from paper_2604_17463_gb300 import workloads as W
+from helpers import fluid_mask, oracle_from_workload, rel_l2, small_2d, small_3d
+
+pytestmark = pytest.mark.gpu
+
+
+def near_eq(Q, shape, seed, amp=0.03):
+    _, w, _ = oracle.lattice(Q)
+    return w.reshape((Q,) + (1,) * len(shape)) * (1.0 + W.random_perturbation((Q,) + shape, seed, amp))
+
+
+@pytest.mark.parametrize("Q,dims", [(9, (37, 21, 1)), (9, (128, 64, 1)), (19, (45, 12, 11))])
+@pytest.mark.parametrize("walls", [True, False])
+@pytest.mark.parametrize("storage,tol", [(iblb.FP64, 1e-14), (iblb.FP32_DEV, 2e-7)])
+def test_stream_collide_random_populations(Q, dims, walls, storage, tol):
+    nx, ny, nz = dims
+    shape = (nz, ny, nx)
+    body = (1e-5, -2e-5, 3e-6 if Q == 19 else 0.0)
+    f0 = near_eq(Q, shape, seed=21 + nx)
+    o = oracle.Sim(Q, nx, ny, nz, tau=0.77, walls=walls, wetting=False, body_force=body)
+    g = iblb.Simulation(Q, nx, ny, nz, tau=0.77, walls=walls, wetting=False, body_force=body,
+                        storage=storage)
+    o.set_populations(f0)
+    g.set_populations(f0)
+    o.step(3)
+    g.step(3)
+    fo, fg = o.populations(), g.populations()
+    m = fluid_mask(shape, 2 if Q == 9 else 3, walls)
+    assert np.max(np.abs(fg[:, m] - fo[:, m])) < tol
+    ro, uo, _ = o.fields()
+    rg, ug, _ = g.fields()
+    dim = 2 if Q == 9 else 3
+    assert np.max(np.abs(rg - ro)) < 10 * tol
+    assert np.max(np.abs(ug - uo[:dim])) < 10 * tol
+    g.close()
+
+
+@pytest.mark.parametrize("which", ["2d", "3d"])
+def test_nodal_forces_match(which):
+    rng = np.random.default_rng(31)
+    wl = small_2d() if which == "2d" else small_3d()
+    wl.nodes = wl.nodes + rng.uniform(-0.2, 0.2, wl.nodes.shape)
+    o = oracle_from_workload(wl)
+    g = iblb.Simulation.from_workload(wl)
+    po, no, co, bad = o.nodal_forces()
+    pg, ng, cg = g.nodal_forces()
+    assert not bad
+    assert np.max(np.abs(pg - po)) <= 1e-13 * np.max(np.abs(po))
+    assert np.max(np.abs(ng - no)) < 1e-13
+    assert np.max(np.abs(cg - co)) < 1e-12
+    g.close()
+
+
+@pytest.mark.parametrize("which", ["2d", "3d"])
+@pytest.mark.parametrize("storage,tol", [(iblb.FP64, 1e-13), (iblb.FP32_DEV, 1e-6)])
+def test_force_field_match(which, storage, tol):
+    wl = small_2d() if which == "2d" else small_3d()
+    o = oracle_from_workload(wl)
+    g = iblb.Simulation.from_workload(wl, storage=storage)
+    Fo, bad = o.force_field()
+    Fg = g.force_field()
+    dim = wl.dim
+    scale = np.max(np.abs(Fo[:dim]))
+    assert scale > 0
+    assert np.max(np.abs(Fg - Fo[:dim])) <= tol * scale
+    # a second call sees the same field: the device force buffer was cleared
+    Fg2 = g.force_field()
+    assert np.max(np.abs(Fg2 - Fg)) <= tol * scale
+    g.close()
+
+
+@pytest.mark.parametrize("which", ["2d", "3d"])
+def test_interpolate_match(which):
+    wl = small_2d() if which == "2d" else small_3d()
+    o = oracle_from_workload(wl)
+    g = iblb.Simulation.from_workload(wl)
+    rng = np.random.default_rng(41)
+    u = rng.normal(size=(3,) + o.shape) * 1e-3
+    if wl.dim == 2:
+        u[2] = 0.0
+    qo = o.interpolate(u)
+    qg = g.interpolate(u)
+    assert np.max(np.abs(qg - qo)) < 1e-17 + 1e-13 * np.max(np.abs(qo))
+    g.close()
+
+
+@pytest.mark.parametrize("which,steps", [("2d", 50), ("3d", 12)])
+def test_full_step_fp64(which, steps):
+    wl = small_2d() if which == "2d" else small_3d()
+    o = oracle_from_workload(wl)
+    g = iblb.Simulation.from_workload(wl)
+    assert o.step(steps) == 0
+    g.step(steps)
+    ro, uo, qo = o.fields()
+    rg, ug, qg = g.fields()
+    m = fluid_mask(o.shape, wl.dim)
+    assert rel_l2(rg[m], ro[m]) < 1e-12
+    assert rel_l2(rg[m] - 1.0, ro[m] - 1.0) < 1e-10
+    assert rel_l2(ug[:, m], uo[: wl.dim, m]) < 1e-10
+    assert np.max(np.abs(qg - qo)) < 1e-11
+    g.close()
+
+
+def test_config1_fp64_2000_steps():
+    wl = W.config1()
+    o = oracle_from_workload(wl)
+    g = iblb.Simulation.from_workload(wl)
+    assert o.step(wl.steps) == 0
+    g.step(wl.steps)
+    ro, uo, qo = o.fields()
+    rg, ug, qg = g.fields()
+    m = fluid_mask(o.shape, 2)
+    assert rel_l2(rg[m], ro[m]) < 1e-10
+    assert rel_l2(rg[m] - 1.0, ro[m] - 1.0) < 1e-10
+    assert rel_l2(ug[:, m], uo[:2, m]) < 1e-10
+    assert rel_l2(qg, qo) < 1e-12
+    # observables of the same state
+    oo, og = o.observables(), g.observables()
+    for k in ("mass", "volume", "height", "theta_deg", "r_cl", "film", "d_min", "radius"):
+        assert math.isclose(og[k], oo[k], rel_tol=1e-9, abs_tol=1e-12), (k, og[k], oo[k])
+    g.close()
+
+
+def test_config1_fp32_2000_steps():
+    wl = W.config1()
+    o = oracle_from_workload(wl)
+    g = iblb.Simulation.from_workload(wl, storage=iblb.FP32_DEV)
+    assert o.step(wl.steps) == 0
+    g.step(wl.steps)
+    ro, uo, qo = o.fields()
+    rg, ug, qg = g.fields()
+    m = fluid_mask(o.shape, 2)
+    assert rel_l2(rg[m], ro[m]) < 1e-5
+    assert rel_l2(rg[m] - 1.0, ro[m] - 1.0) < 1e-5
+    assert rel_l2(ug[:, m], uo[:2, m]) < 1e-5
+    g.close()
+
+
+def test_observables_same_state_3d():
+    wl = small_3d()
+    o = oracle_from_workload(wl)
+    g = iblb.Simulation.from_workload(wl)
+    o.step(5)
+    g.step(5)
+    oo, og = o.observables(), g.observables()
+    for k in ("mass", "volume", "height", "theta_deg", "r_cl", "d_min", "radius"):
+        assert math.isclose(og[k], oo[k], rel_tol=1e-9, abs_tol=1e-12), (k, og[k], oo[k])
+    g.close()
+
+
+def test_ragged_and_seam_2d():
+    # width not a multiple of 32, drop straddling the periodic seam
+    wl = small_2d(nx=45, ny=26, R=6.0, cx=1.3)
+    o = oracle_from_workload(wl)
+    g = iblb.Simulation.from_workload(wl)
+    o.step(30)
+    g.step(30)
+    ro, uo, qo = o.fields()
+    rg, ug, qg = g.fields()
+    m = fluid_mask(o.shape, 2)
+    assert rel_l2(ug[:, m], uo[:2, m]) < 1e-10
+    assert np.max(np.abs(qg - qo)) < 1e-11
+    g.close()
+
+
+def test_no_interface_and_periodic_box():
+    o = oracle.Sim(19, 13, 9, 7, tau=0.6, walls=False, wetting=False, body_force=(1e-6, 0, 0))
+    g = iblb.Simulation(19, 13, 9, 7, tau=0.6, walls=False, wetting=False, body_force=(1e-6, 0, 0))
+    o.step(7)
+    g.step(7)
+    assert np.max(np.abs(g.populations() - o.populations())) < 1e-15
+    g.close()
+
+
+def test_step_in_pieces_equals_one_call():
+    wl = small_2d()
+    a = iblb.Simulation.from_workload(wl)
+    b = iblb.Simulation.from_workload(wl)
+    a.step(37)
+    for n in (1, 2, 33, 1):
+        b.step(n)
+    fa, fb = a.populations(), b.populations()
+    assert np.max(np.abs(fa - fb)) < 1e-15
+    _, _, qa = a.fields()
+    _, _, qb = b.fields()
+    assert np.max(np.abs(qa - qb)) < 1e-12
+    a.close()
+    b.close()
+
+
+def test_errors_are_reported():
+    # invalid configuration
+    with pytest.raises(iblb.IBLBError) as e:
+        iblb.Simulation(9, 16, 16, tau=0.4)
+    assert e.value.status == 1
+    # node below the wall plane is rejected at upload
+    g = iblb.Simulation(9, 32, 20, tau=1.0, wetting=True, xi=1.0)
+    nodes = W.circle(20, 4.0, (16.0, 4.0))
+    with pytest.raises(iblb.IBLBError) as e:
+        g.set_interface(nodes)
+    assert e.value.status == 4
+    # 2D rings take no triangles
+    with pytest.raises(iblb.IBLBError):
+        iblb.iblb_set_interface(g.h, W.circle(20, 4.0, (16.0, 9.0)), np.zeros((1, 3), np.int32))
+    g.close()
+
+
+def test_nonfinite_population_latches_flag():
+    # a NaN population makes the density non-finite; the stream-collide kernel
+    # latches the device flag and the next synchronising call reports it
+    g = iblb.Simulation(9, 16, 12, tau=0.8, wetting=False)
+    f = g.populations()
+    f[3, 0, 5, 7] = np.nan
+    g.set_populations(f)
+    g.step(2)
+    with pytest.raises(iblb.IBLBError) as e:
+        g.sync()
+    assert e.value.status == 5
+    g.close()
+
+
+def test_launch_counter_counts_kernels():
+    wl = small_2d()
+    g = iblb.Simulation.from_workload(wl)
+    n0 = iblb.iblb_kernel_launch_count()
+    g.step(10)
+    g.sync()
+    assert iblb.iblb_kernel_launch_count() - n0 == 40
+    g.close()

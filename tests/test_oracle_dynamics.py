@@ -239,13 +239,16 @@ def test_film_thickness_scales_with_xi():
 
 
 def test_contact_angle_follows_theta_eq():
+    # with the film resolved (xi = 2 lu) the fitted angle settles near theta_eq
+    # (Eq. 11 as printed, film of the outer phase); the remaining excess
+    # shrinks further as xi / dx grows and with time
     th = []
     for t in (60.0, 90.0, 120.0):
-        rc, o, _ = wet_drop(t, 1.0, steps=6000)
+        rc, o, _ = wet_drop(t, 2.0, R=12.0, steps=8000, nx=80, ny=40)
         assert rc == 0
         th.append(o["theta_deg"])
     assert th[0] < th[1] < th[2]
-    assert all(abs(m - t) < 20.0 for m, t in zip(th, (60.0, 90.0, 120.0)))
+    assert all(0.0 < m - t < 12.0 for m, t in zip(th, (60.0, 90.0, 120.0))), th
 
 
 def test_config1_volume_drift_and_wall():
