@@ -157,6 +157,11 @@ enum {
  * each kernel (ms).  Synchronises. */
 iblb_status iblb_step_profiled(iblb_handle h, int n_steps, double* kernel_ms);
 
+/* Launch shape of the stream-collide kernel: block_x threads per block along
+ * x (64, 128 or 256) and evict-first stores of the new populations
+ * (streaming_stores != 0).  Results do not depend on it.  Synchronises. */
+iblb_status iblb_set_tuning(iblb_handle h, int block_x, int streaming_stores);
+
 /* Algorithmic HBM bytes of one stream-collide launch: populations read once
  * and written once per fluid cell. */
 double iblb_stream_bytes_per_step(iblb_handle h);

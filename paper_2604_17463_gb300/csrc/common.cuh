@@ -89,6 +89,12 @@ struct ForceParams {
     double wall_plane;     // 0.5
 };
 
+// Launch shape of the stream-collide kernel (chosen by the autotuner).
+struct Tuning {
+    int block_x = 128;          // threads per block along x: 64, 128 or 256
+    int streaming_stores = 0;   // 1: evict-first stores of the new populations
+};
+
 // ------------------------------------------------------------------ launchers
 // Storage ids match iblb_storage.
 enum Storage : int { ST_FP64 = 0, ST_FP32 = 1, ST_FP16 = 2 };
@@ -99,7 +105,7 @@ enum Storage : int { ST_FP64 = 0, ST_FP32 = 1, ST_FP16 = 2 };
 // density [dim][ncell], read and cleared only in flagged band segments.
 void launch_stream_collide(int Q, int storage, bool write_all, const void* fin, void* fout,
                            void* moments, void* F, uint8_t* flags, const StreamParams& p,
-                           cudaStream_t s);
+                           const Tuning& tu, cudaStream_t s);
 
 // Host FP64 <-> device storage conversion of populations ([Q][ncell], f_i).
 void launch_pack_populations(int Q, int storage, const double* f, void* dst, long long ncell,
@@ -126,9 +132,12 @@ void launch_mass_partials(int Q, int storage, const void* f, const GridParams& g
                           double* partial, cudaStream_t s);
 
 // IB kernels.  q, phi: [N][dim] FP64.
-void launch_forces(int dim, const double* q, int N, const int* tri, const int* csr_ptr,
-                   const int* csr_ent, const ForceParams& fp, double* phi, double* normal,
-                   double* chi, int* err, cudaStream_t s);
+// 2D ring: one kernel; 3D mesh: per-face geometry into face_rec (16 doubles
+// per face) then a per-node CSR gather (two kernels).
+void launch_forces(int dim, const double* q, int N, int M, const int* tri, const int* csr_ptr,
+                   const int* csr_ent, double* face_rec, const ForceParams& fp, double* phi,
+                   double* normal, double* chi, int* err, cudaStream_t s);
+constexpr int FACE_RECORD_DOUBLES = 16;
 void launch_spread(int storage, int dim, const double* q, const double* phi, int N, void* F,
                    uint8_t* flags, const GridParams& g, cudaStream_t s);
 // qdot [N][dim] = sum u Delta; if advect, q += qdot.

@@ -32,6 +32,7 @@ struct iblb_sim {
     size_t relt = 8;           // compute-precision element size
     GridParams g{};
     StreamParams sp{};
+    Tuning tune{};
     ForceParams fp{};
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;  // private stream used only for graph capture
@@ -52,6 +53,7 @@ struct iblb_sim {
     int* tri = nullptr;
     int* csr_ptr = nullptr;
     int* csr_ent = nullptr;
+    double* face_rec = nullptr;  // per-face geometry records (3D)
     std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;  // (parity, steps, last)
     std::string msg;
 };
@@ -88,18 +90,19 @@ void clear_graphs(iblb_sim* h)
     h->graphs.clear();
 }
 
-int kernels_per_step(const iblb_sim* h) { return h->N > 0 ? 4 : 1; }
+int force_kernels(const iblb_sim* h) { return h->dim == 3 ? 2 : 1; }
+int kernels_per_step(const iblb_sim* h) { return h->N > 0 ? 3 + force_kernels(h) : 1; }
 
 // Enqueue one time step on stream s (buffers by the current parity).
 void enqueue_step(iblb_sim* h, cudaStream_t s, bool write_all)
 {
     if (h->N > 0) {
-        launch_forces(h->dim, h->q, h->N, h->tri, h->csr_ptr, h->csr_ent, h->fp, h->phi, nullptr,
+        launch_forces(h->dim, h->q, h->N, h->M, h->tri, h->csr_ptr, h->csr_ent, h->face_rec, h->fp, h->phi, nullptr,
                       nullptr, h->err, s);
         launch_spread(h->storage, h->dim, h->q, h->phi, h->N, h->F, h->flags, h->g, s);
     }
     launch_stream_collide(h->Q, h->storage, write_all, h->f[h->cur], h->f[h->cur ^ 1], h->mom,
-                          h->F, h->flags, h->sp, s);
+                          h->F, h->flags, h->sp, h->tune, s);
     if (h->N > 0)
         launch_interp(h->storage, h->dim, h->q, h->mom, h->N, nullptr, true, h->g, s);
     h->cur ^= 1;
@@ -278,6 +281,7 @@ void iblb_destroy(iblb_handle h)
     free_dev(h->tri);
     free_dev(h->csr_ptr);
     free_dev(h->csr_ent);
+    free_dev(h->face_rec);
     if (h->cap) cudaStreamDestroy(h->cap);
     delete h;
 }
@@ -321,6 +325,7 @@ iblb_status iblb_set_interface(iblb_handle h, const double* xyz, int n_nodes, co
     free_dev(h->tri);
     free_dev(h->csr_ptr);
     free_dev(h->csr_ent);
+    free_dev(h->face_rec);
     h->N = n_nodes;
     h->M = dim == 2 ? n_nodes : n_faces;
     if (n_nodes == 0) return IBLB_OK;
@@ -332,6 +337,7 @@ iblb_status iblb_set_interface(iblb_handle h, const double* xyz, int n_nodes, co
         CK(h, cudaMalloc(&h->tri, sizeof(int) * 3 * (size_t)n_faces));
         CK(h, cudaMalloc(&h->csr_ptr, sizeof(int) * (n_nodes + 1)));
         CK(h, cudaMalloc(&h->csr_ent, sizeof(int) * ent.size()));
+        CK(h, cudaMalloc(&h->face_rec, sizeof(double) * FACE_RECORD_DOUBLES * (size_t)n_faces));
         CK(h, cudaMemcpyAsync(h->tri, tri, sizeof(int) * 3 * (size_t)n_faces,
                               cudaMemcpyHostToDevice, h->stream));
         CK(h, cudaMemcpyAsync(h->csr_ptr, ptr.data(), sizeof(int) * ptr.size(),
@@ -466,9 +472,9 @@ iblb_status iblb_nodal_forces(iblb_handle h, double* phi, double* normal, double
     double *dn = nullptr, *dc = nullptr;
     CK(h, cudaMalloc(&dn, nb));
     CK(h, cudaMalloc(&dc, sizeof(double) * h->N));
-    launch_forces(h->dim, h->q, h->N, h->tri, h->csr_ptr, h->csr_ent, h->fp, h->phi, dn, dc,
+    launch_forces(h->dim, h->q, h->N, h->M, h->tri, h->csr_ptr, h->csr_ent, h->face_rec, h->fp, h->phi, dn, dc,
                   h->err, h->stream);
-    g_launches++;
+    g_launches += force_kernels(h);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && phi)
         e = cudaMemcpyAsync(phi, h->phi, nb, cudaMemcpyDeviceToHost, h->stream);
@@ -490,10 +496,10 @@ iblb_status iblb_force_field(iblb_handle h, double* F)
     double* tmp = nullptr;
     CK(h, cudaMalloc(&tmp, sizeof(double) * h->dim * nc));
     if (h->N > 0) {
-        launch_forces(h->dim, h->q, h->N, h->tri, h->csr_ptr, h->csr_ent, h->fp, h->phi, nullptr,
+        launch_forces(h->dim, h->q, h->N, h->M, h->tri, h->csr_ptr, h->csr_ent, h->face_rec, h->fp, h->phi, nullptr,
                       nullptr, h->err, h->stream);
         launch_spread(h->storage, h->dim, h->q, h->phi, h->N, h->F, h->flags, h->g, h->stream);
-        g_launches += 2;
+        g_launches += force_kernels(h) + 1;
     }
     launch_unpack_force(h->storage, h->g, h->F, h->sp.body, tmp, h->stream);
     g_launches++;
@@ -551,13 +557,13 @@ iblb_status iblb_step_profiled(iblb_handle h, int n_steps, double* kernel_ms)
         const bool ib = h->N > 0;
         cudaEventRecord(ev[0], h->stream);
         if (ib)
-            launch_forces(h->dim, h->q, h->N, h->tri, h->csr_ptr, h->csr_ent, h->fp, h->phi,
+            launch_forces(h->dim, h->q, h->N, h->M, h->tri, h->csr_ptr, h->csr_ent, h->face_rec, h->fp, h->phi,
                           nullptr, nullptr, h->err, h->stream);
         cudaEventRecord(ev[1], h->stream);
         if (ib) launch_spread(h->storage, h->dim, h->q, h->phi, h->N, h->F, h->flags, h->g, h->stream);
         cudaEventRecord(ev[2], h->stream);
         launch_stream_collide(h->Q, h->storage, last, h->f[h->cur], h->f[h->cur ^ 1], h->mom,
-                              h->F, h->flags, h->sp, h->stream);
+                              h->F, h->flags, h->sp, h->tune, h->stream);
         cudaEventRecord(ev[3], h->stream);
         if (ib) launch_interp(h->storage, h->dim, h->q, h->mom, h->N, nullptr, true, h->g, h->stream);
         cudaEventRecord(ev[4], h->stream);
@@ -573,6 +579,18 @@ iblb_status iblb_step_profiled(iblb_handle h, int n_steps, double* kernel_ms)
     for (auto& e : ev) cudaEventDestroy(e);
     CK(h, cudaGetLastError());
     return check_device_flag(h);
+}
+
+iblb_status iblb_set_tuning(iblb_handle h, int block_x, int streaming_stores)
+{
+    if (!h) return IBLB_EINVAL;
+    if (block_x != 64 && block_x != 128 && block_x != 256)
+        return fail(h, IBLB_EINVAL, "block_x must be 64, 128 or 256");
+    CK(h, cudaStreamSynchronize(h->stream));
+    clear_graphs(h);
+    h->tune.block_x = block_x;
+    h->tune.streaming_stores = streaming_stores ? 1 : 0;
+    return IBLB_OK;
 }
 
 double iblb_stream_bytes_per_step(iblb_handle h)

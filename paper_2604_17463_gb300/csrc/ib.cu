@@ -83,9 +83,46 @@ __global__ void k_forces_ring(const double* __restrict__ q, int N, ForceParams f
     if (chi) chi[j] = ch;
 }
 
-// 3D mesh: one thread per node, gathering over its faces from a CSR list of
-// (face, corner) entries sorted by face (no atomics).
-__global__ void k_forces_mesh(const double* __restrict__ q, int N, const int* __restrict__ tri,
+// 3D mesh, pass 1: one thread per face computes the unit normal nu_f, the
+// area A_f and, for each corner v, g_v = nu_f x (prev - next), so that
+// d(A_f)/d(corner v) = g_v / 2.  Record: nu[3], A, g[3][3], pad (16 doubles).
+constexpr int FACE_REC = 16;
+
+__global__ void k_face_geometry(const double* __restrict__ q, const int* __restrict__ tri, int M,
+                                double* __restrict__ rec)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= M) return;
+    double P[3][3];
+    for (int c = 0; c < 3; c++) {
+        const int node = tri[3 * f + c];
+        for (int k = 0; k < 3; k++) P[c][k] = q[3 * node + k];
+    }
+    const double ab[3] = {P[1][0] - P[0][0], P[1][1] - P[0][1], P[1][2] - P[0][2]};
+    const double ac[3] = {P[2][0] - P[0][0], P[2][1] - P[0][1], P[2][2] - P[0][2]};
+    const double nf[3] = {ab[1] * ac[2] - ab[2] * ac[1], ab[2] * ac[0] - ab[0] * ac[2],
+                          ab[0] * ac[1] - ab[1] * ac[0]};
+    const double nlen = sqrt(nf[0] * nf[0] + nf[1] * nf[1] + nf[2] * nf[2]);
+    const double inv = 1.0 / nlen;
+    const double nu[3] = {nf[0] * inv, nf[1] * inv, nf[2] * inv};
+    double* r = rec + (long long)FACE_REC * f;
+    r[0] = nu[0];
+    r[1] = nu[1];
+    r[2] = nu[2];
+    r[3] = 0.5 * nlen;
+    for (int v = 0; v < 3; v++) {
+        const double* nxt = P[(v + 1) % 3];
+        const double* prv = P[(v + 2) % 3];
+        const double e3[3] = {prv[0] - nxt[0], prv[1] - nxt[1], prv[2] - nxt[2]};
+        r[4 + 3 * v + 0] = nu[1] * e3[2] - nu[2] * e3[1];
+        r[4 + 3 * v + 1] = nu[2] * e3[0] - nu[0] * e3[2];
+        r[4 + 3 * v + 2] = nu[0] * e3[1] - nu[1] * e3[0];
+    }
+}
+
+// 3D mesh, pass 2: one thread per node gathers its faces from a CSR list of
+// (face, corner) entries sorted by face (no atomics, fixed summation order).
+__global__ void k_node_forces(const double* __restrict__ q, int N, const double* __restrict__ rec,
                               const int* __restrict__ csr_ptr, const int* __restrict__ csr_ent,
                               ForceParams fp, double* __restrict__ phi, double* __restrict__ nrm,
                               double* __restrict__ chi, int* err)
@@ -96,28 +133,12 @@ __global__ void k_forces_mesh(const double* __restrict__ q, int N, const int* __
     for (int e = csr_ptr[j]; e < csr_ptr[j + 1]; e++) {
         const int ent = csr_ent[e];
         const int f = ent / 3, v = ent - 3 * (ent / 3);
-        double P[3][3];
-        for (int c = 0; c < 3; c++) {
-            const int node = tri[3 * f + c];
-            for (int k = 0; k < 3; k++) P[c][k] = q[3 * node + k];
-        }
-        const double ab[3] = {P[1][0] - P[0][0], P[1][1] - P[0][1], P[1][2] - P[0][2]};
-        const double ac[3] = {P[2][0] - P[0][0], P[2][1] - P[0][1], P[2][2] - P[0][2]};
-        const double nf[3] = {ab[1] * ac[2] - ab[2] * ac[1], ab[2] * ac[0] - ab[0] * ac[2],
-                              ab[0] * ac[1] - ab[1] * ac[0]};
-        const double nlen = sqrt(nf[0] * nf[0] + nf[1] * nf[1] + nf[2] * nf[2]);
-        const double nu[3] = {nf[0] / nlen, nf[1] / nlen, nf[2] / nlen};
-        // d(area_f)/d(corner v) = 1/2 nu x (prev - next)
-        const double* nxt = P[(v + 1) % 3];
-        const double* prv = P[(v + 2) % 3];
-        const double e3[3] = {prv[0] - nxt[0], prv[1] - nxt[1], prv[2] - nxt[2]};
-        const double g[3] = {nu[1] * e3[2] - nu[2] * e3[1], nu[2] * e3[0] - nu[0] * e3[2],
-                             nu[0] * e3[1] - nu[1] * e3[0]};
+        const double* r = rec + (long long)FACE_REC * f;
         for (int k = 0; k < 3; k++) {
-            fs[k] -= fp.sigma * 0.5 * g[k];
-            ns[k] += nu[k];
+            fs[k] -= fp.sigma * 0.5 * r[4 + 3 * v + k];
+            ns[k] += r[k];
         }
-        area += 0.5 * nlen;
+        area += r[3];
     }
     const double nl = sqrt(ns[0] * ns[0] + ns[1] * ns[1] + ns[2] * ns[2]);
     const double nh[3] = {ns[0] / nl, ns[1] / nl, ns[2] / nl};
@@ -134,87 +155,121 @@ __global__ void k_forces_mesh(const double* __restrict__ q, int N, const int* __
     if (chi) chi[j] = area;
 }
 
-void launch_forces(int dim, const double* q, int N, const int* tri, const int* csr_ptr,
-                   const int* csr_ent, const ForceParams& fp, double* phi, double* normal,
-                   double* chi, int* err, cudaStream_t s)
+void launch_forces(int dim, const double* q, int N, int M, const int* tri, const int* csr_ptr,
+                   const int* csr_ent, double* face_rec, const ForceParams& fp, double* phi,
+                   double* normal, double* chi, int* err, cudaStream_t s)
 {
-    const int b = 128, g = (N + b - 1) / b;
-    if (dim == 2)
+    if (dim == 2) {
+        const int b = 128, g = (N + b - 1) / b;
         k_forces_ring<<<g, b, 0, s>>>(q, N, fp, phi, normal, chi, err);
-    else
-        k_forces_mesh<<<g, b, 0, s>>>(q, N, tri, csr_ptr, csr_ent, fp, phi, normal, chi, err);
+    } else {
+        const int b = 64;
+        k_face_geometry<<<(M + b - 1) / b, b, 0, s>>>(q, tri, M, face_rec);
+        k_node_forces<<<(N + b - 1) / b, b, 0, s>>>(q, N, face_rec, csr_ptr, csr_ent, fp, phi,
+                                                    normal, chi, err);
+    }
 }
 
 // ------------------------------------------------------------------ stencil
-// Cell index and weight of stencil point s (0..4^dim-1) of a node; returns
-// false if the point lies on a solid layer / outside along the wall axis.
-template <int D>
-__device__ __forceinline__ bool stencil_point(const GridParams& g, const double* qj, int s,
-                                              long long& cell, double& wgt, int& xi_out,
-                                              long long& row_out)
+// Peskin's 4-point kernel in the weight precision R (FP64 for FP64 storage,
+// FP32 otherwise).
+template <typename R>
+__device__ __forceinline__ R delta4r(R r)
 {
-    const int off[3] = {s & 3, (s >> 2) & 3, s >> 4};
-    const int ext[3] = {g.nx, g.ny, g.nz};
-    int idx[3] = {0, 0, 0};
-    double w = 1.0;
-    bool ok = true;
-#pragma unroll
-    for (int k = 0; k < D; k++) {
-        // a diverged node (non-finite or absurdly far away) touches nothing
-        if (!(fabs(qj[k]) < 1.0e9)) {
-            cell = 0;
-            row_out = 0;
-            xi_out = 0;
-            wgt = 0.0;
-            return false;
-        }
-        const int ik = (int)floor(qj[k]) - 1 + off[k];
-        w *= delta4(qj[k] - (double)ik);
-        if (k == D - 1 && g.walls) {
-            if (ik <= 0 || ik >= ext[k] - 1) ok = false;
-            idx[k] = ik;
-        } else {
-            int r = ik % ext[k];
-            idx[k] = r < 0 ? r + ext[k] : r;
+    const R a = fabs(r);
+    if (a <= R(1)) return (R(3) - R(2) * a + sqrt(R(1) + R(4) * a - R(4) * a * a)) * R(0.125);
+    if (a <= R(2)) return (R(5) - R(2) * a - sqrt(R(-7) + R(12) * a - R(4) * a * a)) * R(0.125);
+    return R(0);
+}
+
+// One warp per node.  Lanes 0 .. 4*D-1 evaluate the 1D weights of the node
+// (axis = lane / 4, offset = lane % 4) once, with the lattice index of that
+// stencil line (wrapped on periodic axes, -1 on a solid layer or outside the
+// lattice along the wall axis); every lane then forms the tensor-product
+// weights of its stencil points from warp shuffles.
+template <int D, typename R>
+__device__ __forceinline__ void node_weights(const GridParams& g, const double* __restrict__ q,
+                                             int node, int lane, R& wk, int& ik)
+{
+    wk = R(0);
+    ik = -1;
+    if (lane < 4 * D) {
+        const int k = lane >> 2;
+        const double qk = q[D * node + k];
+        const int ext = k == 0 ? g.nx : (k == 1 ? g.ny : g.nz);
+        if (fabs(qk) < 1.0e9) {   // a diverged node touches nothing
+            const int i = (int)floor(qk) - 1 + (lane & 3);
+            wk = delta4r<R>((R)(qk - (double)i));
+            if (k == D - 1 && g.walls) {
+                ik = (i <= 0 || i >= ext - 1) ? -1 : i;
+            } else {
+                const int r = i % ext;
+                ik = r < 0 ? r + ext : r;
+            }
         }
     }
-    wgt = w;
-    row_out = (long long)idx[2] * g.ny + idx[1];
-    cell = row_out * g.nx + idx[0];
-    xi_out = idx[0];
-    return ok;
+}
+
+// Weight and cell of stencil point s; all lanes must call it (shuffles).
+template <int D, typename R>
+__device__ __forceinline__ bool point_of(const GridParams& g, R wk, int ik, int s, R& w,
+                                         long long& row, int& ix)
+{
+    const int o0 = s & 3, o1 = (s >> 2) & 3, o2 = (s >> 4) & 3;
+    const R w0 = __shfl_sync(0xffffffffu, wk, o0);
+    const int i0 = __shfl_sync(0xffffffffu, ik, o0);
+    const R w1 = __shfl_sync(0xffffffffu, wk, 4 + o1);
+    const int i1 = __shfl_sync(0xffffffffu, ik, 4 + o1);
+    R w2 = R(1);
+    int i2 = 0;
+    if (D == 3) {
+        w2 = __shfl_sync(0xffffffffu, wk, 8 + o2);
+        i2 = __shfl_sync(0xffffffffu, ik, 8 + o2);
+    }
+    w = w0 * w1 * w2;
+    row = (long long)i2 * g.ny + i1;
+    ix = i0;
+    return i0 >= 0 && i1 >= 0 && i2 >= 0;
 }
 
 // ------------------------------------------------------------------ A2 + A3 spread
-// One thread per (node, stencil point): weighted scatter-add of phi_j into the
-// force density and marking of the 32-cell row segment as part of the band.
+// One warp per node: weighted scatter-add of phi_j into the force density
+// (fire-and-forget atomics) and marking of the 32-cell row segments touched.
 template <int D, typename R>
 __global__ void k_spread(const double* __restrict__ q, const double* __restrict__ phi, int N,
                          R* __restrict__ F, uint8_t* __restrict__ flags, GridParams g)
 {
     constexpr int S = (D == 2) ? 16 : 64;
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const int j = (int)(t / S);
-    const int s = (int)(t - (long long)j * S);
-    if (j >= N) return;
-    double qj[3] = {0, 0, 0};
-    for (int k = 0; k < D; k++) qj[k] = q[D * j + k];
-    long long cell, row;
-    double w;
-    int xi;
-    if (!stencil_point<D>(g, qj, s, cell, w, xi, row)) return;
-    if (w == 0.0) return;
-    for (int k = 0; k < D; k++) atomicAdd(&F[k * g.ncell + cell], (R)(phi[D * j + k] * w));
-    flags[row * g.nseg_x + (xi >> 5)] = 1;
+    constexpr int PPL = (S + 31) / 32;
+    const int node = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (node >= N) return;  // uniform per warp
+    R wk;
+    int ik;
+    node_weights<D, R>(g, q, node, lane, wk, ik);
+    R ph[3];
+    for (int k = 0; k < D; k++) ph[k] = (R)phi[D * node + k];
+#pragma unroll
+    for (int p = 0; p < PPL; p++) {
+        const int s = lane + 32 * p;
+        R w;
+        long long row;
+        int ix;
+        const bool ok = point_of<D, R>(g, wk, ik, s < S ? s : 0, w, row, ix);
+        if (s < S && ok && w != R(0)) {
+            const long long cell = row * g.nx + ix;
+            for (int k = 0; k < D; k++) atomicAdd(&F[k * g.ncell + cell], ph[k] * w);
+            flags[row * g.nseg_x + (ix >> 5)] = 1;
+        }
+    }
 }
 
 void launch_spread(int storage, int dim, const double* q, const double* phi, int N, void* F,
                    uint8_t* flags, const GridParams& g, cudaStream_t s)
 {
-    const int per = (dim == 2) ? 16 : 64;
-    const long long n = (long long)N * per;
-    const int b = 256;
-    const int grid = (int)((n + b - 1) / b);
+    const int b = 128;
+    const long long threads = (long long)N * 32;
+    const int grid = (int)((threads + b - 1) / b);
     if (grid == 0) return;
     if (storage == ST_FP64) {
         if (dim == 2) k_spread<2, double><<<grid, b, 0, s>>>(q, phi, N, (double*)F, flags, g);
@@ -232,26 +287,32 @@ __global__ void k_interp(double* __restrict__ q, const R* __restrict__ mom, int 
                          double* __restrict__ qdot, int advect, GridParams g)
 {
     constexpr int S = (D == 2) ? 16 : 64;
-    const int warp = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    constexpr int PPL = (S + 31) / 32;
+    const int node = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
-    if (warp >= N) return;  // uniform per warp
-    double qj[3] = {0, 0, 0};
-    for (int k = 0; k < D; k++) qj[k] = q[D * warp + k];
-    double acc[3] = {0, 0, 0};
-    for (int s = lane; s < S; s += 32) {
-        long long cell, row;
-        double w;
-        int xi;
-        if (!stencil_point<D>(g, qj, s, cell, w, xi, row)) continue;
-        for (int k = 0; k < D; k++) acc[k] += w * (double)mom[(k + 1) * g.ncell + cell];
+    if (node >= N) return;  // uniform per warp
+    R wk;
+    int ik;
+    node_weights<D, R>(g, q, node, lane, wk, ik);
+    R acc[3] = {R(0), R(0), R(0)};
+#pragma unroll
+    for (int p = 0; p < PPL; p++) {
+        const int s = lane + 32 * p;
+        R w;
+        long long row;
+        int ix;
+        const bool ok = point_of<D, R>(g, wk, ik, s < S ? s : 0, w, row, ix);
+        if (s < S && ok) {
+            const long long cell = row * g.nx + ix;
+            for (int k = 0; k < D; k++) acc[k] += w * mom[(k + 1) * g.ncell + cell];
+        }
     }
     for (int k = 0; k < D; k++)
         for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
-    if (lane == 0) {
-        for (int k = 0; k < D; k++) {
-            if (qdot) qdot[D * warp + k] = acc[k];
-            if (advect) q[D * warp + k] = qj[k] + acc[k];
-        }
+    if (lane < D) {
+        const R a = lane == 0 ? acc[0] : (lane == 1 ? acc[1] : acc[D == 3 ? 2 : 1]);
+        if (qdot) qdot[D * node + lane] = (double)a;
+        if (advect) q[D * node + lane] += (double)a;
     }
 }
 

@@ -32,6 +32,7 @@ template <> struct StorageT<ST_FP64> {
     using R = double;
     __device__ __forceinline__ static R load(const S* p, long long i, float) { return p[i]; }
     __device__ __forceinline__ static void store(S* p, long long i, R v, float) { p[i] = v; }
+    __device__ __forceinline__ static void store_cs(S* p, long long i, R v, float) { __stcs(p + i, v); }
 };
 
 template <> struct StorageT<ST_FP32> {
@@ -39,6 +40,7 @@ template <> struct StorageT<ST_FP32> {
     using R = float;
     __device__ __forceinline__ static R load(const S* p, long long i, float) { return p[i]; }
     __device__ __forceinline__ static void store(S* p, long long i, R v, float) { p[i] = v; }
+    __device__ __forceinline__ static void store_cs(S* p, long long i, R v, float) { __stcs(p + i, v); }
 };
 
 template <> struct StorageT<ST_FP16> {
@@ -50,12 +52,13 @@ template <> struct StorageT<ST_FP16> {
     __device__ __forceinline__ static void store(S* p, long long i, R v, float scale) {
         p[i] = __float2half_rn(v * scale);
     }
+    __device__ __forceinline__ static void store_cs(S* p, long long i, R v, float scale) {
+        __stcs(reinterpret_cast<unsigned short*>(p) + i, __half_as_ushort(__float2half_rn(v * scale)));
+    }
 };
 
-constexpr int SC_BLOCK = 128;
-
-template <int Q, int ST, bool WRITE_ALL>
-__global__ void __launch_bounds__(SC_BLOCK)
+template <int Q, int ST, bool WRITE_ALL, int BLOCK, bool CS>
+__global__ void __launch_bounds__(BLOCK)
 k_stream_collide(const typename StorageT<ST>::S* __restrict__ fin,
                  typename StorageT<ST>::S* __restrict__ fout,
                  typename StorageT<ST>::R* __restrict__ mom,
@@ -175,7 +178,10 @@ k_stream_collide(const typename StorageT<ST>::S* __restrict__ fin,
         const R geq = w * (drho + rho * (R(3) * cu + R(4.5) * cu * cu - usq15));
         const R src = pref * w * (R(3) * (cF - uF) + R(9) * cu * cF);
         const R gn = g[i] + omega * (geq - g[i]) + src;
-        T::store(fout, (long long)i * nc + cell, gn, p.scale);
+        if (CS)
+            T::store_cs(fout, (long long)i * nc + cell, gn, p.scale);
+        else
+            T::store(fout, (long long)i * nc + cell, gn, p.scale);
     }
 
     if (WRITE_ALL || band) {
@@ -188,14 +194,14 @@ k_stream_collide(const typename StorageT<ST>::S* __restrict__ fin,
     if (lane == 0 && band) flags[seg] = 0;
 }
 
-template <int Q, int ST>
-static void launch_sc_t(bool write_all, const void* fin, void* fout, void* mom, void* F,
+template <int Q, int ST, int BLOCK, bool CS>
+static void launch_sc_b(bool write_all, const void* fin, void* fout, void* mom, void* F,
                         uint8_t* flags, const StreamParams& p, cudaStream_t s)
 {
     using T = StorageT<ST>;
     const int woff = p.g.walls ? 1 : 0;
-    dim3 block(SC_BLOCK);
-    dim3 grid((p.g.nx + SC_BLOCK - 1) / SC_BLOCK, 1, 1);
+    dim3 block(BLOCK);
+    dim3 grid((p.g.nx + BLOCK - 1) / BLOCK, 1, 1);
     if (Q == 9) {
         grid.y = p.g.ny - 2 * woff;
     } else {
@@ -207,23 +213,44 @@ static void launch_sc_t(bool write_all, const void* fin, void* fout, void* mom, 
     auto* m = (typename T::R*)mom;
     auto* f = (typename T::R*)F;
     if (write_all)
-        k_stream_collide<Q, ST, true><<<grid, block, 0, s>>>(a, b, m, f, flags, p);
+        k_stream_collide<Q, ST, true, BLOCK, CS><<<grid, block, 0, s>>>(a, b, m, f, flags, p);
     else
-        k_stream_collide<Q, ST, false><<<grid, block, 0, s>>>(a, b, m, f, flags, p);
+        k_stream_collide<Q, ST, false, BLOCK, CS><<<grid, block, 0, s>>>(a, b, m, f, flags, p);
+}
+
+template <int Q, int ST>
+static void launch_sc_t(bool write_all, const void* fin, void* fout, void* mom, void* F,
+                        uint8_t* flags, const StreamParams& p, const Tuning& tu, cudaStream_t s)
+{
+    const bool cs = tu.streaming_stores != 0;
+    switch (tu.block_x) {
+        case 64:
+            if (cs) launch_sc_b<Q, ST, 64, true>(write_all, fin, fout, mom, F, flags, p, s);
+            else launch_sc_b<Q, ST, 64, false>(write_all, fin, fout, mom, F, flags, p, s);
+            break;
+        case 256:
+            if (cs) launch_sc_b<Q, ST, 256, true>(write_all, fin, fout, mom, F, flags, p, s);
+            else launch_sc_b<Q, ST, 256, false>(write_all, fin, fout, mom, F, flags, p, s);
+            break;
+        default:
+            if (cs) launch_sc_b<Q, ST, 128, true>(write_all, fin, fout, mom, F, flags, p, s);
+            else launch_sc_b<Q, ST, 128, false>(write_all, fin, fout, mom, F, flags, p, s);
+            break;
+    }
 }
 
 void launch_stream_collide(int Q, int storage, bool write_all, const void* fin, void* fout,
                            void* moments, void* F, uint8_t* flags, const StreamParams& p,
-                           cudaStream_t s)
+                           const Tuning& tu, cudaStream_t s)
 {
     if (Q == 9) {
-        if (storage == ST_FP64) launch_sc_t<9, ST_FP64>(write_all, fin, fout, moments, F, flags, p, s);
-        else if (storage == ST_FP32) launch_sc_t<9, ST_FP32>(write_all, fin, fout, moments, F, flags, p, s);
-        else launch_sc_t<9, ST_FP16>(write_all, fin, fout, moments, F, flags, p, s);
+        if (storage == ST_FP64) launch_sc_t<9, ST_FP64>(write_all, fin, fout, moments, F, flags, p, tu, s);
+        else if (storage == ST_FP32) launch_sc_t<9, ST_FP32>(write_all, fin, fout, moments, F, flags, p, tu, s);
+        else launch_sc_t<9, ST_FP16>(write_all, fin, fout, moments, F, flags, p, tu, s);
     } else {
-        if (storage == ST_FP64) launch_sc_t<19, ST_FP64>(write_all, fin, fout, moments, F, flags, p, s);
-        else if (storage == ST_FP32) launch_sc_t<19, ST_FP32>(write_all, fin, fout, moments, F, flags, p, s);
-        else launch_sc_t<19, ST_FP16>(write_all, fin, fout, moments, F, flags, p, s);
+        if (storage == ST_FP64) launch_sc_t<19, ST_FP64>(write_all, fin, fout, moments, F, flags, p, tu, s);
+        else if (storage == ST_FP32) launch_sc_t<19, ST_FP32>(write_all, fin, fout, moments, F, flags, p, tu, s);
+        else launch_sc_t<19, ST_FP16>(write_all, fin, fout, moments, F, flags, p, tu, s);
     }
 }
 

@@ -105,6 +105,7 @@ def load():
         "iblb_force_field": (st, [vp, dp]),
         "iblb_interpolate": (st, [vp, dp, dp]),
         "iblb_step_profiled": (st, [vp, ip, dp]),
+        "iblb_set_tuning": (st, [vp, ip, ip]),
         "iblb_stream_bytes_per_step": (ctypes.c_double, [vp]),
         "iblb_fluid_cells": (ctypes.c_longlong, [vp]),
         "iblb_kernel_launch_count": (ctypes.c_longlong, []),
@@ -230,6 +231,10 @@ def iblb_step_profiled(h, n_steps: int) -> np.ndarray:
     return out
 
 
+def iblb_set_tuning(h, block_x: int, streaming_stores: int = 0):
+    _check(h, load().iblb_set_tuning(h, int(block_x), int(streaming_stores)))
+
+
 def iblb_stream_bytes_per_step(h) -> float:
     return load().iblb_stream_bytes_per_step(h)
 
@@ -322,6 +327,9 @@ class Simulation:
         qd = np.zeros((self.N, self.dim))
         iblb_interpolate(self.h, u, qd)
         return qd
+
+    def set_tuning(self, block_x, streaming_stores=0):
+        iblb_set_tuning(self.h, block_x, streaming_stores)
 
     def step_profiled(self, n):
         return iblb_step_profiled(self.h, n)
