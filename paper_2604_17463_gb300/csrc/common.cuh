@@ -91,9 +91,25 @@ struct ForceParams {
 
 // Launch shape of the stream-collide kernel (chosen by the autotuner).
 struct Tuning {
-    int block_x = 128;          // threads per block along x: 64, 128 or 256
-    int streaming_stores = 0;   // 1: evict-first stores of the new populations
+    int variant = 1;            // 0: plain kernel; 1: pipelined kernel where the shape allows
+    int block_x = 128;          // plain kernel: threads per block along x (64, 128, 256)
+    int streaming_stores = 0;   // plain kernel: evict-first stores of the new populations
 };
+
+// Shape of the pipelined stream-collide launch (see lbm_pipe.cu).
+struct PipeShape {
+    int W;                 // tile width (cells), multiple of 256, divides nx
+    int nseg;              // tiles per row
+    long long ntiles;      // tiles in the lattice
+    int plane_bytes;       // shared-memory bytes of one staged direction
+    int stage_bytes;       // Q * plane_bytes
+    long long tx_bytes;    // bytes copied per stage
+    int stages;            // pipeline depth per CTA
+    int ctas_per_sm;
+    int smem_bytes;        // dynamic shared memory per CTA
+    int grid;              // persistent CTAs
+};
+constexpr int PIPE_SMEM_PER_CTA = 227 * 1024 / 2;
 
 // ------------------------------------------------------------------ launchers
 // Storage ids match iblb_storage.
@@ -106,6 +122,13 @@ enum Storage : int { ST_FP64 = 0, ST_FP32 = 1, ST_FP16 = 2 };
 void launch_stream_collide(int Q, int storage, bool write_all, const void* fin, void* fout,
                            void* moments, void* F, uint8_t* flags, const StreamParams& p,
                            const Tuning& tu, cudaStream_t s);
+
+// Pipelined variant (lbm_pipe.cu): usable when pipe_shape() returns true.
+bool pipe_shape(int Q, int storage, const GridParams& g, int sm_count, PipeShape& ps);
+cudaError_t prepare_stream_collide_pipe();
+cudaError_t launch_stream_collide_pipe(int Q, int storage, bool write_all, const void* fin,
+                                       void* fout, void* moments, void* F, uint8_t* flags,
+                                       const StreamParams& p, const PipeShape& ps, cudaStream_t s);
 
 // Host FP64 <-> device storage conversion of populations ([Q][ncell], f_i).
 void launch_pack_populations(int Q, int storage, const double* f, void* dst, long long ncell,

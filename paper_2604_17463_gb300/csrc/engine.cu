@@ -33,6 +33,8 @@ struct iblb_sim {
     GridParams g{};
     StreamParams sp{};
     Tuning tune{};
+    PipeShape pipe{};
+    bool pipe_ok = false;
     ForceParams fp{};
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;  // private stream used only for graph capture
@@ -93,6 +95,16 @@ void clear_graphs(iblb_sim* h)
 int force_kernels(const iblb_sim* h) { return h->dim == 3 ? 2 : 1; }
 int kernels_per_step(const iblb_sim* h) { return h->N > 0 ? 3 + force_kernels(h) : 1; }
 
+void launch_sc(iblb_sim* h, cudaStream_t s, bool write_all)
+{
+    if (h->tune.variant == 1 && h->pipe_ok)
+        launch_stream_collide_pipe(h->Q, h->storage, write_all, h->f[h->cur], h->f[h->cur ^ 1],
+                                   h->mom, h->F, h->flags, h->sp, h->pipe, s);
+    else
+        launch_stream_collide(h->Q, h->storage, write_all, h->f[h->cur], h->f[h->cur ^ 1], h->mom,
+                              h->F, h->flags, h->sp, h->tune, s);
+}
+
 // Enqueue one time step on stream s (buffers by the current parity).
 void enqueue_step(iblb_sim* h, cudaStream_t s, bool write_all)
 {
@@ -101,8 +113,7 @@ void enqueue_step(iblb_sim* h, cudaStream_t s, bool write_all)
                       nullptr, h->err, s);
         launch_spread(h->storage, h->dim, h->q, h->phi, h->N, h->F, h->flags, h->g, s);
     }
-    launch_stream_collide(h->Q, h->storage, write_all, h->f[h->cur], h->f[h->cur ^ 1], h->mom,
-                          h->F, h->flags, h->sp, h->tune, s);
+    launch_sc(h, s, write_all);
     if (h->N > 0)
         launch_interp(h->storage, h->dim, h->q, h->mom, h->N, nullptr, true, h->g, s);
     h->cur ^= 1;
@@ -258,6 +269,12 @@ iblb_status iblb_create(const iblb_config* cfg, void* cuda_stream, iblb_handle* 
     launch_init_moments(h->storage, g, h->mom, h->stream);
     g_launches++;
     sp.err = h->err;
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return bail(e, "device");
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return bail(e, "sm count");
+    if ((e = prepare_stream_collide_pipe()) != cudaSuccess) return bail(e, "pipe attributes");
+    h->pipe_ok = pipe_shape(h->Q, h->storage, g, sms, h->pipe);
     if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "init");
     *out = h;
     return IBLB_OK;
@@ -562,8 +579,7 @@ iblb_status iblb_step_profiled(iblb_handle h, int n_steps, double* kernel_ms)
         cudaEventRecord(ev[1], h->stream);
         if (ib) launch_spread(h->storage, h->dim, h->q, h->phi, h->N, h->F, h->flags, h->g, h->stream);
         cudaEventRecord(ev[2], h->stream);
-        launch_stream_collide(h->Q, h->storage, last, h->f[h->cur], h->f[h->cur ^ 1], h->mom,
-                              h->F, h->flags, h->sp, h->tune, h->stream);
+        launch_sc(h, h->stream, last);
         cudaEventRecord(ev[3], h->stream);
         if (ib) launch_interp(h->storage, h->dim, h->q, h->mom, h->N, nullptr, true, h->g, h->stream);
         cudaEventRecord(ev[4], h->stream);
@@ -581,16 +597,24 @@ iblb_status iblb_step_profiled(iblb_handle h, int n_steps, double* kernel_ms)
     return check_device_flag(h);
 }
 
-iblb_status iblb_set_tuning(iblb_handle h, int block_x, int streaming_stores)
+iblb_status iblb_set_tuning(iblb_handle h, int variant, int block_x, int streaming_stores)
 {
     if (!h) return IBLB_EINVAL;
+    if (variant != 0 && variant != 1) return fail(h, IBLB_EINVAL, "variant must be 0 or 1");
     if (block_x != 64 && block_x != 128 && block_x != 256)
         return fail(h, IBLB_EINVAL, "block_x must be 64, 128 or 256");
     CK(h, cudaStreamSynchronize(h->stream));
     clear_graphs(h);
+    h->tune.variant = variant;
     h->tune.block_x = block_x;
     h->tune.streaming_stores = streaming_stores ? 1 : 0;
     return IBLB_OK;
+}
+
+int iblb_stream_collide_variant(iblb_handle h)
+{
+    if (!h) return -1;
+    return (h->tune.variant == 1 && h->pipe_ok) ? 1 : 0;
 }
 
 double iblb_stream_bytes_per_step(iblb_handle h)

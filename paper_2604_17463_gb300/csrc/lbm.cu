@@ -21,41 +21,9 @@
 // spread kernel; elsewhere F is the uniform body force.  The moments are
 // written only in flagged segments (for the interpolation) or everywhere on
 // the last step of a call.
-#include "common.cuh"
+#include "lbm_core.cuh"
 
 namespace iblb {
-
-template <int ST> struct StorageT;
-
-template <> struct StorageT<ST_FP64> {
-    using S = double;
-    using R = double;
-    __device__ __forceinline__ static R load(const S* p, long long i, float) { return p[i]; }
-    __device__ __forceinline__ static void store(S* p, long long i, R v, float) { p[i] = v; }
-    __device__ __forceinline__ static void store_cs(S* p, long long i, R v, float) { __stcs(p + i, v); }
-};
-
-template <> struct StorageT<ST_FP32> {
-    using S = float;
-    using R = float;
-    __device__ __forceinline__ static R load(const S* p, long long i, float) { return p[i]; }
-    __device__ __forceinline__ static void store(S* p, long long i, R v, float) { p[i] = v; }
-    __device__ __forceinline__ static void store_cs(S* p, long long i, R v, float) { __stcs(p + i, v); }
-};
-
-template <> struct StorageT<ST_FP16> {
-    using S = __half;
-    using R = float;
-    __device__ __forceinline__ static R load(const S* p, long long i, float inv_scale) {
-        return __half2float(p[i]) * inv_scale;
-    }
-    __device__ __forceinline__ static void store(S* p, long long i, R v, float scale) {
-        p[i] = __float2half_rn(v * scale);
-    }
-    __device__ __forceinline__ static void store_cs(S* p, long long i, R v, float scale) {
-        __stcs(reinterpret_cast<unsigned short*>(p) + i, __half_as_ushort(__float2half_rn(v * scale)));
-    }
-};
 
 template <int Q, int ST, bool WRITE_ALL, int BLOCK, bool CS>
 __global__ void __launch_bounds__(BLOCK)
@@ -134,20 +102,6 @@ k_stream_collide(const typename StorageT<ST>::S* __restrict__ fin,
             g[i] = T::load(fin, (long long)i * nc + src, p.inv_scale);
     }
 
-    // moments of the deviations
-    R drho = 0, jx = 0, jy = 0, jz = 0;
-#pragma unroll
-    for (int i = 0; i < Q; i++) {
-        drho += g[i];
-        if (L::cx(i) > 0) jx += g[i];
-        if (L::cx(i) < 0) jx -= g[i];
-        if (L::cy(i) > 0) jy += g[i];
-        if (L::cy(i) < 0) jy -= g[i];
-        if (D == 3) {
-            if (L::cz(i) > 0) jz += g[i];
-            if (L::cz(i) < 0) jz -= g[i];
-        }
-    }
     R Fx = (R)p.body[0], Fy = (R)p.body[1], Fz = (R)p.body[2];
     if (band) {
         Fx += F[cell];
@@ -159,38 +113,23 @@ k_stream_collide(const typename StorageT<ST>::S* __restrict__ fin,
             F[2 * nc + cell] = 0;
         }
     }
-    const R rho = R(1) + drho;
-    const R inv_rho = R(1) / rho;
-    const R ux = (jx + R(0.5) * Fx) * inv_rho;
-    const R uy = (jy + R(0.5) * Fy) * inv_rho;
-    const R uz = (D == 3) ? (jz + R(0.5) * Fz) * inv_rho : R(0);
-    const R usq15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
-    const R omega = (R)p.omega;
-    const R pref = R(1) - R(0.5) * omega;
-    const R uF = ux * Fx + uy * Fy + uz * Fz;
-
+    const CellMoments<Q, R> mo = cell_moments<Q, R>(g, Fx, Fy, Fz);
+    cell_collide<Q, R>(g, mo, (R)p.omega, Fx, Fy, Fz);
 #pragma unroll
     for (int i = 0; i < Q; i++) {
-        const R cx = (R)L::cx(i), cy = (R)L::cy(i), cz = (R)L::cz(i);
-        const R w = (R)L::w(i);
-        const R cu = cx * ux + cy * uy + (D == 3 ? cz * uz : R(0));
-        const R cF = cx * Fx + cy * Fy + (D == 3 ? cz * Fz : R(0));
-        const R geq = w * (drho + rho * (R(3) * cu + R(4.5) * cu * cu - usq15));
-        const R src = pref * w * (R(3) * (cF - uF) + R(9) * cu * cF);
-        const R gn = g[i] + omega * (geq - g[i]) + src;
         if (CS)
-            T::store_cs(fout, (long long)i * nc + cell, gn, p.scale);
+            T::store_cs(fout, (long long)i * nc + cell, g[i], p.scale);
         else
-            T::store(fout, (long long)i * nc + cell, gn, p.scale);
+            T::store(fout, (long long)i * nc + cell, g[i], p.scale);
     }
 
     if (WRITE_ALL || band) {
-        mom[cell] = drho;
-        mom[nc + cell] = ux;
-        mom[2 * nc + cell] = uy;
-        if (D == 3) mom[3 * nc + cell] = uz;
+        mom[cell] = mo.drho;
+        mom[nc + cell] = mo.ux;
+        mom[2 * nc + cell] = mo.uy;
+        if (D == 3) mom[3 * nc + cell] = mo.uz;
     }
-    if (!isfinite(drho)) atomicOr(p.err, ERR_NONFINITE);
+    if (!isfinite(mo.drho)) atomicOr(p.err, ERR_NONFINITE);
     if (lane == 0 && band) flags[seg] = 0;
 }
 

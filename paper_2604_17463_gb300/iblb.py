@@ -105,7 +105,8 @@ def load():
         "iblb_force_field": (st, [vp, dp]),
         "iblb_interpolate": (st, [vp, dp, dp]),
         "iblb_step_profiled": (st, [vp, ip, dp]),
-        "iblb_set_tuning": (st, [vp, ip, ip]),
+        "iblb_set_tuning": (st, [vp, ip, ip, ip]),
+        "iblb_stream_collide_variant": (ctypes.c_int, [vp]),
         "iblb_stream_bytes_per_step": (ctypes.c_double, [vp]),
         "iblb_fluid_cells": (ctypes.c_longlong, [vp]),
         "iblb_kernel_launch_count": (ctypes.c_longlong, []),
@@ -231,8 +232,12 @@ def iblb_step_profiled(h, n_steps: int) -> np.ndarray:
     return out
 
 
-def iblb_set_tuning(h, block_x: int, streaming_stores: int = 0):
-    _check(h, load().iblb_set_tuning(h, int(block_x), int(streaming_stores)))
+def iblb_set_tuning(h, variant: int, block_x: int = 128, streaming_stores: int = 0):
+    _check(h, load().iblb_set_tuning(h, int(variant), int(block_x), int(streaming_stores)))
+
+
+def iblb_stream_collide_variant(h) -> int:
+    return load().iblb_stream_collide_variant(h)
 
 
 def iblb_stream_bytes_per_step(h) -> float:
@@ -328,8 +333,12 @@ class Simulation:
         iblb_interpolate(self.h, u, qd)
         return qd
 
-    def set_tuning(self, block_x, streaming_stores=0):
-        iblb_set_tuning(self.h, block_x, streaming_stores)
+    def set_tuning(self, variant, block_x=128, streaming_stores=0):
+        iblb_set_tuning(self.h, variant, block_x, streaming_stores)
+
+    @property
+    def variant(self):
+        return iblb_stream_collide_variant(self.h)
 
     def step_profiled(self, n):
         return iblb_step_profiled(self.h, n)
