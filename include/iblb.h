@@ -160,11 +160,14 @@ iblb_status iblb_step_profiled(iblb_handle h, int n_steps, double* kernel_ms);
 /* Launch shape of the stream-collide kernel.  variant 1 (default) selects the
  * pipelined kernel (persistent CTAs; a producer warp stages the source rows
  * in shared memory with bulk asynchronous copies) where the lattice allows it
- * (nx a multiple of 256); variant 0 the plain one-cell-per-thread kernel with
- * block_x threads per block along x (64, 128 or 256) and evict-first stores
- * when streaming_stores != 0.  Results do not depend on the choice.
+ * (nx a multiple of 32 up to 1024: tiles of rows_per_tile whole rows; else
+ * nx a multiple of 256: row segments), with ctas_per_sm (1 or 2) resident
+ * CTAs per SM; variant 0 the plain one-cell-per-thread kernel with block_x
+ * threads per block along x (64, 128 or 256) and evict-first stores when
+ * streaming_stores != 0.  Results do not depend on the choice.
  * Synchronises. */
-iblb_status iblb_set_tuning(iblb_handle h, int variant, int block_x, int streaming_stores);
+iblb_status iblb_set_tuning(iblb_handle h, int variant, int block_x, int streaming_stores,
+                            int rows_per_tile, int ctas_per_sm);
 
 /* The stream-collide variant in use (0 plain, 1 pipelined). */
 int iblb_stream_collide_variant(iblb_handle h);

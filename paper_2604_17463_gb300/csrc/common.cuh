@@ -94,22 +94,29 @@ struct Tuning {
     int variant = 1;            // 0: plain kernel; 1: pipelined kernel where the shape allows
     int block_x = 128;          // plain kernel: threads per block along x (64, 128, 256)
     int streaming_stores = 0;   // plain kernel: evict-first stores of the new populations
+    int rows_per_tile = 2;      // pipelined kernel, rows mode: rows per tile
+    int ctas_per_sm = 2;        // pipelined kernel: resident CTAs per SM (1 or 2)
 };
 
 // Shape of the pipelined stream-collide launch (see lbm_pipe.cu).
+enum : int { PIPE_ROWS = 0, PIPE_SEGMENTS = 1 };
 struct PipeShape {
-    int W;                 // tile width (cells), multiple of 256, divides nx
-    int nseg;              // tiles per row
+    int mode;              // PIPE_ROWS: R whole rows per tile; PIPE_SEGMENTS: W-cell segments
+    int R;                 // rows per tile (rows mode)
+    int yblocks;           // tiles along y per layer (rows mode)
+    int W;                 // tile width in cells (segment mode: multiple of 256)
+    int nseg;              // tiles per row (segment mode)
     long long ntiles;      // tiles in the lattice
     int plane_bytes;       // shared-memory bytes of one staged direction
     int stage_bytes;       // Q * plane_bytes
-    long long tx_bytes;    // bytes copied per stage
+    long long tx_bytes;    // bytes copied per full stage
     int stages;            // pipeline depth per CTA
     int ctas_per_sm;
     int smem_bytes;        // dynamic shared memory per CTA
     int grid;              // persistent CTAs
 };
-constexpr int PIPE_SMEM_PER_CTA = 227 * 1024 / 2;
+constexpr int PIPE_SMEM_ONE_CTA = 227 * 1024;
+constexpr int PIPE_SMEM_PER_CTA = 227 * 1024 / 2 - 1024;
 
 // ------------------------------------------------------------------ launchers
 // Storage ids match iblb_storage.
@@ -124,7 +131,8 @@ void launch_stream_collide(int Q, int storage, bool write_all, const void* fin, 
                            const Tuning& tu, cudaStream_t s);
 
 // Pipelined variant (lbm_pipe.cu): usable when pipe_shape() returns true.
-bool pipe_shape(int Q, int storage, const GridParams& g, int sm_count, PipeShape& ps);
+bool pipe_shape(int Q, int storage, const GridParams& g, int sm_count, int rows_per_tile,
+                int ctas_per_sm, PipeShape& ps);
 cudaError_t prepare_stream_collide_pipe();
 cudaError_t launch_stream_collide_pipe(int Q, int storage, bool write_all, const void* fin,
                                        void* fout, void* moments, void* F, uint8_t* flags,

@@ -35,6 +35,7 @@ struct iblb_sim {
     Tuning tune{};
     PipeShape pipe{};
     bool pipe_ok = false;
+    int sm_count = 0;
     ForceParams fp{};
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;  // private stream used only for graph capture
@@ -274,7 +275,9 @@ iblb_status iblb_create(const iblb_config* cfg, void* cuda_stream, iblb_handle* 
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
         return bail(e, "sm count");
     if ((e = prepare_stream_collide_pipe()) != cudaSuccess) return bail(e, "pipe attributes");
-    h->pipe_ok = pipe_shape(h->Q, h->storage, g, sms, h->pipe);
+    h->sm_count = sms;
+    h->pipe_ok = pipe_shape(h->Q, h->storage, g, sms, h->tune.rows_per_tile,
+                            h->tune.ctas_per_sm, h->pipe);
     if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "init");
     *out = h;
     return IBLB_OK;
@@ -597,17 +600,24 @@ iblb_status iblb_step_profiled(iblb_handle h, int n_steps, double* kernel_ms)
     return check_device_flag(h);
 }
 
-iblb_status iblb_set_tuning(iblb_handle h, int variant, int block_x, int streaming_stores)
+iblb_status iblb_set_tuning(iblb_handle h, int variant, int block_x, int streaming_stores,
+                            int rows_per_tile, int ctas_per_sm)
 {
     if (!h) return IBLB_EINVAL;
     if (variant != 0 && variant != 1) return fail(h, IBLB_EINVAL, "variant must be 0 or 1");
     if (block_x != 64 && block_x != 128 && block_x != 256)
         return fail(h, IBLB_EINVAL, "block_x must be 64, 128 or 256");
+    if (rows_per_tile < 1 || rows_per_tile > 64) return fail(h, IBLB_EINVAL, "rows_per_tile in 1..64");
+    if (ctas_per_sm != 1 && ctas_per_sm != 2) return fail(h, IBLB_EINVAL, "ctas_per_sm must be 1 or 2");
     CK(h, cudaStreamSynchronize(h->stream));
     clear_graphs(h);
     h->tune.variant = variant;
     h->tune.block_x = block_x;
     h->tune.streaming_stores = streaming_stores ? 1 : 0;
+    h->tune.rows_per_tile = rows_per_tile;
+    h->tune.ctas_per_sm = ctas_per_sm;
+    h->pipe_ok = pipe_shape(h->Q, h->storage, h->g, h->sm_count, rows_per_tile, ctas_per_sm,
+                            h->pipe);
     return IBLB_OK;
 }
 

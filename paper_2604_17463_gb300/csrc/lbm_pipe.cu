@@ -3,12 +3,16 @@
 // Same update as the plain kernel in lbm.cu (pull streaming with halfway
 // bounce-back, moments with the half-force term, BGK + Guo, Eq. 1-6), with
 // the loads decoupled from the arithmetic:
-//   - persistent CTAs (a few per SM) walk the tiles round-robin; a tile is one
-//     x-segment of W cells (W a multiple of 256) of one fluid row;
-//   - a producer warp stages, for each of the Q directions, the source-row
-//     segment of the tile plus a 16-byte halo on each side into shared memory
-//     with bulk asynchronous copies (cp.async.bulk, completion counted in
-//     bytes on an mbarrier), several tiles ahead of the consumers;
+//   - persistent CTAs (a few per SM) walk the tiles round-robin;
+//   - a producer warp stages, for each of the Q directions, the source rows
+//     of a tile into shared memory with bulk asynchronous copies
+//     (cp.async.bulk, completion counted in bytes on an mbarrier), several
+//     tiles ahead of the consumers.  Two tile shapes:
+//       rows mode:    R whole rows (nx <= 1024, nx % 32 == 0); the periodic
+//                     x-shift wraps inside shared memory and consecutive
+//                     source rows of a direction go in one copy;
+//       segment mode: one x-segment of W cells (W a multiple of 256) of one
+//                     row plus a 16-byte halo on each side;
 //   - eight consumer warps read the shifted populations from shared memory,
 //     collide and store the new populations with coalesced stores, then
 //     release the stage on a second mbarrier.
@@ -121,6 +125,63 @@ __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, int* 
 constexpr int PIPE_CONSUMER_WARPS = 8;
 constexpr int PIPE_THREADS = 32 * (1 + PIPE_CONSUMER_WARPS);
 
+// Tile t -> first lattice row (y0, z) and first cell x0, with R_t rows.
+template <int D>
+__device__ __forceinline__ void decode_tile(const PipeShape& ps, const GridParams& g, long long t,
+                                            int& y0, int& z, int& x0, int& rows)
+{
+    const int woff = g.walls ? 1 : 0;
+    if (ps.mode == PIPE_ROWS) {
+        const int ny_f = (D == 2) ? g.ny - 2 * woff : g.ny;   // rows stacked along y
+        const int yb = (int)(t % ps.yblocks);
+        const long long zi = t / ps.yblocks;
+        const int ylo = (D == 2) ? woff : 0;
+        y0 = ylo + yb * ps.R;
+        rows = min(ps.R, ylo + ny_f - y0);
+        z = (D == 2) ? 0 : (int)zi + woff;
+        x0 = 0;
+    } else {
+        const long long row_idx = t / ps.nseg;
+        x0 = (int)(t - row_idx * ps.nseg) * ps.W;
+        rows = 1;
+        if (D == 2) {
+            y0 = (int)row_idx + woff;
+            z = 0;
+        } else {
+            z = (int)(row_idx / g.ny) + woff;
+            y0 = (int)(row_idx % g.ny);
+        }
+    }
+}
+
+// Source of direction i for the destination row (y, z): the plane and row to
+// stage (the opposite direction of the same row under bounce-back).
+template <int D>
+__device__ __forceinline__ void source_row(const GridParams& g, int y, int z, int cy, int cz, int i,
+                                           int op, int& plane, int& sy, int& sz)
+{
+    plane = i;
+    bool bb = false;
+    if (D == 2) {
+        int sa = y - cy;
+        if (g.walls) bb = (sa <= 0 || sa >= g.ny - 1);
+        else sa = (sa + g.ny) % g.ny;
+        sy = sa;
+        sz = 0;
+    } else {
+        sy = (y - cy + g.ny) % g.ny;
+        int sa = z - cz;
+        if (g.walls) bb = (sa <= 0 || sa >= g.nz - 1);
+        else sa = (sa + g.nz) % g.nz;
+        sz = sa;
+    }
+    if (bb) {
+        plane = op;
+        sy = y;
+        sz = z;
+    }
+}
+
 template <int Q, int ST, bool WRITE_ALL>
 __global__ void __launch_bounds__(PIPE_THREADS, 2)
 k_sc_pipe(const typename StorageT<ST>::S* __restrict__ fin,
@@ -145,8 +206,7 @@ k_sc_pipe(const typename StorageT<ST>::S* __restrict__ fin,
     const int nx = p.g.nx, ny = p.g.ny;
     const long long nc = p.g.ncell;
     const int walls = p.g.walls;
-    const int woff = walls ? 1 : 0;
-    const int W = ps.W;
+    const bool rows_mode = ps.mode == PIPE_ROWS;
 
     if (threadIdx.x == 0) {
         abort_flag = 0;
@@ -167,49 +227,45 @@ k_sc_pipe(const typename StorageT<ST>::S* __restrict__ fin,
                 const uint32_t par = (uint32_t)(((k / ps.stages) - 1) & 1);
                 if (!wait_phase(&empty[s], par, p.err, &abort_flag)) break;
             }
-            const long long row_idx = t / ps.nseg;
-            const int x0 = (int)(t - row_idx * ps.nseg) * W;
-            int y, z;
-            if (D == 2) {
-                y = (int)row_idx + woff;
-                z = 0;
-            } else {
-                z = (int)(row_idx / ny) + woff;
-                y = (int)(row_idx % ny);
-            }
+            int y0, z, x0, rows;
+            decode_tile<D>(ps, p.g, t, y0, z, x0, rows);
             unsigned char* stage = smem + (size_t)s * ps.stage_bytes;
-            if (lane == 0) mbar_arrive_expect_tx(&full[s], (uint32_t)ps.tx_bytes);
+            const uint32_t tx = rows_mode ? (uint32_t)(Q * rows * nx * ELT) : (uint32_t)ps.tx_bytes;
+            if (lane == 0) mbar_arrive_expect_tx(&full[s], tx);
             __syncwarp();
             if (lane < Q) {
-                const int cx = tab<Q>().v[lane][0], cy = tab<Q>().v[lane][1];
-                const int cz = tab<Q>().v[lane][2], op = tab<Q>().v[lane][3];
-                (void)cx;
-                int plane = lane, sy = y, sz = z;
-                bool bb = false;
-                if (D == 2) {
-                    int sa = y - cy;
-                    if (walls) bb = (sa <= 0 || sa >= ny - 1);
-                    else sa = (sa + ny) % ny;
-                    sy = sa;
-                } else {
-                    sy = (y - cy + ny) % ny;
-                    int sa = z - cz;
-                    const int nz = p.g.nz;
-                    if (walls) bb = (sa <= 0 || sa >= nz - 1);
-                    else sa = (sa + nz) % nz;
-                    sz = sa;
-                }
-                if (bb) {
-                    plane = op;
-                    sy = y;
-                    sz = z;
-                }
-                const S* row = fin + (long long)plane * nc + ((long long)sz * ny + sy) * nx;
+                const int cy = tab<Q>().v[lane][1], cz = tab<Q>().v[lane][2];
+                const int op = tab<Q>().v[lane][3];
                 unsigned char* dst = stage + (size_t)lane * ps.plane_bytes;
-                bulk_g2s(dst + HALO * ELT, row + x0, (uint32_t)(W * ELT), &full[s]);
-                bulk_g2s(dst, row + (x0 > 0 ? x0 - HALO : nx - HALO), 16u, &full[s]);
-                bulk_g2s(dst + (size_t)(HALO + W) * ELT, row + (x0 + W < nx ? x0 + W : 0), 16u,
-                         &full[s]);
+                if (rows_mode) {
+                    // merge consecutive source rows of this direction into runs
+                    const size_t row_bytes = (size_t)nx * ELT;
+                    int r = 0;
+                    while (r < rows) {
+                        int plane, sy, sz;
+                        source_row<D>(p.g, y0 + r, z, cy, cz, lane, op, plane, sy, sz);
+                        int len = 1;
+                        while (r + len < rows) {
+                            int pl2, sy2, sz2;
+                            source_row<D>(p.g, y0 + r + len, z, cy, cz, lane, op, pl2, sy2, sz2);
+                            if (pl2 != plane || sz2 != sz || sy2 != sy + len) break;
+                            ++len;
+                        }
+                        const S* src = fin + (long long)plane * nc + ((long long)sz * ny + sy) * nx;
+                        bulk_g2s(dst + (size_t)r * row_bytes, src, (uint32_t)(len * row_bytes),
+                                 &full[s]);
+                        r += len;
+                    }
+                } else {
+                    const int W = ps.W;
+                    int plane, sy, sz;
+                    source_row<D>(p.g, y0, z, cy, cz, lane, op, plane, sy, sz);
+                    const S* row = fin + (long long)plane * nc + ((long long)sz * ny + sy) * nx;
+                    bulk_g2s(dst + HALO * ELT, row + x0, (uint32_t)(W * ELT), &full[s]);
+                    bulk_g2s(dst, row + (x0 > 0 ? x0 - HALO : nx - HALO), 16u, &full[s]);
+                    bulk_g2s(dst + (size_t)(HALO + W) * ELT, row + (x0 + W < nx ? x0 + W : 0),
+                             16u, &full[s]);
+                }
             }
             __syncwarp();
         }
@@ -231,33 +287,30 @@ k_sc_pipe(const typename StorageT<ST>::S* __restrict__ fin,
         return;
     }
 
-    // ---------------- consumers: warp c takes chunks c, c + 8, ... of every tile
+    // ---------------- consumers: warp c takes chunks c, c + 8, ... of every
+    // tile (a chunk is 32 consecutive cells of one row) and arrives on the
+    // stage's empty barrier once per tile, with or without work.
     const int cwarp = warp - 1;
     const R omega = (R)p.omega;
     long long k = 0;
     for (long long t = blockIdx.x; t < ps.ntiles; t += gridDim.x, ++k) {
         const int s = (int)(k % ps.stages);
         if (!wait_phase(&full[s], (uint32_t)((k / ps.stages) & 1), p.err, &abort_flag)) break;
-        const long long row_idx = t / ps.nseg;
-        const int x0 = (int)(t - row_idx * ps.nseg) * W;
-        int y, z;
-        if (D == 2) {
-            y = (int)row_idx + woff;
-            z = 0;
-        } else {
-            z = (int)(row_idx / ny) + woff;
-            y = (int)(row_idx % ny);
-        }
-        const int a = (D == 2) ? y : z;
-        const int Lw = (D == 2) ? ny : p.g.nz;
-        const bool solid_m = walls && (a - 1 == 0);
-        const bool solid_p = walls && (a + 1 == Lw - 1);
+        int y0, z, x0, rows;
+        decode_tile<D>(ps, p.g, t, y0, z, x0, rows);
         const unsigned char* stage = smem + (size_t)s * ps.stage_bytes;
-        const long long rowl = (long long)z * ny + y;
-
-        for (int lx0 = cwarp * 32; lx0 < W; lx0 += PIPE_CONSUMER_WARPS * 32) {
-            const int lx = lx0 + lane;
+        const int width = rows_mode ? nx : ps.W;
+        const int chunks = rows * (width >> 5);
+        for (int c = cwarp; c < chunks; c += PIPE_CONSUMER_WARPS) {
+            const int r = c / (width >> 5);
+            const int lx = (c - r * (width >> 5)) * 32 + lane;
+            const int y = y0 + r;
             const int x = x0 + lx;
+            const int a = (D == 2) ? y : z;
+            const int Lw = (D == 2) ? ny : p.g.nz;
+            const bool solid_m = walls && (a - 1 == 0);
+            const bool solid_p = walls && (a + 1 == Lw - 1);
+            const long long rowl = (long long)z * ny + y;
             const long long cell = rowl * nx + x;
             const long long seg = rowl * p.g.nseg_x + (x >> 5);
             int band = 0;
@@ -271,7 +324,15 @@ k_sc_pipe(const typename StorageT<ST>::S* __restrict__ fin,
                 const bool bb = cwl == 0 ? false : (cwl > 0 ? solid_m : solid_p);
                 const int shift = bb ? 0 : L::cx(i);
                 const S* pl = reinterpret_cast<const S*>(stage + (size_t)i * ps.plane_bytes);
-                g[i] = T::load(pl, HALO + lx - shift, p.inv_scale);
+                int idx;
+                if (rows_mode) {
+                    int xs = lx - shift;
+                    xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
+                    idx = r * nx + xs;
+                } else {
+                    idx = HALO + lx - shift;
+                }
+                g[i] = T::load(pl, idx, p.inv_scale);
             }
             R Fx = (R)p.body[0], Fy = (R)p.body[1], Fz = (R)p.body[2];
             if (band) {
@@ -303,34 +364,58 @@ k_sc_pipe(const typename StorageT<ST>::S* __restrict__ fin,
 }
 
 // ------------------------------------------------------------------ host side
-bool pipe_shape(int Q, int storage, const GridParams& g, int sm_count, PipeShape& ps)
+static int elt_of(int storage) { return storage == ST_FP64 ? 8 : (storage == ST_FP32 ? 4 : 2); }
+
+bool pipe_shape(int Q, int storage, const GridParams& g, int sm_count, int rows_per_tile,
+                int ctas_per_sm, PipeShape& ps)
 {
-    const int elt = storage == ST_FP64 ? 8 : (storage == ST_FP32 ? 4 : 2);
+    const int elt = elt_of(storage);
     const int halo = 16 / elt;
-    if (g.nx % 256 != 0 || g.nx % halo != 0) return false;
-    int W = g.nx;
-    while (W > 1024) {
-        if (W % 2 != 0 || (W / 2) % 256 != 0) return false;
-        W /= 2;
-    }
     const int woff = g.walls ? 1 : 0;
-    const long long rows = (g.dim == 2) ? (long long)(g.ny - 2 * woff)
-                                        : (long long)g.ny * (g.nz - 2 * woff);
-    ps.W = W;
-    ps.nseg = g.nx / W;
-    ps.ntiles = rows * ps.nseg;
-    ps.plane_bytes = (W + 2 * halo) * elt;
+    if (ctas_per_sm < 1 || ctas_per_sm > 2) return false;
+    ps.ctas_per_sm = ctas_per_sm;
+    const int budget = (ctas_per_sm == 1 ? PIPE_SMEM_ONE_CTA : PIPE_SMEM_PER_CTA) - 1024;
+    if (g.nx % 32 == 0 && g.nx <= 1024) {
+        ps.mode = PIPE_ROWS;
+        const int ny_f = (g.dim == 2) ? g.ny - 2 * woff : g.ny;
+        const long long nz_f = (g.dim == 2) ? 1 : (long long)(g.nz - 2 * woff);
+        int R = rows_per_tile > 0 ? rows_per_tile : 1;
+        // at least 2 stages
+        while (R > 1 && 2LL * Q * R * g.nx * elt > budget) R--;
+        if (R > ny_f) R = ny_f;
+        ps.R = R;
+        ps.W = g.nx;
+        ps.nseg = 1;
+        ps.yblocks = (ny_f + R - 1) / R;
+        ps.ntiles = nz_f * ps.yblocks;
+        ps.plane_bytes = R * g.nx * elt;
+        ps.tx_bytes = (long long)Q * ps.plane_bytes;
+    } else {
+        if (g.nx % 256 != 0 || g.nx % halo != 0) return false;
+        ps.mode = PIPE_SEGMENTS;
+        int W = g.nx;
+        while (W > 1024 || 2LL * Q * (W * elt + 32) > budget) {
+            if (W % 2 != 0 || (W / 2) % 256 != 0) return false;
+            W /= 2;
+        }
+        const long long rows = (g.dim == 2) ? (long long)(g.ny - 2 * woff)
+                                            : (long long)g.ny * (g.nz - 2 * woff);
+        ps.R = 1;
+        ps.W = W;
+        ps.nseg = g.nx / W;
+        ps.yblocks = 0;
+        ps.ntiles = rows * ps.nseg;
+        ps.plane_bytes = (W + 2 * halo) * elt;
+        ps.tx_bytes = (long long)Q * (W * elt + 32);
+    }
     ps.stage_bytes = Q * ps.plane_bytes;
-    ps.tx_bytes = (long long)Q * (W * elt + 32);
-    ps.ctas_per_sm = 2;
-    const int budget = PIPE_SMEM_PER_CTA - 1024;
     ps.stages = budget / ps.stage_bytes;
     if (ps.stages > 8) ps.stages = 8;
     if (ps.stages < 2) return false;
     ps.smem_bytes = ps.stages * ps.stage_bytes + 2 * ps.stages * 8;
     ps.grid = sm_count * ps.ctas_per_sm;
     if (ps.ntiles < ps.grid) ps.grid = (int)ps.ntiles;
-    return ps.tx_bytes < (1 << 20);
+    return ps.tx_bytes < (1 << 20) && ps.ntiles > 0;
 }
 
 template <int Q, int ST>
@@ -353,7 +438,7 @@ static cudaError_t launch_pipe_t(bool write_all, const void* fin, void* fout, vo
 template <int Q, int ST>
 static cudaError_t prepare_t()
 {
-    const int bytes = PIPE_SMEM_PER_CTA;
+    const int bytes = PIPE_SMEM_ONE_CTA;
     cudaError_t e = cudaFuncSetAttribute(k_sc_pipe<Q, ST, true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)

@@ -105,7 +105,7 @@ def load():
         "iblb_force_field": (st, [vp, dp]),
         "iblb_interpolate": (st, [vp, dp, dp]),
         "iblb_step_profiled": (st, [vp, ip, dp]),
-        "iblb_set_tuning": (st, [vp, ip, ip, ip]),
+        "iblb_set_tuning": (st, [vp, ip, ip, ip, ip, ip]),
         "iblb_stream_collide_variant": (ctypes.c_int, [vp]),
         "iblb_stream_bytes_per_step": (ctypes.c_double, [vp]),
         "iblb_fluid_cells": (ctypes.c_longlong, [vp]),
@@ -232,8 +232,10 @@ def iblb_step_profiled(h, n_steps: int) -> np.ndarray:
     return out
 
 
-def iblb_set_tuning(h, variant: int, block_x: int = 128, streaming_stores: int = 0):
-    _check(h, load().iblb_set_tuning(h, int(variant), int(block_x), int(streaming_stores)))
+def iblb_set_tuning(h, variant: int, block_x: int = 128, streaming_stores: int = 0,
+                    rows_per_tile: int = 2, ctas_per_sm: int = 2):
+    _check(h, load().iblb_set_tuning(h, int(variant), int(block_x), int(streaming_stores),
+                                     int(rows_per_tile), int(ctas_per_sm)))
 
 
 def iblb_stream_collide_variant(h) -> int:
@@ -333,8 +335,9 @@ class Simulation:
         iblb_interpolate(self.h, u, qd)
         return qd
 
-    def set_tuning(self, variant, block_x=128, streaming_stores=0):
-        iblb_set_tuning(self.h, variant, block_x, streaming_stores)
+    def set_tuning(self, variant, block_x=128, streaming_stores=0, rows_per_tile=2,
+                   ctas_per_sm=2):
+        iblb_set_tuning(self.h, variant, block_x, streaming_stores, rows_per_tile, ctas_per_sm)
 
     @property
     def variant(self):

@@ -43,7 +43,7 @@ def truncated_circle(n: int, radius: float, theta0_deg: float, base_y: float,
     pts = np.zeros((n, 2))
     # parametrise: start at the right end of the base, walk the arc CCW to the
     # left end, then walk the base back left -> right.
-    a_start = -math.pi / 2 + th                  # angle of the right contact point
+    a_start = math.pi / 2 - th                   # angle of the right contact point
     for k, sk in enumerate(s):
         if sk < arc_len:
             ang = a_start + sk / radius
