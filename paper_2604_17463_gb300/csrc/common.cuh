@@ -115,8 +115,11 @@ struct PipeShape {
     int smem_bytes;        // dynamic shared memory per CTA
     int grid;              // persistent CTAs
 };
-constexpr int PIPE_SMEM_ONE_CTA = 227 * 1024;
-constexpr int PIPE_SMEM_PER_CTA = 227 * 1024 / 2 - 1024;
+// Shared-memory limits of the device (bytes), read at creation.
+struct SmemLimits {
+    int per_block_optin;   // cudaDevAttrMaxSharedMemoryPerBlockOptin
+    int per_sm;            // cudaDevAttrMaxSharedMemoryPerMultiprocessor
+};
 
 // ------------------------------------------------------------------ launchers
 // Storage ids match iblb_storage.
@@ -131,9 +134,9 @@ void launch_stream_collide(int Q, int storage, bool write_all, const void* fin, 
                            const Tuning& tu, cudaStream_t s);
 
 // Pipelined variant (lbm_pipe.cu): usable when pipe_shape() returns true.
-bool pipe_shape(int Q, int storage, const GridParams& g, int sm_count, int rows_per_tile,
-                int ctas_per_sm, PipeShape& ps);
-cudaError_t prepare_stream_collide_pipe();
+bool pipe_shape(int Q, int storage, const GridParams& g, int sm_count, const SmemLimits& lim,
+                int rows_per_tile, int ctas_per_sm, PipeShape& ps);
+cudaError_t prepare_stream_collide_pipe(const SmemLimits& lim);
 cudaError_t launch_stream_collide_pipe(int Q, int storage, bool write_all, const void* fin,
                                        void* fout, void* moments, void* F, uint8_t* flags,
                                        const StreamParams& p, const PipeShape& ps, cudaStream_t s);

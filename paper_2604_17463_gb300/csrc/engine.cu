@@ -23,6 +23,7 @@ using namespace iblb;
 
 namespace {
 std::atomic<long long> g_launches{0};
+thread_local std::string g_create_error;  // why the last iblb_create on this thread failed
 }
 
 struct iblb_sim {
@@ -36,6 +37,7 @@ struct iblb_sim {
     PipeShape pipe{};
     bool pipe_ok = false;
     int sm_count = 0;
+    SmemLimits smem{};
     ForceParams fp{};
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;  // private stream used only for graph capture
@@ -183,7 +185,7 @@ const char* iblb_status_string(iblb_status s)
     return "unknown status";
 }
 
-const char* iblb_last_error(iblb_handle h) { return h ? h->msg.c_str() : "null handle"; }
+const char* iblb_last_error(iblb_handle h) { return h ? h->msg.c_str() : g_create_error.c_str(); }
 
 long long iblb_kernel_launch_count(void) { return g_launches.load(); }
 
@@ -191,6 +193,7 @@ iblb_status iblb_create(const iblb_config* cfg, void* cuda_stream, iblb_handle* 
 {
     if (!cfg || !out) return IBLB_EINVAL;
     *out = nullptr;
+    g_create_error = "iblb_create: invalid configuration";
     const iblb_config& c = *cfg;
     if (c.lattice != IBLB_D2Q9 && c.lattice != IBLB_D3Q19) return IBLB_EINVAL;
     const int dim = c.lattice == IBLB_D2Q9 ? 2 : 3;
@@ -242,7 +245,7 @@ iblb_status iblb_create(const iblb_config* cfg, void* cuda_stream, iblb_handle* 
 
     auto bail = [&](cudaError_t e, const char* where) {
         iblb_destroy(h);
-        (void)where;
+        g_create_error = std::string("iblb_create: ") + where + ": " + cudaGetErrorString(e);
         return e == cudaErrorMemoryAllocation ? IBLB_ENOMEM : IBLB_ECUDA;
     };
     cudaError_t e;
@@ -274,9 +277,14 @@ iblb_status iblb_create(const iblb_config* cfg, void* cuda_stream, iblb_handle* 
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return bail(e, "device");
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
         return bail(e, "sm count");
-    if ((e = prepare_stream_collide_pipe()) != cudaSuccess) return bail(e, "pipe attributes");
+    if ((e = cudaDeviceGetAttribute(&h->smem.per_block_optin,
+                                    cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&h->smem.per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor,
+                                    dev)) != cudaSuccess)
+        return bail(e, "shared memory limits");
+    if ((e = prepare_stream_collide_pipe(h->smem)) != cudaSuccess) return bail(e, "pipe attributes");
     h->sm_count = sms;
-    h->pipe_ok = pipe_shape(h->Q, h->storage, g, sms, h->tune.rows_per_tile,
+    h->pipe_ok = pipe_shape(h->Q, h->storage, g, sms, h->smem, h->tune.rows_per_tile,
                             h->tune.ctas_per_sm, h->pipe);
     if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "init");
     *out = h;
@@ -616,8 +624,8 @@ iblb_status iblb_set_tuning(iblb_handle h, int variant, int block_x, int streami
     h->tune.streaming_stores = streaming_stores ? 1 : 0;
     h->tune.rows_per_tile = rows_per_tile;
     h->tune.ctas_per_sm = ctas_per_sm;
-    h->pipe_ok = pipe_shape(h->Q, h->storage, h->g, h->sm_count, rows_per_tile, ctas_per_sm,
-                            h->pipe);
+    h->pipe_ok = pipe_shape(h->Q, h->storage, h->g, h->sm_count, h->smem, rows_per_tile,
+                            ctas_per_sm, h->pipe);
     return IBLB_OK;
 }
 

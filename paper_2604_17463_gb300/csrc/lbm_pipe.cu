@@ -366,15 +366,25 @@ k_sc_pipe(const typename StorageT<ST>::S* __restrict__ fin,
 // ------------------------------------------------------------------ host side
 static int elt_of(int storage) { return storage == ST_FP64 ? 8 : (storage == ST_FP32 ? 4 : 2); }
 
-bool pipe_shape(int Q, int storage, const GridParams& g, int sm_count, int rows_per_tile,
-                int ctas_per_sm, PipeShape& ps)
+// Dynamic shared memory a CTA may request: the opt-in maximum for one CTA per
+// SM, half the SM's capacity for two; each less the static shared memory and
+// the per-CTA reservation.
+static int dyn_smem_limit(const SmemLimits& lim, int ctas_per_sm)
+{
+    const int one = lim.per_block_optin - 512;
+    const int two = (lim.per_sm - 2 * 1024) / 2 - 512;
+    return ctas_per_sm == 1 ? one : (two < one ? two : one);
+}
+
+bool pipe_shape(int Q, int storage, const GridParams& g, int sm_count, const SmemLimits& lim,
+                int rows_per_tile, int ctas_per_sm, PipeShape& ps)
 {
     const int elt = elt_of(storage);
     const int halo = 16 / elt;
     const int woff = g.walls ? 1 : 0;
     if (ctas_per_sm < 1 || ctas_per_sm > 2) return false;
     ps.ctas_per_sm = ctas_per_sm;
-    const int budget = (ctas_per_sm == 1 ? PIPE_SMEM_ONE_CTA : PIPE_SMEM_PER_CTA) - 1024;
+    const int budget = dyn_smem_limit(lim, ctas_per_sm) - 2 * 8 * 8;  // less the barriers
     if (g.nx % 32 == 0 && g.nx <= 1024) {
         ps.mode = PIPE_ROWS;
         const int ny_f = (g.dim == 2) ? g.ny - 2 * woff : g.ny;
@@ -436,9 +446,8 @@ static cudaError_t launch_pipe_t(bool write_all, const void* fin, void* fout, vo
 }
 
 template <int Q, int ST>
-static cudaError_t prepare_t()
+static cudaError_t prepare_t(int bytes)
 {
-    const int bytes = PIPE_SMEM_ONE_CTA;
     cudaError_t e = cudaFuncSetAttribute(k_sc_pipe<Q, ST, true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
@@ -447,17 +456,18 @@ static cudaError_t prepare_t()
     return e;
 }
 
-cudaError_t prepare_stream_collide_pipe()
+cudaError_t prepare_stream_collide_pipe(const SmemLimits& lim)
 {
-    static bool done = false;
-    if (done) return cudaSuccess;
-    cudaError_t e = prepare_t<9, ST_FP64>();
-    if (e == cudaSuccess) e = prepare_t<9, ST_FP32>();
-    if (e == cudaSuccess) e = prepare_t<9, ST_FP16>();
-    if (e == cudaSuccess) e = prepare_t<19, ST_FP64>();
-    if (e == cudaSuccess) e = prepare_t<19, ST_FP32>();
-    if (e == cudaSuccess) e = prepare_t<19, ST_FP16>();
-    if (e == cudaSuccess) done = true;
+    static int done_bytes = -1;
+    const int bytes = dyn_smem_limit(lim, 1);
+    if (done_bytes == bytes) return cudaSuccess;
+    cudaError_t e = prepare_t<9, ST_FP64>(bytes);
+    if (e == cudaSuccess) e = prepare_t<9, ST_FP32>(bytes);
+    if (e == cudaSuccess) e = prepare_t<9, ST_FP16>(bytes);
+    if (e == cudaSuccess) e = prepare_t<19, ST_FP64>(bytes);
+    if (e == cudaSuccess) e = prepare_t<19, ST_FP32>(bytes);
+    if (e == cudaSuccess) e = prepare_t<19, ST_FP16>(bytes);
+    if (e == cudaSuccess) done_bytes = bytes;
     return e;
 }
 

@@ -129,7 +129,7 @@ def _dptr(a: Optional[np.ndarray]):
 def _check(h, status: int):
     if status != IBLB_OK:
         lib = load()
-        msg = lib.iblb_last_error(h).decode() if h else ""
+        msg = (lib.iblb_last_error(h) or b"").decode()
         raise IBLBError(status, msg)
 
 
