@@ -79,24 +79,41 @@ __device__ __forceinline__ CellMoments<Q, R> cell_moments(const R* g, R Fx, R Fy
 }
 
 // BGK relaxation with the Guo source; g is overwritten with g*.
+// Written per pair of opposite directions (i, opp(i)): c.u and c.F change
+// sign between the two, so omega g^eq + S splits into a part common to both
+// and a part of opposite sign:
+//   sym  = w [omega (drho - rho 3/2 u.u + 9/2 rho (c.u)^2) - 3 pref u.F + 9 pref (c.u)(c.F)]
+//   asym = w [3 omega rho (c.u) + 3 pref (c.F)]
+//   g*_i = (1 - omega) g_i + sym + asym,   g*_opp = (1 - omega) g_opp + sym - asym
+// with pref = 1 - omega/2; the rest direction has c = 0.
 template <int Q, typename R>
 __device__ __forceinline__ void cell_collide(R* g, const CellMoments<Q, R>& m, R omega, R Fx, R Fy,
                                              R Fz)
 {
     using L = Stencil<Q>;
     constexpr int D = L::D;
-    const R usq15 = R(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
     const R pref = R(1) - R(0.5) * omega;
+    const R om1 = R(1) - omega;
     const R uF = m.ux * Fx + m.uy * Fy + m.uz * Fz;
+    const R base = omega * (m.drho - m.rho * (R(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz)));
+    const R sym0 = base - R(3) * pref * uF;     // common part without the (c.u) terms
+    const R k2 = omega * R(4.5) * m.rho;        // coefficient of (c.u)^2
+    const R k1 = omega * R(3) * m.rho;          // coefficient of (c.u)
+    const R p3 = R(3) * pref;
+    const R p9 = R(9) * pref;
+    g[0] = om1 * g[0] + (R)L::w(0) * sym0;
 #pragma unroll
-    for (int i = 0; i < Q; i++) {
-        const R cx = (R)L::cx(i), cy = (R)L::cy(i), cz = (R)L::cz(i);
+    for (int i = 1; i < Q; i++) {
+        if (L::opp(i) < i) continue;  // each pair once
+        const int o = L::opp(i);
         const R w = (R)L::w(i);
-        const R cu = cx * m.ux + cy * m.uy + (D == 3 ? cz * m.uz : R(0));
-        const R cF = cx * Fx + cy * Fy + (D == 3 ? cz * Fz : R(0));
-        const R geq = w * (m.drho + m.rho * (R(3) * cu + R(4.5) * cu * cu - usq15));
-        const R src = pref * w * (R(3) * (cF - uF) + R(9) * cu * cF);
-        g[i] = g[i] + omega * (geq - g[i]) + src;
+        const R cu = (R)L::cx(i) * m.ux + (R)L::cy(i) * m.uy + (D == 3 ? (R)L::cz(i) * m.uz : R(0));
+        const R cF = (R)L::cx(i) * Fx + (R)L::cy(i) * Fy + (D == 3 ? (R)L::cz(i) * Fz : R(0));
+        const R sym = w * (sym0 + cu * (k2 * cu + p9 * cF));
+        const R asym = w * (k1 * cu + p3 * cF);
+        const R gi = g[i], go = g[o];
+        g[i] = om1 * gi + sym + asym;
+        g[o] = om1 * go + sym - asym;
     }
 }
 

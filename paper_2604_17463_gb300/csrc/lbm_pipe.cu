@@ -122,8 +122,6 @@ __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, int* 
 
 }  // namespace
 
-constexpr int PIPE_CONSUMER_WARPS = 8;
-constexpr int PIPE_THREADS = 32 * (1 + PIPE_CONSUMER_WARPS);
 
 // Tile t -> first lattice row (y0, z) and first cell x0, with R_t rows.
 template <int D>
@@ -182,8 +180,9 @@ __device__ __forceinline__ void source_row(const GridParams& g, int y, int z, in
     }
 }
 
-template <int Q, int ST, bool WRITE_ALL>
-__global__ void __launch_bounds__(PIPE_THREADS, 2)
+// NC consumer warps per CTA: 8 with two CTAs per SM, 16 with one.
+template <int Q, int ST, bool WRITE_ALL, int NC>
+__global__ void __launch_bounds__(32 * (NC + 1), 16 / NC)
 k_sc_pipe(const typename StorageT<ST>::S* __restrict__ fin,
           typename StorageT<ST>::S* __restrict__ fout, typename StorageT<ST>::R* __restrict__ mom,
           typename StorageT<ST>::R* __restrict__ F, uint8_t* __restrict__ flags,
@@ -212,7 +211,7 @@ k_sc_pipe(const typename StorageT<ST>::S* __restrict__ fin,
         abort_flag = 0;
         for (int s = 0; s < ps.stages; s++) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], PIPE_CONSUMER_WARPS);
+            mbar_init(&empty[s], NC);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -287,7 +286,7 @@ k_sc_pipe(const typename StorageT<ST>::S* __restrict__ fin,
         return;
     }
 
-    // ---------------- consumers: warp c takes chunks c, c + 8, ... of every
+    // ---------------- consumers: warp c takes chunks c, c + NC, ... of every
     // tile (a chunk is 32 consecutive cells of one row) and arrives on the
     // stage's empty barrier once per tile, with or without work.
     const int cwarp = warp - 1;
@@ -301,7 +300,7 @@ k_sc_pipe(const typename StorageT<ST>::S* __restrict__ fin,
         const unsigned char* stage = smem + (size_t)s * ps.stage_bytes;
         const int width = rows_mode ? nx : ps.W;
         const int chunks = rows * (width >> 5);
-        for (int c = cwarp; c < chunks; c += PIPE_CONSUMER_WARPS) {
+        for (int c = cwarp; c < chunks; c += NC) {
             const int r = c / (width >> 5);
             const int lx = (c - r * (width >> 5)) * 32 + lane;
             const int y = y0 + r;
@@ -428,6 +427,18 @@ bool pipe_shape(int Q, int storage, const GridParams& g, int sm_count, const Sme
     return ps.tx_bytes < (1 << 20) && ps.ntiles > 0;
 }
 
+template <int Q, int ST, int NC>
+static void launch_pipe_nc(bool write_all, const typename StorageT<ST>::S* a,
+                           typename StorageT<ST>::S* b, typename StorageT<ST>::R* m,
+                           typename StorageT<ST>::R* f, uint8_t* flags, const StreamParams& p,
+                           const PipeShape& ps, cudaStream_t s)
+{
+    if (write_all)
+        k_sc_pipe<Q, ST, true, NC><<<ps.grid, 32 * (NC + 1), ps.smem_bytes, s>>>(a, b, m, f, flags, p, ps);
+    else
+        k_sc_pipe<Q, ST, false, NC><<<ps.grid, 32 * (NC + 1), ps.smem_bytes, s>>>(a, b, m, f, flags, p, ps);
+}
+
 template <int Q, int ST>
 static cudaError_t launch_pipe_t(bool write_all, const void* fin, void* fout, void* mom, void* F,
                                  uint8_t* flags, const StreamParams& p, const PipeShape& ps,
@@ -438,21 +449,21 @@ static cudaError_t launch_pipe_t(bool write_all, const void* fin, void* fout, vo
     auto* b = (typename T::S*)fout;
     auto* m = (typename T::R*)mom;
     auto* f = (typename T::R*)F;
-    if (write_all)
-        k_sc_pipe<Q, ST, true><<<ps.grid, PIPE_THREADS, ps.smem_bytes, s>>>(a, b, m, f, flags, p, ps);
+    if (ps.ctas_per_sm == 1)
+        launch_pipe_nc<Q, ST, 16>(write_all, a, b, m, f, flags, p, ps, s);
     else
-        k_sc_pipe<Q, ST, false><<<ps.grid, PIPE_THREADS, ps.smem_bytes, s>>>(a, b, m, f, flags, p, ps);
+        launch_pipe_nc<Q, ST, 8>(write_all, a, b, m, f, flags, p, ps, s);
     return cudaGetLastError();
 }
 
 template <int Q, int ST>
 static cudaError_t prepare_t(int bytes)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_sc_pipe<Q, ST, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_sc_pipe<Q, ST, false>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(k_sc_pipe<Q, ST, true, 8>, a, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sc_pipe<Q, ST, false, 8>, a, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sc_pipe<Q, ST, true, 16>, a, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sc_pipe<Q, ST, false, 16>, a, bytes);
     return e;
 }
 
