@@ -211,7 +211,8 @@ def run_ours(args, wl):
     sim = iblb.Simulation.from_workload(wl, storage=storage, stream=stream.cuda_stream)
     cells = sim.fluid_cells
 
-    # ---- device-resident throughput (value)
+    # ---- launch shape from the autotuner, then device-resident throughput (value)
+    tuned = sim.autotune(trials=10)
     sim.step(args.warmup)
     sim.sync()
     n0 = iblb.iblb_kernel_launch_count()
@@ -258,6 +259,8 @@ def run_ours(args, wl):
                            xi=wl.xi, theta_eq_deg=wl.theta_eq_deg, pi_n=wl.pi_n, pi_m=wl.pi_m,
                            storage=storage)
     sim2.set_interface(xyz_host, tri)
+    sim2.set_tuning(tuned["variant"], tuned["block_x"], 0, tuned["rows_per_tile"],
+                    tuned["ctas_per_sm"])
     sim2.step(args.warmup)
     sim2.sync()
     barrier()
@@ -293,6 +296,7 @@ def run_ours(args, wl):
                    "nz": wl.nz, "storage": args.storage, "nodes": int(wl.nodes.shape[0]),
                    "faces": int(wl.faces.shape[0]), "fluid_cells": cells,
                    "l2": "state (2 x 1.26 GB) larger than L2; no flush",
+                   "stream_collide_tuning": tuned,
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "kernel": "stream_collide", "achieved": achieved,
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",

@@ -169,6 +169,15 @@ iblb_status iblb_step_profiled(iblb_handle h, int n_steps, double* kernel_ms);
 iblb_status iblb_set_tuning(iblb_handle h, int variant, int block_x, int streaming_stores,
                             int rows_per_tile, int ctas_per_sm);
 
+/* Autotuner: time every applicable stream-collide launch shape (plain kernel
+ * with 64/128/256-thread blocks; pipelined kernel with 1, 2 or 4 rows per
+ * tile and 1 or 2 CTAs per SM) over `trials` launches each and keep the
+ * fastest.  The trial launches read the current populations and write only
+ * the second (scratch) population buffer, so the simulation state is left
+ * unchanged.  chosen[4] (may be NULL) receives variant, block_x,
+ * rows_per_tile, ctas_per_sm.  Synchronises. */
+iblb_status iblb_autotune(iblb_handle h, int trials, int* chosen);
+
 /* The stream-collide variant in use (0 plain, 1 pipelined). */
 int iblb_stream_collide_variant(iblb_handle h);
 

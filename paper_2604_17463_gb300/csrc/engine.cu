@@ -629,6 +629,77 @@ iblb_status iblb_set_tuning(iblb_handle h, int variant, int block_x, int streami
     return IBLB_OK;
 }
 
+iblb_status iblb_autotune(iblb_handle h, int trials, int* chosen)
+{
+    if (!h || trials < 1) return h ? fail(h, IBLB_EINVAL, "trials must be >= 1") : IBLB_EINVAL;
+    struct Cand {
+        int variant, block_x, rows, ctas;
+    };
+    std::vector<Cand> cands = {{0, 64, 2, 2}, {0, 128, 2, 2}, {0, 256, 2, 2}};
+    const int rows_opts[] = {1, 2, 4};
+    for (int ctas = 1; ctas <= 2; ctas++)
+        for (int r : rows_opts) {
+            PipeShape ps{};
+            if (pipe_shape(h->Q, h->storage, h->g, h->sm_count, h->smem, r, ctas, ps))
+                cands.push_back({1, 128, r, ctas});
+        }
+    CK(h, cudaStreamSynchronize(h->stream));
+    const Tuning saved = h->tune;
+    const PipeShape saved_ps = h->pipe;
+    const bool saved_ok = h->pipe_ok;
+    cudaEvent_t e0, e1;
+    CK(h, cudaEventCreate(&e0));
+    CK(h, cudaEventCreate(&e1));
+    float best = 1e30f;
+    Cand pick = {saved.variant, saved.block_x, saved.rows_per_tile, saved.ctas_per_sm};
+    for (const Cand& c : cands) {
+        h->tune.variant = c.variant;
+        h->tune.block_x = c.block_x;
+        h->tune.rows_per_tile = c.rows;
+        h->tune.ctas_per_sm = c.ctas;
+        h->pipe_ok = pipe_shape(h->Q, h->storage, h->g, h->sm_count, h->smem, c.rows, c.ctas,
+                                h->pipe);
+        // trial launches read f[cur] and write the scratch buffer f[cur ^ 1]
+        // only: with every band flag clear no other state is touched
+        launch_sc(h, h->stream, false);
+        cudaEventRecord(e0, h->stream);
+        for (int t = 0; t < trials; t++) launch_sc(h, h->stream, false);
+        cudaEventRecord(e1, h->stream);
+        g_launches += trials + 1;
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return cuda_fail(h, e, "autotune");
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            pick = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    (void)saved_ps;
+    (void)saved_ok;
+    clear_graphs(h);
+    h->tune.variant = pick.variant;
+    h->tune.block_x = pick.block_x;
+    h->tune.rows_per_tile = pick.rows;
+    h->tune.ctas_per_sm = pick.ctas;
+    h->pipe_ok = pipe_shape(h->Q, h->storage, h->g, h->sm_count, h->smem, pick.rows, pick.ctas,
+                            h->pipe);
+    if (chosen) {
+        chosen[0] = pick.variant;
+        chosen[1] = pick.block_x;
+        chosen[2] = pick.rows;
+        chosen[3] = pick.ctas;
+    }
+    CK(h, cudaGetLastError());
+    return check_device_flag(h);
+}
+
 int iblb_stream_collide_variant(iblb_handle h)
 {
     if (!h) return -1;

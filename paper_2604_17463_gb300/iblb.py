@@ -107,6 +107,7 @@ def load():
         "iblb_step_profiled": (st, [vp, ip, dp]),
         "iblb_set_tuning": (st, [vp, ip, ip, ip, ip, ip]),
         "iblb_stream_collide_variant": (ctypes.c_int, [vp]),
+        "iblb_autotune": (st, [vp, ip, ctypes.POINTER(ctypes.c_int)]),
         "iblb_stream_bytes_per_step": (ctypes.c_double, [vp]),
         "iblb_fluid_cells": (ctypes.c_longlong, [vp]),
         "iblb_kernel_launch_count": (ctypes.c_longlong, []),
@@ -238,6 +239,12 @@ def iblb_set_tuning(h, variant: int, block_x: int = 128, streaming_stores: int =
                                      int(rows_per_tile), int(ctas_per_sm)))
 
 
+def iblb_autotune(h, trials: int = 10) -> dict:
+    out = (ctypes.c_int * 4)()
+    _check(h, load().iblb_autotune(h, int(trials), out))
+    return {"variant": out[0], "block_x": out[1], "rows_per_tile": out[2], "ctas_per_sm": out[3]}
+
+
 def iblb_stream_collide_variant(h) -> int:
     return load().iblb_stream_collide_variant(h)
 
@@ -338,6 +345,9 @@ class Simulation:
     def set_tuning(self, variant, block_x=128, streaming_stores=0, rows_per_tile=2,
                    ctas_per_sm=2):
         iblb_set_tuning(self.h, variant, block_x, streaming_stores, rows_per_tile, ctas_per_sm)
+
+    def autotune(self, trials=10):
+        return iblb_autotune(self.h, trials)
 
     @property
     def variant(self):

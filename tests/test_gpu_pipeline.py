@@ -84,3 +84,24 @@ def test_pipeline_used_by_default_on_benchmark_shape():
     g.step(3)
     g.sync()
     g.close()
+
+
+def test_autotune_leaves_state_unchanged():
+    R, xi = 6.0, 1.0
+    nodes, faces = W.icosphere(2, R, (64.3, 9.7, W.WALL_PLANE + R + 2 * xi))
+    wl = W.Workload("tune3d", 19, 128, 20, 18, 0.8, 5e-3, xi, 75.0, 9, 3, 10, nodes, faces)
+    a = iblb.Simulation.from_workload(wl, storage=iblb.FP32_DEV)
+    b = iblb.Simulation.from_workload(wl, storage=iblb.FP32_DEV)
+    a.step(5)
+    b.step(5)
+    pick = b.autotune(trials=3)
+    assert pick["variant"] in (0, 1)
+    a.step(5)
+    b.step(5)
+    fa, fb = a.populations(), b.populations()
+    assert np.max(np.abs(fa - fb)) < 1e-7
+    _, _, qa = a.fields()
+    _, _, qb = b.fields()
+    assert np.max(np.abs(qa - qb)) < 1e-9
+    a.close()
+    b.close()
