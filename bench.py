@@ -212,7 +212,14 @@ def run_ours(args, wl):
     cells = sim.fluid_cells
 
     # ---- launch shape from the autotuner, then device-resident throughput (value)
-    tuned = sim.autotune(trials=10)
+    if args.tuning:
+        v, bx, rows, ctas = (int(x) for x in args.tuning.split(","))
+        sim.set_tuning(v, bx, 0, rows, ctas)
+        tuned = {"variant": sim.variant, "block_x": bx, "rows_per_tile": rows,
+                 "ctas_per_sm": ctas, "source": "fixed"}
+    else:
+        tuned = sim.autotune(trials=10)
+        tuned["source"] = "autotuner"
     sim.step(args.warmup)
     sim.sync()
     n0 = iblb.iblb_kernel_launch_count()
@@ -324,6 +331,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tuning", default="",
+                    help="fixed stream-collide launch shape 'variant,block_x,rows,ctas' "
+                         "instead of the autotuner (used for profiler runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
