@@ -35,7 +35,8 @@ WORKLOAD_NAME = "d3q19_256x256x128_icosphere_R40_fp32dev"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "stream_collide_d3q19_256x256x128_fp32.txt")
-LBM_SOURCE = os.path.join(ROOT, "paper_2604_17463_gb300", "csrc", "lbm.cu")
+CSRC = os.path.join(ROOT, "paper_2604_17463_gb300", "csrc")
+SC_SOURCES = [os.path.join(CSRC, n) for n in ("lbm.cu", "lbm_pipe.cu", "lbm_core.cuh", "common.cuh")]
 
 
 def hbm_peak():
@@ -46,9 +47,12 @@ def hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def source_digest(path):
-    with open(path, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+def source_digest(paths):
+    h = hashlib.sha256()
+    for path in paths:
+        with open(path, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def ncu_traffic():
@@ -61,7 +65,7 @@ def ncu_traffic():
                 if ":" in line:
                     k, v = line.split(":", 1)
                     vals[k.strip()] = v.strip()
-        if vals.get("lbm.cu sha256[:16]") != source_digest(LBM_SOURCE):
+        if vals.get("stream-collide sources sha256[:16]") != source_digest(SC_SOURCES):
             return None
         return float(vals["dram bytes per launch"])
     except Exception:

@@ -77,6 +77,8 @@ struct StreamParams {
     GridParams g;
     double omega;          // 1 / tau
     double body[3];        // uniform force density
+    float omega_f;         // the same in FP32 (no per-thread conversion on the FP32 paths)
+    float body_f[3];
     float scale, inv_scale;  // binary16 storage scale (1 for other storage)
     int* err;
 };

@@ -231,6 +231,8 @@ iblb_status iblb_create(const iblb_config* cfg, void* cuda_stream, iblb_handle* 
     sp.g = g;
     sp.omega = 1.0 / c.tau;
     for (int k = 0; k < 3; k++) sp.body[k] = (k < dim) ? c.body_force[k] : 0.0;
+    sp.omega_f = (float)sp.omega;
+    for (int k = 0; k < 3; k++) sp.body_f[k] = (float)sp.body[k];
     const int sexp = c.fp16_scale_exp ? c.fp16_scale_exp : 16;
     sp.scale = c.storage == IBLB_FP16_DEV ? std::ldexp(1.0f, sexp) : 1.0f;
     sp.inv_scale = 1.0f / sp.scale;

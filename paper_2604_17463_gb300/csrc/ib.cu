@@ -120,28 +120,35 @@ __global__ void k_face_geometry(const double* __restrict__ q, const int* __restr
     }
 }
 
-// 3D mesh, pass 2: one thread per node gathers its faces from a CSR list of
-// (face, corner) entries sorted by face (no atomics, fixed summation order).
+// 3D mesh, pass 2: eight lanes per node gather its faces from a CSR list of
+// (face, corner) entries (lane k takes entries k, k + 8, ...), then reduce by
+// shuffles; no atomics.
 __global__ void k_node_forces(const double* __restrict__ q, int N, const double* __restrict__ rec,
                               const int* __restrict__ csr_ptr, const int* __restrict__ csr_ent,
                               ForceParams fp, double* __restrict__ phi, double* __restrict__ nrm,
                               double* __restrict__ chi, int* err)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= N) return;
-    double fs[3] = {0, 0, 0}, ns[3] = {0, 0, 0}, area = 0.0;
-    for (int e = csr_ptr[j]; e < csr_ptr[j + 1]; e++) {
-        const int ent = csr_ent[e];
-        const int f = ent / 3, v = ent - 3 * (ent / 3);
-        const double* r = rec + (long long)FACE_REC * f;
-        for (int k = 0; k < 3; k++) {
-            fs[k] -= fp.sigma * 0.5 * r[4 + 3 * v + k];
-            ns[k] += r[k];
+    const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int j = (int)(gt >> 3);
+    const int sub = (int)(gt & 7);
+    double v[7] = {0, 0, 0, 0, 0, 0, 0};  // tension[3], normal sum[3], area
+    if (j < N) {
+        for (int e = csr_ptr[j] + sub; e < csr_ptr[j + 1]; e += 8) {
+            const int ent = csr_ent[e];
+            const int f = ent / 3, c = ent - 3 * (ent / 3);
+            const double* r = rec + (long long)FACE_REC * f;
+            for (int k = 0; k < 3; k++) {
+                v[k] -= fp.sigma * 0.5 * r[4 + 3 * c + k];
+                v[3 + k] += r[k];
+            }
+            v[6] += r[3];
         }
-        area += r[3];
     }
-    const double nl = sqrt(ns[0] * ns[0] + ns[1] * ns[1] + ns[2] * ns[2]);
-    const double nh[3] = {ns[0] / nl, ns[1] / nl, ns[2] / nl};
+    for (int o = 4; o > 0; o >>= 1)
+        for (int k = 0; k < 7; k++) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    if (sub != 0 || j >= N) return;
+    const double nl = sqrt(v[3] * v[3] + v[4] * v[4] + v[5] * v[5]);
+    const double nh[3] = {v[3] / nl, v[4] / nl, v[5] / nl};
     double pi = 0.0;
     if (fp.wetting) {
         const double d = q[3 * j + 2] - fp.wall_plane;
@@ -149,10 +156,10 @@ __global__ void k_node_forces(const double* __restrict__ q, int N, const double*
         pi = wetting_pi(fp, d);
     }
     for (int k = 0; k < 3; k++) {
-        phi[3 * j + k] = fs[k] + (-area * pi * nh[k]) / 3.0;
+        phi[3 * j + k] = v[k] + (-v[6] * pi * nh[k]) / 3.0;
         if (nrm) nrm[3 * j + k] = nh[k];
     }
-    if (chi) chi[j] = area;
+    if (chi) chi[j] = v[6];
 }
 
 void launch_forces(int dim, const double* q, int N, int M, const int* tri, const int* csr_ptr,
@@ -165,8 +172,9 @@ void launch_forces(int dim, const double* q, int N, int M, const int* tri, const
     } else {
         const int b = 64;
         k_face_geometry<<<(M + b - 1) / b, b, 0, s>>>(q, tri, M, face_rec);
-        k_node_forces<<<(N + b - 1) / b, b, 0, s>>>(q, N, face_rec, csr_ptr, csr_ent, fp, phi,
-                                                    normal, chi, err);
+        const long long t = 8LL * N;
+        k_node_forces<<<(int)((t + 127) / 128), 128, 0, s>>>(q, N, face_rec, csr_ptr, csr_ent, fp,
+                                                             phi, normal, chi, err);
     }
 }
 
@@ -182,30 +190,46 @@ __device__ __forceinline__ R delta4r(R r)
     return R(0);
 }
 
-// One warp per node.  Lanes 0 .. 4*D-1 evaluate the 1D weights of the node
-// (axis = lane / 4, offset = lane % 4) once, with the lattice index of that
-// stencil line (wrapped on periodic axes, -1 on a solid layer or outside the
-// lattice along the wall axis); every lane then forms the tensor-product
-// weights of its stencil points from warp shuffles.
+// One warp per node.  Lanes 0 .. D-1 split the node coordinate of their axis
+// into floor and fraction (FP64, once per axis); lanes 0 .. 4*D-1 then
+// evaluate the 1D weights of the node (axis = lane / 4, offset o = lane % 4,
+// distance to the stencil line = fraction + 1 - o) in the weight precision R,
+// with the lattice index of that stencil line (wrapped on periodic axes, -1
+// on a solid layer or outside the lattice along the wall axis).  Every lane
+// then forms the tensor-product weights of its stencil points from warp
+// shuffles.  All lanes must call it.
 template <int D, typename R>
 __device__ __forceinline__ void node_weights(const GridParams& g, const double* __restrict__ q,
                                              int node, int lane, R& wk, int& ik)
 {
+    int base = 0, ok = 0;
+    R frac = R(0);
+    if (lane < D) {
+        const double qk = q[D * node + lane];
+        if (fabs(qk) < 1.0e9) {   // a diverged node touches nothing
+            const double fl = floor(qk);
+            base = (int)fl - 1;
+            frac = (R)(qk - fl);
+            ok = 1;
+        }
+    }
+    const int k = lane >> 2;
+    const int src = k < D ? k : 0;
+    const int b = __shfl_sync(0xffffffffu, base, src);
+    const R fr = __shfl_sync(0xffffffffu, frac, src);
+    const int okk = __shfl_sync(0xffffffffu, ok, src);
     wk = R(0);
     ik = -1;
-    if (lane < 4 * D) {
-        const int k = lane >> 2;
-        const double qk = q[D * node + k];
+    if (lane < 4 * D && okk) {
+        const int o = lane & 3;
         const int ext = k == 0 ? g.nx : (k == 1 ? g.ny : g.nz);
-        if (fabs(qk) < 1.0e9) {   // a diverged node touches nothing
-            const int i = (int)floor(qk) - 1 + (lane & 3);
-            wk = delta4r<R>((R)(qk - (double)i));
-            if (k == D - 1 && g.walls) {
-                ik = (i <= 0 || i >= ext - 1) ? -1 : i;
-            } else {
-                const int r = i % ext;
-                ik = r < 0 ? r + ext : r;
-            }
+        const int i = b + o;
+        wk = delta4r<R>(fr + (R)(1 - o));
+        if (k == D - 1 && g.walls) {
+            ik = (i <= 0 || i >= ext - 1) ? -1 : i;
+        } else {
+            const int r = i % ext;
+            ik = r < 0 ? r + ext : r;
         }
     }
 }
@@ -247,8 +271,10 @@ __global__ void k_spread(const double* __restrict__ q, const double* __restrict_
     R wk;
     int ik;
     node_weights<D, R>(g, q, node, lane, wk, ik);
+    R phl = R(0);
+    if (lane < D) phl = (R)phi[D * node + lane];
     R ph[3];
-    for (int k = 0; k < D; k++) ph[k] = (R)phi[D * node + k];
+    for (int k = 0; k < D; k++) ph[k] = __shfl_sync(0xffffffffu, phl, k);
 #pragma unroll
     for (int p = 0; p < PPL; p++) {
         const int s = lane + 32 * p;

@@ -44,6 +44,20 @@ template <> struct StorageT<ST_FP16> {
     }
 };
 
+// Relaxation rate and body force in the compute precision.
+template <typename R>
+__device__ __forceinline__ R param_omega(const StreamParams& p);
+template <>
+__device__ __forceinline__ double param_omega<double>(const StreamParams& p) { return p.omega; }
+template <>
+__device__ __forceinline__ float param_omega<float>(const StreamParams& p) { return p.omega_f; }
+template <typename R>
+__device__ __forceinline__ R param_body(const StreamParams& p, int k);
+template <>
+__device__ __forceinline__ double param_body<double>(const StreamParams& p, int k) { return p.body[k]; }
+template <>
+__device__ __forceinline__ float param_body<float>(const StreamParams& p, int k) { return p.body_f[k]; }
+
 // Moments of the deviations and the velocity with the half-force term.
 template <int Q, typename R>
 struct CellMoments {

@@ -290,7 +290,7 @@ k_sc_pipe(const typename StorageT<ST>::S* __restrict__ fin,
     // tile (a chunk is 32 consecutive cells of one row) and arrives on the
     // stage's empty barrier once per tile, with or without work.
     const int cwarp = warp - 1;
-    const R omega = (R)p.omega;
+    const R omega = param_omega<R>(p);
     long long k = 0;
     for (long long t = blockIdx.x; t < ps.ntiles; t += gridDim.x, ++k) {
         const int s = (int)(k % ps.stages);
@@ -333,7 +333,7 @@ k_sc_pipe(const typename StorageT<ST>::S* __restrict__ fin,
                 }
                 g[i] = T::load(pl, idx, p.inv_scale);
             }
-            R Fx = (R)p.body[0], Fy = (R)p.body[1], Fz = (R)p.body[2];
+            R Fx = param_body<R>(p, 0), Fy = param_body<R>(p, 1), Fz = param_body<R>(p, 2);
             if (band) {
                 Fx += F[cell];
                 Fy += F[nc + cell];
