@@ -186,6 +186,43 @@ int iblb_stream_collide_variant(iblb_handle h);
 double iblb_stream_bytes_per_step(iblb_handle h);
 long long iblb_fluid_cells(iblb_handle h);
 
+/* ---- mass reduction without device allocation ----
+ *
+ * The paper has no counterpart: this is a service of the library.
+ *
+ * iblb_mass_static computes the same FP64 mass as iblb_observables (sum of
+ * rho over the fluid cells) for a population array the caller owns, without
+ * allocating device memory.  It is meant for callers that cannot call
+ * cudaMalloc when they need the number: a process that reserves all of its
+ * GPU memory up front (for example a serving loop running from a fixed
+ * pool), code that runs while another component owns the device allocator,
+ * or an embedding that forbids device allocations after initialisation.
+ *
+ *   f_dev     device pointer to the populations in this library's storage
+ *             form: deviations f_i - w_i, layout [Q][nx*ny*nz] (x fastest),
+ *             double (IBLB_FP64), float (IBLB_FP32_DEV) or binary16 scaled
+ *             by 2^fp16_scale_exp (IBLB_FP16_DEV; 0 selects 16)
+ *   mass_dev  device pointer to one double that receives the mass
+ *   walls     1: the first and last layer along the wall axis are solid and
+ *             excluded, as in iblb_config
+ *   cuda_stream  stream the two kernels are enqueued on (asynchronous)
+ *
+ * Scratch: per-block partial sums live in one file-scope device array of
+ * IBLB_STATIC_PARTIALS doubles (512 KiB), which every GPU that loads the
+ * library holds until the process exits.  One partial covers 16384 cells, so
+ * lattices above IBLB_STATIC_PARTIALS * 16384 cells are rejected with
+ * IBLB_EINVAL before anything is launched.  Each call overwrites the
+ * partials it uses (the array keeps the last call's values; nothing needs
+ * to start at zero), and all calls share the array: calls that overlap on
+ * the GPU (on different streams, or from different threads) race and give
+ * wrong results.  The first call on a device resolves the array's device
+ * address with that device current; make that first call before any stream
+ * capture.  The call makes no cudaMalloc, cudaFree or other allocating call.
+ * Returns IBLB_EINVAL for bad arguments, IBLB_ECUDA if a CUDA call fails. */
+#define IBLB_STATIC_PARTIALS 65536
+iblb_status iblb_mass_static(const void* f_dev, int lattice, int storage, int nx, int ny, int nz,
+                             int walls, int fp16_scale_exp, double* mass_dev, void* cuda_stream);
+
 /* Number of kernels this library has launched since load (counting every
  * launch, including those inside CUDA graphs). */
 long long iblb_kernel_launch_count(void);

@@ -108,6 +108,7 @@ def load():
         "iblb_set_tuning": (st, [vp, ip, ip, ip, ip, ip]),
         "iblb_stream_collide_variant": (ctypes.c_int, [vp]),
         "iblb_autotune": (st, [vp, ip, ctypes.POINTER(ctypes.c_int)]),
+        "iblb_mass_static": (st, [vp, ip, ip, ip, ip, ip, ip, ip, vp, vp]),
         "iblb_stream_bytes_per_step": (ctypes.c_double, [vp]),
         "iblb_fluid_cells": (ctypes.c_longlong, [vp]),
         "iblb_kernel_launch_count": (ctypes.c_longlong, []),
@@ -243,6 +244,18 @@ def iblb_autotune(h, trials: int = 10) -> dict:
     out = (ctypes.c_int * 4)()
     _check(h, load().iblb_autotune(h, int(trials), out))
     return {"variant": out[0], "block_x": out[1], "rows_per_tile": out[2], "ctas_per_sm": out[3]}
+
+
+def iblb_mass_static(f_dev_ptr: int, lattice: int, storage: int, nx: int, ny: int, nz: int,
+                     walls: int, fp16_scale_exp: int, mass_dev_ptr: int, stream: Optional[int] = None):
+    """FP64 mass of a caller-owned device population array, with no device
+    allocation (see include/iblb.h); pointers are device addresses."""
+    s = current_stream_handle() if stream is None else stream
+    st = load().iblb_mass_static(ctypes.c_void_p(f_dev_ptr), int(lattice), int(storage), int(nx),
+                                 int(ny), int(nz), int(walls), int(fp16_scale_exp),
+                                 ctypes.c_void_p(mass_dev_ptr), ctypes.c_void_p(s))
+    if st != IBLB_OK:
+        raise IBLBError(st, "iblb_mass_static")
 
 
 def iblb_stream_collide_variant(h) -> int:
