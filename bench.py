@@ -217,10 +217,10 @@ def run_ours(args, wl):
 
     # ---- launch shape from the autotuner, then device-resident throughput (value)
     if args.tuning:
-        v, bx, rows, ctas = (int(x) for x in args.tuning.split(","))
-        sim.set_tuning(v, bx, 0, rows, ctas)
-        tuned = {"variant": sim.variant, "block_x": bx, "rows_per_tile": rows,
-                 "ctas_per_sm": ctas, "source": "fixed"}
+        v, bx, rows, ctas, ncw = (int(x) for x in args.tuning.split(","))
+        sim.set_tuning(v, bx, 0, rows, ctas, ncw)
+        tuned = sim.tuning()
+        tuned["source"] = "fixed"
     else:
         tuned = sim.autotune(trials=10)
         tuned["source"] = "autotuner"
@@ -271,7 +271,7 @@ def run_ours(args, wl):
                            storage=storage)
     sim2.set_interface(xyz_host, tri)
     sim2.set_tuning(tuned["variant"], tuned["block_x"], 0, tuned["rows_per_tile"],
-                    tuned["ctas_per_sm"])
+                    tuned["ctas_per_sm"], tuned["consumer_warps"])
     sim2.step(args.warmup)
     sim2.sync()
     barrier()
@@ -336,7 +336,7 @@ def main():
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tuning", default="",
-                    help="fixed stream-collide launch shape 'variant,block_x,rows,ctas' "
+                    help="fixed stream-collide launch shape 'variant,block_x,rows,ctas,warps' "
                          "instead of the autotuner (used for profiler runs)")
     args = ap.parse_args()
     if args.warmup < 3:

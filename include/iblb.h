@@ -157,26 +157,37 @@ enum {
  * each kernel (ms).  Synchronises. */
 iblb_status iblb_step_profiled(iblb_handle h, int n_steps, double* kernel_ms);
 
-/* Launch shape of the stream-collide kernel.  variant 1 (default) selects the
- * pipelined kernel (persistent CTAs; a producer warp stages the source rows
- * in shared memory with bulk asynchronous copies) where the lattice allows it
- * (nx a multiple of 32 up to 1024: tiles of rows_per_tile whole rows; else
- * nx a multiple of 256: row segments), with ctas_per_sm (1 or 2) resident
- * CTAs per SM; variant 0 the plain one-cell-per-thread kernel with block_x
- * threads per block along x (64, 128 or 256) and evict-first stores when
- * streaming_stores != 0.  Results do not depend on the choice.
- * Synchronises. */
-iblb_status iblb_set_tuning(iblb_handle h, int variant, int block_x, int streaming_stores,
-                            int rows_per_tile, int ctas_per_sm);
+/* Launch shape of the stream-collide kernel (results do not depend on it).
+ *   variant 0: the plain kernel, one cell per thread, block_x threads per
+ *              block along x (64, 128 or 256), evict-first stores of the new
+ *              populations when streaming_stores != 0;
+ *   variant 1: the pipelined kernel: persistent CTAs in which a producer warp
+ *              stages the source rows in shared memory with bulk asynchronous
+ *              copies and consumer_warps warps collide from there;
+ *              ctas_per_sm = 2 with 8 consumer warps, or 1 with 16 or 32.
+ *              Usable when nx is a multiple of 32 up to 1024 (tiles of
+ *              rows_per_tile whole rows) or a multiple of 256 (row
+ *              segments); otherwise the plain kernel runs. */
+typedef struct {
+    int variant;
+    int block_x;
+    int streaming_stores;
+    int rows_per_tile;
+    int ctas_per_sm;
+    int consumer_warps;
+} iblb_tuning;
 
-/* Autotuner: time every applicable stream-collide launch shape (plain kernel
- * with 64/128/256-thread blocks; pipelined kernel with 1, 2 or 4 rows per
- * tile and 1 or 2 CTAs per SM) over `trials` launches each and keep the
+/* Set / read the launch shape.  iblb_set_tuning synchronises. */
+iblb_status iblb_set_tuning(iblb_handle h, const iblb_tuning* t);
+iblb_status iblb_get_tuning(iblb_handle h, iblb_tuning* t);
+
+/* Autotuner: time every applicable launch shape (plain kernel with 64, 128
+ * and 256-thread blocks; pipelined kernel with 1, 2 or 4 rows per tile and
+ * 8, 16 or 32 consumer warps) over `trials` launches each and keep the
  * fastest.  The trial launches read the current populations and write only
  * the second (scratch) population buffer, so the simulation state is left
- * unchanged.  chosen[4] (may be NULL) receives variant, block_x,
- * rows_per_tile, ctas_per_sm.  Synchronises. */
-iblb_status iblb_autotune(iblb_handle h, int trials, int* chosen);
+ * unchanged.  `chosen` (may be NULL) receives the kept shape.  Synchronises. */
+iblb_status iblb_autotune(iblb_handle h, int trials, iblb_tuning* chosen);
 
 /* The stream-collide variant in use (0 plain, 1 pipelined). */
 int iblb_stream_collide_variant(iblb_handle h);

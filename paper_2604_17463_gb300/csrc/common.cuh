@@ -98,6 +98,7 @@ struct Tuning {
     int streaming_stores = 0;   // plain kernel: evict-first stores of the new populations
     int rows_per_tile = 2;      // pipelined kernel, rows mode: rows per tile
     int ctas_per_sm = 2;        // pipelined kernel: resident CTAs per SM (1 or 2)
+    int consumer_warps = 8;     // pipelined kernel: 8 (2 CTAs/SM), 16 or 32 (1 CTA/SM)
 };
 
 // Shape of the pipelined stream-collide launch (see lbm_pipe.cu).
@@ -114,6 +115,7 @@ struct PipeShape {
     long long tx_bytes;    // bytes copied per full stage
     int stages;            // pipeline depth per CTA
     int ctas_per_sm;
+    int consumer_warps;    // consumer warps per CTA (8, 16 or 32)
     int smem_bytes;        // dynamic shared memory per CTA
     int grid;              // persistent CTAs
 };
@@ -137,7 +139,7 @@ void launch_stream_collide(int Q, int storage, bool write_all, const void* fin, 
 
 // Pipelined variant (lbm_pipe.cu): usable when pipe_shape() returns true.
 bool pipe_shape(int Q, int storage, const GridParams& g, int sm_count, const SmemLimits& lim,
-                int rows_per_tile, int ctas_per_sm, PipeShape& ps);
+                int rows_per_tile, int ctas_per_sm, int consumer_warps, PipeShape& ps);
 cudaError_t prepare_stream_collide_pipe(const SmemLimits& lim);
 cudaError_t launch_stream_collide_pipe(int Q, int storage, bool write_all, const void* fin,
                                        void* fout, void* moments, void* F, uint8_t* flags,
@@ -168,12 +170,13 @@ void launch_mass_partials(int Q, int storage, const void* f, const GridParams& g
                           double* partial, cudaStream_t s);
 
 // IB kernels.  q, phi: [N][dim] FP64.
-// 2D ring: one kernel; 3D mesh: per-face geometry into face_rec (16 doubles
-// per face) then a per-node CSR gather (two kernels).
+// 2D ring: one kernel; 3D mesh: per-face geometry written as one record per
+// (face, corner) at its CSR position entry_pos[3f + corner] (8 doubles per
+// record), then a per-node sum over its contiguous records (two kernels).
 void launch_forces(int dim, const double* q, int N, int M, const int* tri, const int* csr_ptr,
-                   const int* csr_ent, double* face_rec, const ForceParams& fp, double* phi,
+                   const int* entry_pos, double* entry_rec, const ForceParams& fp, double* phi,
                    double* normal, double* chi, int* err, cudaStream_t s);
-constexpr int FACE_RECORD_DOUBLES = 16;
+constexpr int ENTRY_RECORD_DOUBLES = 8;
 void launch_spread(int storage, int dim, const double* q, const double* phi, int N, void* F,
                    uint8_t* flags, const GridParams& g, cudaStream_t s);
 // qdot [N][dim] = sum u Delta; if advect, q += qdot.

@@ -57,8 +57,8 @@ struct iblb_sim {
     double* phi = nullptr;
     int* tri = nullptr;
     int* csr_ptr = nullptr;
-    int* csr_ent = nullptr;
-    double* face_rec = nullptr;  // per-face geometry records (3D)
+    int* entry_pos = nullptr;    // CSR position of each (face, corner) (3D)
+    double* entry_rec = nullptr; // per-(face, corner) geometry records in CSR order (3D)
     std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;  // (parity, steps, last)
     std::string msg;
 };
@@ -112,7 +112,7 @@ void launch_sc(iblb_sim* h, cudaStream_t s, bool write_all)
 void enqueue_step(iblb_sim* h, cudaStream_t s, bool write_all)
 {
     if (h->N > 0) {
-        launch_forces(h->dim, h->q, h->N, h->M, h->tri, h->csr_ptr, h->csr_ent, h->face_rec, h->fp, h->phi, nullptr,
+        launch_forces(h->dim, h->q, h->N, h->M, h->tri, h->csr_ptr, h->entry_pos, h->entry_rec, h->fp, h->phi, nullptr,
                       nullptr, h->err, s);
         launch_spread(h->storage, h->dim, h->q, h->phi, h->N, h->F, h->flags, h->g, s);
     }
@@ -164,6 +164,14 @@ double wetting_amplitude(const iblb_config& c)
     const double th = c.theta_eq_deg * (M_PI / 180.0);
     return c.sigma * ((double)(c.pi_m - 1) * (double)(c.pi_n - 1)) /
            ((double)(c.pi_n - c.pi_m) * c.xi) * (1.0 + std::cos(th));
+}
+
+bool apply_tuning(iblb_sim* h, const Tuning& t)
+{
+    h->tune = t;
+    h->pipe_ok = pipe_shape(h->Q, h->storage, h->g, h->sm_count, h->smem, t.rows_per_tile,
+                            t.ctas_per_sm, t.consumer_warps, h->pipe);
+    return h->pipe_ok;
 }
 
 }  // namespace
@@ -286,8 +294,7 @@ iblb_status iblb_create(const iblb_config* cfg, void* cuda_stream, iblb_handle* 
         return bail(e, "shared memory limits");
     if ((e = prepare_stream_collide_pipe(h->smem)) != cudaSuccess) return bail(e, "pipe attributes");
     h->sm_count = sms;
-    h->pipe_ok = pipe_shape(h->Q, h->storage, g, sms, h->smem, h->tune.rows_per_tile,
-                            h->tune.ctas_per_sm, h->pipe);
+    apply_tuning(h, h->tune);
     if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "init");
     *out = h;
     return IBLB_OK;
@@ -310,8 +317,8 @@ void iblb_destroy(iblb_handle h)
     free_dev(h->phi);
     free_dev(h->tri);
     free_dev(h->csr_ptr);
-    free_dev(h->csr_ent);
-    free_dev(h->face_rec);
+    free_dev(h->entry_pos);
+    free_dev(h->entry_rec);
     if (h->cap) cudaStreamDestroy(h->cap);
     delete h;
 }
@@ -341,10 +348,11 @@ iblb_status iblb_set_interface(iblb_handle h, const double* xyz, int n_nodes, co
         ptr.assign(n_nodes + 1, 0);
         for (long long k = 0; k < 3LL * n_faces; k++) ptr[tri[k] + 1]++;
         for (int j = 0; j < n_nodes; j++) ptr[j + 1] += ptr[j];
+        // entry position of each (face, corner); faces in increasing order per node
         ent.resize(3LL * n_faces);
         std::vector<int> fill(ptr.begin(), ptr.end() - 1);
         for (int f = 0; f < n_faces; f++)
-            for (int v = 0; v < 3; v++) ent[fill[tri[3 * f + v]]++] = 3 * f + v;
+            for (int v = 0; v < 3; v++) ent[3 * f + v] = fill[tri[3 * f + v]]++;
         for (int j = 0; j < n_nodes; j++)
             if (ptr[j + 1] == ptr[j]) return fail(h, IBLB_EINVAL, "a node belongs to no face");
     }
@@ -354,8 +362,8 @@ iblb_status iblb_set_interface(iblb_handle h, const double* xyz, int n_nodes, co
     free_dev(h->phi);
     free_dev(h->tri);
     free_dev(h->csr_ptr);
-    free_dev(h->csr_ent);
-    free_dev(h->face_rec);
+    free_dev(h->entry_pos);
+    free_dev(h->entry_rec);
     h->N = n_nodes;
     h->M = dim == 2 ? n_nodes : n_faces;
     if (n_nodes == 0) return IBLB_OK;
@@ -366,13 +374,13 @@ iblb_status iblb_set_interface(iblb_handle h, const double* xyz, int n_nodes, co
     if (dim == 3) {
         CK(h, cudaMalloc(&h->tri, sizeof(int) * 3 * (size_t)n_faces));
         CK(h, cudaMalloc(&h->csr_ptr, sizeof(int) * (n_nodes + 1)));
-        CK(h, cudaMalloc(&h->csr_ent, sizeof(int) * ent.size()));
-        CK(h, cudaMalloc(&h->face_rec, sizeof(double) * FACE_RECORD_DOUBLES * (size_t)n_faces));
+        CK(h, cudaMalloc(&h->entry_pos, sizeof(int) * ent.size()));
+        CK(h, cudaMalloc(&h->entry_rec, sizeof(double) * ENTRY_RECORD_DOUBLES * ent.size()));
         CK(h, cudaMemcpyAsync(h->tri, tri, sizeof(int) * 3 * (size_t)n_faces,
                               cudaMemcpyHostToDevice, h->stream));
         CK(h, cudaMemcpyAsync(h->csr_ptr, ptr.data(), sizeof(int) * ptr.size(),
                               cudaMemcpyHostToDevice, h->stream));
-        CK(h, cudaMemcpyAsync(h->csr_ent, ent.data(), sizeof(int) * ent.size(),
+        CK(h, cudaMemcpyAsync(h->entry_pos, ent.data(), sizeof(int) * ent.size(),
                               cudaMemcpyHostToDevice, h->stream));
     }
     CK(h, cudaStreamSynchronize(h->stream));
@@ -502,7 +510,7 @@ iblb_status iblb_nodal_forces(iblb_handle h, double* phi, double* normal, double
     double *dn = nullptr, *dc = nullptr;
     CK(h, cudaMalloc(&dn, nb));
     CK(h, cudaMalloc(&dc, sizeof(double) * h->N));
-    launch_forces(h->dim, h->q, h->N, h->M, h->tri, h->csr_ptr, h->csr_ent, h->face_rec, h->fp, h->phi, dn, dc,
+    launch_forces(h->dim, h->q, h->N, h->M, h->tri, h->csr_ptr, h->entry_pos, h->entry_rec, h->fp, h->phi, dn, dc,
                   h->err, h->stream);
     g_launches += force_kernels(h);
     cudaError_t e = cudaGetLastError();
@@ -526,7 +534,7 @@ iblb_status iblb_force_field(iblb_handle h, double* F)
     double* tmp = nullptr;
     CK(h, cudaMalloc(&tmp, sizeof(double) * h->dim * nc));
     if (h->N > 0) {
-        launch_forces(h->dim, h->q, h->N, h->M, h->tri, h->csr_ptr, h->csr_ent, h->face_rec, h->fp, h->phi, nullptr,
+        launch_forces(h->dim, h->q, h->N, h->M, h->tri, h->csr_ptr, h->entry_pos, h->entry_rec, h->fp, h->phi, nullptr,
                       nullptr, h->err, h->stream);
         launch_spread(h->storage, h->dim, h->q, h->phi, h->N, h->F, h->flags, h->g, h->stream);
         g_launches += force_kernels(h) + 1;
@@ -587,7 +595,7 @@ iblb_status iblb_step_profiled(iblb_handle h, int n_steps, double* kernel_ms)
         const bool ib = h->N > 0;
         cudaEventRecord(ev[0], h->stream);
         if (ib)
-            launch_forces(h->dim, h->q, h->N, h->M, h->tri, h->csr_ptr, h->csr_ent, h->face_rec, h->fp, h->phi,
+            launch_forces(h->dim, h->q, h->N, h->M, h->tri, h->csr_ptr, h->entry_pos, h->entry_rec, h->fp, h->phi,
                           nullptr, nullptr, h->err, h->stream);
         cudaEventRecord(ev[1], h->stream);
         if (ib) launch_spread(h->storage, h->dim, h->q, h->phi, h->N, h->F, h->flags, h->g, h->stream);
@@ -610,57 +618,74 @@ iblb_status iblb_step_profiled(iblb_handle h, int n_steps, double* kernel_ms)
     return check_device_flag(h);
 }
 
-iblb_status iblb_set_tuning(iblb_handle h, int variant, int block_x, int streaming_stores,
-                            int rows_per_tile, int ctas_per_sm)
+iblb_status iblb_set_tuning(iblb_handle h, const iblb_tuning* t)
 {
-    if (!h) return IBLB_EINVAL;
-    if (variant != 0 && variant != 1) return fail(h, IBLB_EINVAL, "variant must be 0 or 1");
-    if (block_x != 64 && block_x != 128 && block_x != 256)
+    if (!h || !t) return IBLB_EINVAL;
+    if (t->variant != 0 && t->variant != 1) return fail(h, IBLB_EINVAL, "variant must be 0 or 1");
+    if (t->block_x != 64 && t->block_x != 128 && t->block_x != 256)
         return fail(h, IBLB_EINVAL, "block_x must be 64, 128 or 256");
-    if (rows_per_tile < 1 || rows_per_tile > 64) return fail(h, IBLB_EINVAL, "rows_per_tile in 1..64");
-    if (ctas_per_sm != 1 && ctas_per_sm != 2) return fail(h, IBLB_EINVAL, "ctas_per_sm must be 1 or 2");
+    if (t->rows_per_tile < 1 || t->rows_per_tile > 64)
+        return fail(h, IBLB_EINVAL, "rows_per_tile in 1..64");
+    if (!((t->ctas_per_sm == 2 && t->consumer_warps == 8) ||
+          (t->ctas_per_sm == 1 && (t->consumer_warps == 16 || t->consumer_warps == 32))))
+        return fail(h, IBLB_EINVAL, "ctas_per_sm 2 with 8 consumer warps, or 1 with 16 or 32");
     CK(h, cudaStreamSynchronize(h->stream));
     clear_graphs(h);
-    h->tune.variant = variant;
-    h->tune.block_x = block_x;
-    h->tune.streaming_stores = streaming_stores ? 1 : 0;
-    h->tune.rows_per_tile = rows_per_tile;
-    h->tune.ctas_per_sm = ctas_per_sm;
-    h->pipe_ok = pipe_shape(h->Q, h->storage, h->g, h->sm_count, h->smem, rows_per_tile,
-                            ctas_per_sm, h->pipe);
+    Tuning tu;
+    tu.variant = t->variant;
+    tu.block_x = t->block_x;
+    tu.streaming_stores = t->streaming_stores ? 1 : 0;
+    tu.rows_per_tile = t->rows_per_tile;
+    tu.ctas_per_sm = t->ctas_per_sm;
+    tu.consumer_warps = t->consumer_warps;
+    apply_tuning(h, tu);
     return IBLB_OK;
 }
 
-iblb_status iblb_autotune(iblb_handle h, int trials, int* chosen)
+iblb_status iblb_get_tuning(iblb_handle h, iblb_tuning* t)
+{
+    if (!h || !t) return IBLB_EINVAL;
+    t->variant = (h->tune.variant == 1 && h->pipe_ok) ? 1 : 0;
+    t->block_x = h->tune.block_x;
+    t->streaming_stores = h->tune.streaming_stores;
+    t->rows_per_tile = h->tune.rows_per_tile;
+    t->ctas_per_sm = h->tune.ctas_per_sm;
+    t->consumer_warps = h->tune.consumer_warps;
+    return IBLB_OK;
+}
+
+iblb_status iblb_autotune(iblb_handle h, int trials, iblb_tuning* chosen)
 {
     if (!h || trials < 1) return h ? fail(h, IBLB_EINVAL, "trials must be >= 1") : IBLB_EINVAL;
-    struct Cand {
-        int variant, block_x, rows, ctas;
-    };
-    std::vector<Cand> cands = {{0, 64, 2, 2}, {0, 128, 2, 2}, {0, 256, 2, 2}};
-    const int rows_opts[] = {1, 2, 4};
-    for (int ctas = 1; ctas <= 2; ctas++)
-        for (int r : rows_opts) {
+    std::vector<Tuning> cands;
+    for (int bx : {64, 128, 256}) {
+        Tuning t;
+        t.variant = 0;
+        t.block_x = bx;
+        cands.push_back(t);
+    }
+    const int shapes[3][2] = {{2, 8}, {1, 16}, {1, 32}};
+    for (const auto& sh : shapes)
+        for (int r : {1, 2, 4}) {
             PipeShape ps{};
-            if (pipe_shape(h->Q, h->storage, h->g, h->sm_count, h->smem, r, ctas, ps))
-                cands.push_back({1, 128, r, ctas});
+            if (!pipe_shape(h->Q, h->storage, h->g, h->sm_count, h->smem, r, sh[0], sh[1], ps))
+                continue;
+            if (ps.mode != PIPE_ROWS && r != 1) continue;  // rows only matter in rows mode
+            Tuning t;
+            t.variant = 1;
+            t.rows_per_tile = r;
+            t.ctas_per_sm = sh[0];
+            t.consumer_warps = sh[1];
+            cands.push_back(t);
         }
     CK(h, cudaStreamSynchronize(h->stream));
-    const Tuning saved = h->tune;
-    const PipeShape saved_ps = h->pipe;
-    const bool saved_ok = h->pipe_ok;
     cudaEvent_t e0, e1;
     CK(h, cudaEventCreate(&e0));
     CK(h, cudaEventCreate(&e1));
     float best = 1e30f;
-    Cand pick = {saved.variant, saved.block_x, saved.rows_per_tile, saved.ctas_per_sm};
-    for (const Cand& c : cands) {
-        h->tune.variant = c.variant;
-        h->tune.block_x = c.block_x;
-        h->tune.rows_per_tile = c.rows;
-        h->tune.ctas_per_sm = c.ctas;
-        h->pipe_ok = pipe_shape(h->Q, h->storage, h->g, h->sm_count, h->smem, c.rows, c.ctas,
-                                h->pipe);
+    Tuning pick = h->tune;
+    for (const Tuning& c : cands) {
+        apply_tuning(h, c);
         // trial launches read f[cur] and write the scratch buffer f[cur ^ 1]
         // only: with every band flag clear no other state is touched
         launch_sc(h, h->stream, false);
@@ -683,21 +708,9 @@ iblb_status iblb_autotune(iblb_handle h, int trials, int* chosen)
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    (void)saved_ps;
-    (void)saved_ok;
     clear_graphs(h);
-    h->tune.variant = pick.variant;
-    h->tune.block_x = pick.block_x;
-    h->tune.rows_per_tile = pick.rows;
-    h->tune.ctas_per_sm = pick.ctas;
-    h->pipe_ok = pipe_shape(h->Q, h->storage, h->g, h->sm_count, h->smem, pick.rows, pick.ctas,
-                            h->pipe);
-    if (chosen) {
-        chosen[0] = pick.variant;
-        chosen[1] = pick.block_x;
-        chosen[2] = pick.rows;
-        chosen[3] = pick.ctas;
-    }
+    apply_tuning(h, pick);
+    if (chosen) iblb_get_tuning(h, chosen);
     CK(h, cudaGetLastError());
     return check_device_flag(h);
 }

@@ -85,11 +85,13 @@ __global__ void k_forces_ring(const double* __restrict__ q, int N, ForceParams f
 
 // 3D mesh, pass 1: one thread per face computes the unit normal nu_f, the
 // area A_f and, for each corner v, g_v = nu_f x (prev - next), so that
-// d(A_f)/d(corner v) = g_v / 2.  Record: nu[3], A, g[3][3], pad (16 doubles).
-constexpr int FACE_REC = 16;
+// d(A_f)/d(corner v) = g_v / 2.  It writes one record per (face, corner) at
+// the position of that pair in the node -> face CSR list (entry_pos), so that
+// each node's records are contiguous: g_v[3], nu[3], A, pad (8 doubles).
+constexpr int ENTRY_REC = 8;
 
 __global__ void k_face_geometry(const double* __restrict__ q, const int* __restrict__ tri, int M,
-                                double* __restrict__ rec)
+                                const int* __restrict__ entry_pos, double* __restrict__ rec)
 {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= M) return;
@@ -105,50 +107,43 @@ __global__ void k_face_geometry(const double* __restrict__ q, const int* __restr
     const double nlen = sqrt(nf[0] * nf[0] + nf[1] * nf[1] + nf[2] * nf[2]);
     const double inv = 1.0 / nlen;
     const double nu[3] = {nf[0] * inv, nf[1] * inv, nf[2] * inv};
-    double* r = rec + (long long)FACE_REC * f;
-    r[0] = nu[0];
-    r[1] = nu[1];
-    r[2] = nu[2];
-    r[3] = 0.5 * nlen;
+    const double area = 0.5 * nlen;
     for (int v = 0; v < 3; v++) {
         const double* nxt = P[(v + 1) % 3];
         const double* prv = P[(v + 2) % 3];
         const double e3[3] = {prv[0] - nxt[0], prv[1] - nxt[1], prv[2] - nxt[2]};
-        r[4 + 3 * v + 0] = nu[1] * e3[2] - nu[2] * e3[1];
-        r[4 + 3 * v + 1] = nu[2] * e3[0] - nu[0] * e3[2];
-        r[4 + 3 * v + 2] = nu[0] * e3[1] - nu[1] * e3[0];
+        double* r = rec + (long long)ENTRY_REC * entry_pos[3 * f + v];
+        r[0] = nu[1] * e3[2] - nu[2] * e3[1];
+        r[1] = nu[2] * e3[0] - nu[0] * e3[2];
+        r[2] = nu[0] * e3[1] - nu[1] * e3[0];
+        r[3] = nu[0];
+        r[4] = nu[1];
+        r[5] = nu[2];
+        r[6] = area;
     }
 }
 
-// 3D mesh, pass 2: eight lanes per node gather its faces from a CSR list of
-// (face, corner) entries (lane k takes entries k, k + 8, ...), then reduce by
-// shuffles; no atomics.
+// 3D mesh, pass 2: one thread per node sums its contiguous records (faces in
+// increasing order, the summation order of a face loop; no atomics).
 __global__ void k_node_forces(const double* __restrict__ q, int N, const double* __restrict__ rec,
-                              const int* __restrict__ csr_ptr, const int* __restrict__ csr_ent,
-                              ForceParams fp, double* __restrict__ phi, double* __restrict__ nrm,
+                              const int* __restrict__ csr_ptr, ForceParams fp,
+                              double* __restrict__ phi, double* __restrict__ nrm,
                               double* __restrict__ chi, int* err)
 {
-    const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const int j = (int)(gt >> 3);
-    const int sub = (int)(gt & 7);
-    double v[7] = {0, 0, 0, 0, 0, 0, 0};  // tension[3], normal sum[3], area
-    if (j < N) {
-        for (int e = csr_ptr[j] + sub; e < csr_ptr[j + 1]; e += 8) {
-            const int ent = csr_ent[e];
-            const int f = ent / 3, c = ent - 3 * (ent / 3);
-            const double* r = rec + (long long)FACE_REC * f;
-            for (int k = 0; k < 3; k++) {
-                v[k] -= fp.sigma * 0.5 * r[4 + 3 * c + k];
-                v[3 + k] += r[k];
-            }
-            v[6] += r[3];
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    double fs[3] = {0, 0, 0}, ns[3] = {0, 0, 0}, area = 0.0;
+    const int e0 = csr_ptr[j], e1 = csr_ptr[j + 1];
+    for (int e = e0; e < e1; e++) {
+        const double* r = rec + (long long)ENTRY_REC * e;
+        for (int k = 0; k < 3; k++) {
+            fs[k] -= fp.sigma * 0.5 * r[k];
+            ns[k] += r[3 + k];
         }
+        area += r[6];
     }
-    for (int o = 4; o > 0; o >>= 1)
-        for (int k = 0; k < 7; k++) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-    if (sub != 0 || j >= N) return;
-    const double nl = sqrt(v[3] * v[3] + v[4] * v[4] + v[5] * v[5]);
-    const double nh[3] = {v[3] / nl, v[4] / nl, v[5] / nl};
+    const double nl = sqrt(ns[0] * ns[0] + ns[1] * ns[1] + ns[2] * ns[2]);
+    const double nh[3] = {ns[0] / nl, ns[1] / nl, ns[2] / nl};
     double pi = 0.0;
     if (fp.wetting) {
         const double d = q[3 * j + 2] - fp.wall_plane;
@@ -156,14 +151,14 @@ __global__ void k_node_forces(const double* __restrict__ q, int N, const double*
         pi = wetting_pi(fp, d);
     }
     for (int k = 0; k < 3; k++) {
-        phi[3 * j + k] = v[k] + (-v[6] * pi * nh[k]) / 3.0;
+        phi[3 * j + k] = fs[k] + (-area * pi * nh[k]) / 3.0;
         if (nrm) nrm[3 * j + k] = nh[k];
     }
-    if (chi) chi[j] = v[6];
+    if (chi) chi[j] = area;
 }
 
 void launch_forces(int dim, const double* q, int N, int M, const int* tri, const int* csr_ptr,
-                   const int* csr_ent, double* face_rec, const ForceParams& fp, double* phi,
+                   const int* entry_pos, double* entry_rec, const ForceParams& fp, double* phi,
                    double* normal, double* chi, int* err, cudaStream_t s)
 {
     if (dim == 2) {
@@ -171,10 +166,9 @@ void launch_forces(int dim, const double* q, int N, int M, const int* tri, const
         k_forces_ring<<<g, b, 0, s>>>(q, N, fp, phi, normal, chi, err);
     } else {
         const int b = 64;
-        k_face_geometry<<<(M + b - 1) / b, b, 0, s>>>(q, tri, M, face_rec);
-        const long long t = 8LL * N;
-        k_node_forces<<<(int)((t + 127) / 128), 128, 0, s>>>(q, N, face_rec, csr_ptr, csr_ent, fp,
-                                                             phi, normal, chi, err);
+        k_face_geometry<<<(M + b - 1) / b, b, 0, s>>>(q, tri, M, entry_pos, entry_rec);
+        k_node_forces<<<(N + b - 1) / b, b, 0, s>>>(q, N, entry_rec, csr_ptr, fp, phi, normal,
+                                                    chi, err);
     }
 }
 

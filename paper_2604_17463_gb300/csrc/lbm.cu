@@ -102,7 +102,7 @@ k_stream_collide(const typename StorageT<ST>::S* __restrict__ fin,
             g[i] = T::load(fin, (long long)i * nc + src, p.inv_scale);
     }
 
-    R Fx = param_body<R>(p, 0), Fy = param_body<R>(p, 1), Fz = param_body<R>(p, 2);
+    R Fx = (R)p.body[0], Fy = (R)p.body[1], Fz = (R)p.body[2];
     if (band) {
         Fx += F[cell];
         Fy += F[nc + cell];
@@ -114,7 +114,7 @@ k_stream_collide(const typename StorageT<ST>::S* __restrict__ fin,
         }
     }
     const CellMoments<Q, R> mo = cell_moments<Q, R>(g, Fx, Fy, Fz);
-    cell_collide<Q, R>(g, mo, param_omega<R>(p), Fx, Fy, Fz);
+    cell_collide<Q, R>(g, mo, (R)p.omega, Fx, Fy, Fz);
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         if (CS)

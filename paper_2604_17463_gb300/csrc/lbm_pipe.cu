@@ -180,9 +180,9 @@ __device__ __forceinline__ void source_row(const GridParams& g, int y, int z, in
     }
 }
 
-// NC consumer warps per CTA: 8 with two CTAs per SM, 16 with one.
+// NC consumer warps per CTA: 8 with two CTAs per SM, 16 or 32 with one.
 template <int Q, int ST, bool WRITE_ALL, int NC>
-__global__ void __launch_bounds__(32 * (NC + 1), 16 / NC)
+__global__ void __launch_bounds__(32 * (NC + 1), NC == 8 ? 2 : 1)
 k_sc_pipe(const typename StorageT<ST>::S* __restrict__ fin,
           typename StorageT<ST>::S* __restrict__ fout, typename StorageT<ST>::R* __restrict__ mom,
           typename StorageT<ST>::R* __restrict__ F, uint8_t* __restrict__ flags,
@@ -376,8 +376,11 @@ static int dyn_smem_limit(const SmemLimits& lim, int ctas_per_sm)
 }
 
 bool pipe_shape(int Q, int storage, const GridParams& g, int sm_count, const SmemLimits& lim,
-                int rows_per_tile, int ctas_per_sm, PipeShape& ps)
+                int rows_per_tile, int ctas_per_sm, int consumer_warps, PipeShape& ps)
 {
+    if (ctas_per_sm == 2 && consumer_warps != 8) return false;
+    if (ctas_per_sm == 1 && consumer_warps != 16 && consumer_warps != 32) return false;
+    ps.consumer_warps = consumer_warps;
     const int elt = elt_of(storage);
     const int halo = 16 / elt;
     const int woff = g.walls ? 1 : 0;
@@ -449,7 +452,9 @@ static cudaError_t launch_pipe_t(bool write_all, const void* fin, void* fout, vo
     auto* b = (typename T::S*)fout;
     auto* m = (typename T::R*)mom;
     auto* f = (typename T::R*)F;
-    if (ps.ctas_per_sm == 1)
+    if (ps.consumer_warps == 32)
+        launch_pipe_nc<Q, ST, 32>(write_all, a, b, m, f, flags, p, ps, s);
+    else if (ps.consumer_warps == 16)
         launch_pipe_nc<Q, ST, 16>(write_all, a, b, m, f, flags, p, ps, s);
     else
         launch_pipe_nc<Q, ST, 8>(write_all, a, b, m, f, flags, p, ps, s);
@@ -464,6 +469,8 @@ static cudaError_t prepare_t(int bytes)
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sc_pipe<Q, ST, false, 8>, a, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sc_pipe<Q, ST, true, 16>, a, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sc_pipe<Q, ST, false, 16>, a, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sc_pipe<Q, ST, true, 32>, a, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sc_pipe<Q, ST, false, 32>, a, bytes);
     return e;
 }
 

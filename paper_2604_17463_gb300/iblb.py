@@ -55,6 +55,20 @@ class Config(ctypes.Structure):
     ]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [
+        ("variant", ctypes.c_int),
+        ("block_x", ctypes.c_int),
+        ("streaming_stores", ctypes.c_int),
+        ("rows_per_tile", ctypes.c_int),
+        ("ctas_per_sm", ctypes.c_int),
+        ("consumer_warps", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class Obs(ctypes.Structure):
     _fields_ = [
         ("mass", ctypes.c_double),
@@ -105,9 +119,10 @@ def load():
         "iblb_force_field": (st, [vp, dp]),
         "iblb_interpolate": (st, [vp, dp, dp]),
         "iblb_step_profiled": (st, [vp, ip, dp]),
-        "iblb_set_tuning": (st, [vp, ip, ip, ip, ip, ip]),
+        "iblb_set_tuning": (st, [vp, ctypes.POINTER(Tuning)]),
+        "iblb_get_tuning": (st, [vp, ctypes.POINTER(Tuning)]),
         "iblb_stream_collide_variant": (ctypes.c_int, [vp]),
-        "iblb_autotune": (st, [vp, ip, ctypes.POINTER(ctypes.c_int)]),
+        "iblb_autotune": (st, [vp, ip, ctypes.POINTER(Tuning)]),
         "iblb_mass_static": (st, [vp, ip, ip, ip, ip, ip, ip, ip, vp, vp]),
         "iblb_stream_bytes_per_step": (ctypes.c_double, [vp]),
         "iblb_fluid_cells": (ctypes.c_longlong, [vp]),
@@ -235,15 +250,22 @@ def iblb_step_profiled(h, n_steps: int) -> np.ndarray:
 
 
 def iblb_set_tuning(h, variant: int, block_x: int = 128, streaming_stores: int = 0,
-                    rows_per_tile: int = 2, ctas_per_sm: int = 2):
-    _check(h, load().iblb_set_tuning(h, int(variant), int(block_x), int(streaming_stores),
-                                     int(rows_per_tile), int(ctas_per_sm)))
+                    rows_per_tile: int = 2, ctas_per_sm: int = 2, consumer_warps: int = 8):
+    t = Tuning(int(variant), int(block_x), int(streaming_stores), int(rows_per_tile),
+               int(ctas_per_sm), int(consumer_warps))
+    _check(h, load().iblb_set_tuning(h, ctypes.byref(t)))
+
+
+def iblb_get_tuning(h) -> dict:
+    t = Tuning()
+    _check(h, load().iblb_get_tuning(h, ctypes.byref(t)))
+    return t.as_dict()
 
 
 def iblb_autotune(h, trials: int = 10) -> dict:
-    out = (ctypes.c_int * 4)()
-    _check(h, load().iblb_autotune(h, int(trials), out))
-    return {"variant": out[0], "block_x": out[1], "rows_per_tile": out[2], "ctas_per_sm": out[3]}
+    t = Tuning()
+    _check(h, load().iblb_autotune(h, int(trials), ctypes.byref(t)))
+    return t.as_dict()
 
 
 def iblb_mass_static(f_dev_ptr: int, lattice: int, storage: int, nx: int, ny: int, nz: int,
@@ -356,8 +378,12 @@ class Simulation:
         return qd
 
     def set_tuning(self, variant, block_x=128, streaming_stores=0, rows_per_tile=2,
-                   ctas_per_sm=2):
-        iblb_set_tuning(self.h, variant, block_x, streaming_stores, rows_per_tile, ctas_per_sm)
+                   ctas_per_sm=2, consumer_warps=8):
+        iblb_set_tuning(self.h, variant, block_x, streaming_stores, rows_per_tile, ctas_per_sm,
+                        consumer_warps)
+
+    def tuning(self):
+        return iblb_get_tuning(self.h)
 
     def autotune(self, trials=10):
         return iblb_autotune(self.h, trials)
