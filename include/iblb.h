@@ -164,7 +164,7 @@ iblb_status iblb_step_profiled(iblb_handle h, int n_steps, double* kernel_ms);
  *   variant 1: the pipelined kernel: persistent CTAs in which a producer warp
  *              stages the source rows in shared memory with bulk asynchronous
  *              copies and consumer_warps warps collide from there;
- *              ctas_per_sm = 2 with 8 consumer warps, or 1 with 16 or 32.
+ *              ctas_per_sm = 2 with 8 consumer warps, or 1 with 16 or 24.
  *              Usable when nx is a multiple of 32 up to 1024 (tiles of
  *              rows_per_tile whole rows) or a multiple of 256 (row
  *              segments); otherwise the plain kernel runs. */
@@ -183,7 +183,7 @@ iblb_status iblb_get_tuning(iblb_handle h, iblb_tuning* t);
 
 /* Autotuner: time every applicable launch shape (plain kernel with 64, 128
  * and 256-thread blocks; pipelined kernel with 1, 2 or 4 rows per tile and
- * 8, 16 or 32 consumer warps) over `trials` launches each and keep the
+ * 8, 16 or 24 consumer warps) over `trials` launches each and keep the
  * fastest.  The trial launches read the current populations and write only
  * the second (scratch) population buffer, so the simulation state is left
  * unchanged.  `chosen` (may be NULL) receives the kept shape.  Synchronises. */

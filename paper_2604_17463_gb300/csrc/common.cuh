@@ -98,7 +98,7 @@ struct Tuning {
     int streaming_stores = 0;   // plain kernel: evict-first stores of the new populations
     int rows_per_tile = 2;      // pipelined kernel, rows mode: rows per tile
     int ctas_per_sm = 2;        // pipelined kernel: resident CTAs per SM (1 or 2)
-    int consumer_warps = 8;     // pipelined kernel: 8 (2 CTAs/SM), 16 or 32 (1 CTA/SM)
+    int consumer_warps = 8;     // pipelined kernel: 8 (2 CTAs/SM), 16 or 24 (1 CTA/SM)
 };
 
 // Shape of the pipelined stream-collide launch (see lbm_pipe.cu).
@@ -115,7 +115,7 @@ struct PipeShape {
     long long tx_bytes;    // bytes copied per full stage
     int stages;            // pipeline depth per CTA
     int ctas_per_sm;
-    int consumer_warps;    // consumer warps per CTA (8, 16 or 32)
+    int consumer_warps;    // consumer warps per CTA (8, 16 or 24)
     int smem_bytes;        // dynamic shared memory per CTA
     int grid;              // persistent CTAs
 };

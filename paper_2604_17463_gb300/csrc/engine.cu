@@ -98,14 +98,15 @@ void clear_graphs(iblb_sim* h)
 int force_kernels(const iblb_sim* h) { return h->dim == 3 ? 2 : 1; }
 int kernels_per_step(const iblb_sim* h) { return h->N > 0 ? 3 + force_kernels(h) : 1; }
 
-void launch_sc(iblb_sim* h, cudaStream_t s, bool write_all)
+cudaError_t launch_sc(iblb_sim* h, cudaStream_t s, bool write_all)
 {
     if (h->tune.variant == 1 && h->pipe_ok)
-        launch_stream_collide_pipe(h->Q, h->storage, write_all, h->f[h->cur], h->f[h->cur ^ 1],
-                                   h->mom, h->F, h->flags, h->sp, h->pipe, s);
-    else
-        launch_stream_collide(h->Q, h->storage, write_all, h->f[h->cur], h->f[h->cur ^ 1], h->mom,
-                              h->F, h->flags, h->sp, h->tune, s);
+        return launch_stream_collide_pipe(h->Q, h->storage, write_all, h->f[h->cur],
+                                          h->f[h->cur ^ 1], h->mom, h->F, h->flags, h->sp,
+                                          h->pipe, s);
+    launch_stream_collide(h->Q, h->storage, write_all, h->f[h->cur], h->f[h->cur ^ 1], h->mom,
+                          h->F, h->flags, h->sp, h->tune, s);
+    return cudaPeekAtLastError();
 }
 
 // Enqueue one time step on stream s (buffers by the current parity).
@@ -201,6 +202,7 @@ iblb_status iblb_create(const iblb_config* cfg, void* cuda_stream, iblb_handle* 
 {
     if (!cfg || !out) return IBLB_EINVAL;
     *out = nullptr;
+    (void)cudaGetLastError();  // errors of earlier, unrelated calls are not ours to report
     g_create_error = "iblb_create: invalid configuration";
     const iblb_config& c = *cfg;
     if (c.lattice != IBLB_D2Q9 && c.lattice != IBLB_D3Q19) return IBLB_EINVAL;
@@ -627,8 +629,8 @@ iblb_status iblb_set_tuning(iblb_handle h, const iblb_tuning* t)
     if (t->rows_per_tile < 1 || t->rows_per_tile > 64)
         return fail(h, IBLB_EINVAL, "rows_per_tile in 1..64");
     if (!((t->ctas_per_sm == 2 && t->consumer_warps == 8) ||
-          (t->ctas_per_sm == 1 && (t->consumer_warps == 16 || t->consumer_warps == 32))))
-        return fail(h, IBLB_EINVAL, "ctas_per_sm 2 with 8 consumer warps, or 1 with 16 or 32");
+          (t->ctas_per_sm == 1 && (t->consumer_warps == 16 || t->consumer_warps == 24))))
+        return fail(h, IBLB_EINVAL, "ctas_per_sm 2 with 8 consumer warps, or 1 with 16 or 24");
     CK(h, cudaStreamSynchronize(h->stream));
     clear_graphs(h);
     Tuning tu;
@@ -664,7 +666,7 @@ iblb_status iblb_autotune(iblb_handle h, int trials, iblb_tuning* chosen)
         t.block_x = bx;
         cands.push_back(t);
     }
-    const int shapes[3][2] = {{2, 8}, {1, 16}, {1, 32}};
+    const int shapes[3][2] = {{2, 8}, {1, 16}, {1, 24}};
     for (const auto& sh : shapes)
         for (int r : {1, 2, 4}) {
             PipeShape ps{};
@@ -688,7 +690,10 @@ iblb_status iblb_autotune(iblb_handle h, int trials, iblb_tuning* chosen)
         apply_tuning(h, c);
         // trial launches read f[cur] and write the scratch buffer f[cur ^ 1]
         // only: with every band flag clear no other state is touched
-        launch_sc(h, h->stream, false);
+        if (launch_sc(h, h->stream, false) != cudaSuccess) {  // shape not launchable here
+            (void)cudaGetLastError();
+            continue;
+        }
         cudaEventRecord(e0, h->stream);
         for (int t = 0; t < trials; t++) launch_sc(h, h->stream, false);
         cudaEventRecord(e1, h->stream);

@@ -180,7 +180,7 @@ __device__ __forceinline__ void source_row(const GridParams& g, int y, int z, in
     }
 }
 
-// NC consumer warps per CTA: 8 with two CTAs per SM, 16 or 32 with one.
+// NC consumer warps per CTA: 8 with two CTAs per SM, 16 or 24 with one.
 template <int Q, int ST, bool WRITE_ALL, int NC>
 __global__ void __launch_bounds__(32 * (NC + 1), NC == 8 ? 2 : 1)
 k_sc_pipe(const typename StorageT<ST>::S* __restrict__ fin,
@@ -379,7 +379,7 @@ bool pipe_shape(int Q, int storage, const GridParams& g, int sm_count, const Sme
                 int rows_per_tile, int ctas_per_sm, int consumer_warps, PipeShape& ps)
 {
     if (ctas_per_sm == 2 && consumer_warps != 8) return false;
-    if (ctas_per_sm == 1 && consumer_warps != 16 && consumer_warps != 32) return false;
+    if (ctas_per_sm == 1 && consumer_warps != 16 && consumer_warps != 24) return false;
     ps.consumer_warps = consumer_warps;
     const int elt = elt_of(storage);
     const int halo = 16 / elt;
@@ -452,8 +452,8 @@ static cudaError_t launch_pipe_t(bool write_all, const void* fin, void* fout, vo
     auto* b = (typename T::S*)fout;
     auto* m = (typename T::R*)mom;
     auto* f = (typename T::R*)F;
-    if (ps.consumer_warps == 32)
-        launch_pipe_nc<Q, ST, 32>(write_all, a, b, m, f, flags, p, ps, s);
+    if (ps.consumer_warps == 24)
+        launch_pipe_nc<Q, ST, 24>(write_all, a, b, m, f, flags, p, ps, s);
     else if (ps.consumer_warps == 16)
         launch_pipe_nc<Q, ST, 16>(write_all, a, b, m, f, flags, p, ps, s);
     else
@@ -469,8 +469,8 @@ static cudaError_t prepare_t(int bytes)
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sc_pipe<Q, ST, false, 8>, a, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sc_pipe<Q, ST, true, 16>, a, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sc_pipe<Q, ST, false, 16>, a, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sc_pipe<Q, ST, true, 32>, a, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sc_pipe<Q, ST, false, 32>, a, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sc_pipe<Q, ST, true, 24>, a, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sc_pipe<Q, ST, false, 24>, a, bytes);
     return e;
 }
 
