@@ -65,7 +65,7 @@ def ncu_traffic():
                 if ":" in line:
                     k, v = line.split(":", 1)
                     vals[k.strip()] = v.strip()
-        if vals.get("stream-collide sources sha256[:16]") != source_digest(SC_SOURCES):
+        if vals.get("stream-collide sources sha256 prefix") != source_digest(SC_SOURCES):
             return None
         return float(vals["dram bytes per launch"])
     except Exception:
