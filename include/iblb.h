@@ -197,6 +197,65 @@ int iblb_stream_collide_variant(iblb_handle h);
 double iblb_stream_bytes_per_step(iblb_handle h);
 long long iblb_fluid_cells(iblb_handle h);
 
+/* ---- batched engine and serving admission ----
+ *
+ * A batch advances many independent droplet simulations ("slots") of one
+ * lattice type and one storage form with shared launches: every phase of a
+ * time step is one launch over all active slots (the stream-collide phase a
+ * persistent kernel walking a (slot, tile) work list).  Slot state lives in
+ * one device arena of hbm_budget_bytes allocated at creation; a request is
+ * admitted when its footprint fits (first fit), else IBLB_EAGAIN.  Slots
+ * must have walls, no body force, and the batch's lattice and storage.
+ * Each slot's tile shape (cells per thread of the stream-collide tiles) is
+ * chosen at admission by timing the candidates on that slot (cached per
+ * lattice width).  Calls on one batch are not thread-safe. */
+typedef struct iblb_batch_s* iblb_batch;
+
+typedef struct {
+    int slots_used, slots_active, slots_done;
+    size_t arena_bytes, free_bytes;
+    long long kernel_launches;
+} iblb_batch_info;
+
+/* Device bytes one slot of this configuration and interface takes. */
+size_t iblb_batch_footprint(const iblb_config* cfg, int n_nodes, int n_faces);
+
+iblb_status iblb_batch_create(int lattice, int storage, size_t hbm_budget_bytes, int max_slots,
+                              void* cuda_stream, iblb_batch* out);
+void        iblb_batch_destroy(iblb_batch b);
+const char* iblb_batch_last_error(iblb_batch b);
+
+/* Admit a simulation at rest with the given interface (as iblb_set_interface)
+ * for n_steps steps; *slot_out receives its slot.  IBLB_EAGAIN: no free slot
+ * or no room in the arena now (retry after releases).  Synchronises. */
+iblb_status iblb_batch_admit(iblb_batch b, const iblb_config* cfg, const double* xyz, int n_nodes,
+                             const int* tri, int n_faces, long long n_steps, int* slot_out);
+
+/* Advance every active slot by up to max_steps steps (asynchronous).  A slot
+ * stops at its own last step and becomes done; *n_completed (may be NULL)
+ * counts the slots that completed during this call. */
+iblb_status iblb_batch_run(iblb_batch b, int max_steps, int* n_completed);
+iblb_status iblb_batch_sync(iblb_batch b);
+
+/* Slots that are done and not yet released (up to cap of them in
+ * done_slots; *n_done is their total number). */
+iblb_status iblb_batch_poll(iblb_batch b, int* done_slots, int cap, int* n_done);
+
+/* Steps done by a slot, and its latched device faults as a status. */
+iblb_status iblb_batch_slot_status(iblb_batch b, int slot, long long* steps_done);
+
+/* FP64 observables / fields of a slot (as iblb_observables / iblb_read_fields;
+ * the fields are those of the slot's last step).  Synchronise. */
+iblb_status iblb_batch_observables(iblb_batch b, int slot, iblb_obs* out);
+iblb_status iblb_batch_read_fields(iblb_batch b, int slot, double* rho, double* u, double* xyz);
+
+/* Free a slot and its arena memory. */
+iblb_status iblb_batch_release(iblb_batch b, int slot);
+iblb_status iblb_batch_stats(iblb_batch b, iblb_batch_info* info);
+
+/* The cells per thread chosen by the tile autotuner for a slot. */
+int iblb_batch_slot_tile(iblb_batch b, int slot);
+
 /* ---- mass reduction without device allocation ----
  *
  * The paper has no counterpart: this is a service of the library.

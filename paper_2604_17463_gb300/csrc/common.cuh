@@ -188,4 +188,7 @@ void launch_observables(int dim, const double* q, int N, const int* tri, int M,
                         const double* mass_partial, int n_partial, double xi, double wall_plane,
                         double* out, cudaStream_t s);
 
+// Kernel-launch accounting shared by the engines (iblb_kernel_launch_count).
+void add_launches(long long n);
+
 }  // namespace iblb

@@ -23,6 +23,11 @@ using namespace iblb;
 
 namespace {
 std::atomic<long long> g_launches{0};
+}
+
+void iblb::add_launches(long long n) { g_launches += n; }
+
+namespace {
 thread_local std::string g_create_error;  // why the last iblb_create on this thread failed
 }
 

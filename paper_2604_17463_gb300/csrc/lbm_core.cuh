@@ -131,4 +131,55 @@ __device__ __forceinline__ void cell_collide(R* g, const CellMoments<Q, R>& m, R
     }
 }
 
+// Pull streaming of one fluid cell (x, y, z) with halfway bounce-back at the
+// solid first/last layer of the wall axis (y in 2D, z in 3D) when walls != 0
+// and periodic wrap elsewhere: g_i = g*_i(x - c_i), or g*_opp(i)(x) when
+// x - c_i is solid.
+template <int Q, int ST>
+__device__ __forceinline__ void pull_cell(const typename StorageT<ST>::S* __restrict__ fin,
+                                          const GridParams& g, int x, int y, int z,
+                                          long long cell, float inv_scale,
+                                          typename StorageT<ST>::R* out)
+{
+    using L = Stencil<Q>;
+    constexpr int D = L::D;
+    const int nx = g.nx, ny = g.ny;
+    const long long nc = g.ncell;
+    const int xm = (x == 0) ? nx - 1 : x - 1;
+    const int xp = (x == nx - 1) ? 0 : x + 1;
+    const int Lw = (D == 2) ? ny : g.nz;
+    const int a = (D == 2) ? y : z;
+    int am = a - 1, ap = a + 1;
+    bool solid_m = false, solid_p = false;
+    if (g.walls) {
+        solid_m = (am == 0);
+        solid_p = (ap == Lw - 1);
+    } else {
+        if (am < 0) am = Lw - 1;
+        if (ap >= Lw) ap = 0;
+    }
+    int ym = y, yp = y;
+    if (D == 3) {
+        ym = (y == 0) ? ny - 1 : y - 1;
+        yp = (y == ny - 1) ? 0 : y + 1;
+    }
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        const int cx = L::cx(i), cy = L::cy(i);
+        const int sx = cx == 0 ? x : (cx > 0 ? xm : xp);
+        const int cw = (D == 2) ? cy : L::cz(i);
+        const int sa = cw == 0 ? a : (cw > 0 ? am : ap);
+        const bool solid = cw == 0 ? false : (cw > 0 ? solid_m : solid_p);
+        long long src;
+        if (D == 2) {
+            src = (long long)sa * nx + sx;
+        } else {
+            const int sy = cy == 0 ? y : (cy > 0 ? ym : yp);
+            src = ((long long)sa * ny + sy) * nx + sx;
+        }
+        out[i] = solid ? StorageT<ST>::load(fin, (long long)L::opp(i) * nc + cell, inv_scale)
+                       : StorageT<ST>::load(fin, (long long)i * nc + src, inv_scale);
+    }
+}
+
 }  // namespace iblb

@@ -87,6 +87,17 @@ class Obs(ctypes.Structure):
                 for k, _ in self._fields_}
 
 
+class BatchInfo(ctypes.Structure):
+    _fields_ = [
+        ("slots_used", ctypes.c_int),
+        ("slots_active", ctypes.c_int),
+        ("slots_done", ctypes.c_int),
+        ("arena_bytes", ctypes.c_size_t),
+        ("free_bytes", ctypes.c_size_t),
+        ("kernel_launches", ctypes.c_longlong),
+    ]
+
+
 _lib = None
 
 
@@ -124,6 +135,21 @@ def load():
         "iblb_stream_collide_variant": (ctypes.c_int, [vp]),
         "iblb_autotune": (st, [vp, ip, ctypes.POINTER(Tuning)]),
         "iblb_mass_static": (st, [vp, ip, ip, ip, ip, ip, ip, ip, vp, vp]),
+        "iblb_batch_footprint": (ctypes.c_size_t, [ctypes.POINTER(Config), ip, ip]),
+        "iblb_batch_create": (st, [ip, ip, ctypes.c_size_t, ip, vp, ctypes.POINTER(vp)]),
+        "iblb_batch_destroy": (None, [vp]),
+        "iblb_batch_last_error": (ctypes.c_char_p, [vp]),
+        "iblb_batch_admit": (st, [vp, ctypes.POINTER(Config), dp, ip, ctypes.POINTER(ctypes.c_int),
+                                  ip, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int)]),
+        "iblb_batch_run": (st, [vp, ip, ctypes.POINTER(ctypes.c_int)]),
+        "iblb_batch_sync": (st, [vp]),
+        "iblb_batch_poll": (st, [vp, ctypes.POINTER(ctypes.c_int), ip, ctypes.POINTER(ctypes.c_int)]),
+        "iblb_batch_slot_status": (st, [vp, ip, ctypes.POINTER(ctypes.c_longlong)]),
+        "iblb_batch_observables": (st, [vp, ip, ctypes.POINTER(Obs)]),
+        "iblb_batch_read_fields": (st, [vp, ip, dp, dp, dp]),
+        "iblb_batch_release": (st, [vp, ip]),
+        "iblb_batch_stats": (st, [vp, ctypes.POINTER(BatchInfo)]),
+        "iblb_batch_slot_tile": (ctypes.c_int, [vp, ip]),
         "iblb_stream_bytes_per_step": (ctypes.c_double, [vp]),
         "iblb_fluid_cells": (ctypes.c_longlong, [vp]),
         "iblb_kernel_launch_count": (ctypes.c_longlong, []),
@@ -402,3 +428,114 @@ class Simulation:
     @property
     def stream_bytes_per_step(self):
         return iblb_stream_bytes_per_step(self.h)
+
+
+# ------------------------------------------------------------------ batch
+class Batch:
+    """Many droplet simulations of one lattice type and storage form advanced
+    by shared launches (libiblb's batched engine)."""
+
+    def __init__(self, lattice: int, storage: int, hbm_budget_bytes: int, max_slots: int = 1024,
+                 stream: Optional[int] = None):
+        lib = load()
+        self.lattice = lattice
+        self.storage = storage
+        self.dim = 2 if lattice == D2Q9 else 3
+        h = ctypes.c_void_p()
+        s = current_stream_handle() if stream is None else stream
+        st = lib.iblb_batch_create(int(lattice), int(storage), int(hbm_budget_bytes),
+                                   int(max_slots), ctypes.c_void_p(s), ctypes.byref(h))
+        if st != IBLB_OK:
+            raise IBLBError(st, "iblb_batch_create")
+        self.h = h
+        self.max_slots = max_slots
+        self.meta = {}
+
+    def _check(self, st):
+        if st != IBLB_OK:
+            raise IBLBError(st, (load().iblb_batch_last_error(self.h) or b"").decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().iblb_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def footprint(cfg: Config, n_nodes: int, n_faces: int = 0) -> int:
+        return int(load().iblb_batch_footprint(ctypes.byref(cfg), int(n_nodes), int(n_faces)))
+
+    def admit(self, cfg: Config, xyz, tri=None, n_steps: int = 1000) -> Optional[int]:
+        """Slot index, or None if the batch has no room right now."""
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, self.dim)
+        t = None if tri is None else np.ascontiguousarray(tri, dtype=np.int32).reshape(-1, 3)
+        tp = None if t is None else t.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        slot = ctypes.c_int(-1)
+        st = load().iblb_batch_admit(self.h, ctypes.byref(cfg), _dptr(xyz), xyz.shape[0], tp,
+                                     0 if t is None else t.shape[0], int(n_steps),
+                                     ctypes.byref(slot))
+        if st == 7:  # IBLB_EAGAIN
+            return None
+        self._check(st)
+        self.meta[slot.value] = (cfg, xyz.shape[0])
+        return slot.value
+
+    def admit_workload(self, wl, n_steps=None, **over) -> Optional[int]:
+        kw = dict(tau=wl.tau, walls=wl.walls, wetting=wl.wetting, sigma=wl.sigma, xi=wl.xi,
+                  theta_eq_deg=wl.theta_eq_deg, pi_n=wl.pi_n, pi_m=wl.pi_m, storage=self.storage)
+        kw.update(over)
+        cfg = make_config(wl.lattice, wl.nx, wl.ny, wl.nz, **kw)
+        return self.admit(cfg, wl.nodes, wl.faces, wl.steps if n_steps is None else n_steps)
+
+    def run(self, max_steps: int) -> int:
+        done = ctypes.c_int(0)
+        self._check(load().iblb_batch_run(self.h, int(max_steps), ctypes.byref(done)))
+        return done.value
+
+    def sync(self):
+        self._check(load().iblb_batch_sync(self.h))
+
+    def poll(self):
+        n = ctypes.c_int(0)
+        buf = (ctypes.c_int * self.max_slots)()
+        self._check(load().iblb_batch_poll(self.h, buf, self.max_slots, ctypes.byref(n)))
+        return [buf[i] for i in range(min(n.value, self.max_slots))]
+
+    def steps_done(self, slot: int) -> int:
+        v = ctypes.c_longlong(0)
+        self._check(load().iblb_batch_slot_status(self.h, int(slot), ctypes.byref(v)))
+        return v.value
+
+    def observables(self, slot: int) -> dict:
+        o = Obs()
+        self._check(load().iblb_batch_observables(self.h, int(slot), ctypes.byref(o)))
+        return o.as_dict()
+
+    def fields(self, slot: int):
+        cfg, n = self.meta[slot]
+        nz = 1 if self.dim == 2 else cfg.nz
+        ncell = cfg.nx * cfg.ny * nz
+        rho = np.zeros(ncell)
+        u = np.zeros(self.dim * ncell)
+        q = np.zeros(n * self.dim)
+        self._check(load().iblb_batch_read_fields(self.h, int(slot), _dptr(rho), _dptr(u),
+                                                  _dptr(q)))
+        shape = (nz, cfg.ny, cfg.nx)
+        return rho.reshape(shape), u.reshape((self.dim,) + shape), q.reshape(n, self.dim)
+
+    def release(self, slot: int):
+        self._check(load().iblb_batch_release(self.h, int(slot)))
+        self.meta.pop(slot, None)
+
+    def tile(self, slot: int) -> int:
+        return load().iblb_batch_slot_tile(self.h, int(slot))
+
+    def info(self) -> dict:
+        i = BatchInfo()
+        self._check(load().iblb_batch_stats(self.h, ctypes.byref(i)))
+        return {k: getattr(i, k) for k, _ in i._fields_}
