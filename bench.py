@@ -327,6 +327,99 @@ def run_ours(args, wl):
     return 0
 
 
+def run_batch_mode(args):
+    """Batched engine on the 256-drop workload (widths 64-1024, step counts
+    scaled by 1/step_div): sequential single-engine FP32 vs batched FP32 and
+    batched binary16 storage; sims/hour and the contact-angle difference of
+    the reduced-precision batch against the sequential FP32 runs."""
+    import torch
+    from paper_2604_17463_gb300 import iblb, serve
+    from paper_2604_17463_gb300 import workloads as W
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    wls = W.config4(count=args.count, steps_lo=5000 // args.step_div, steps_hi=50000 // args.step_div)
+    stream = torch.cuda.current_stream().cuda_stream
+    n0 = iblb.iblb_kernel_launch_count()
+    seq = serve.run_sequential(wls, iblb.FP32_DEV, stream=stream)
+    b32 = serve.run_batched(wls, iblb.FP32_DEV, 16 << 30, stream=stream)
+    b16 = serve.run_batched(wls, iblb.FP16_DEV, 16 << 30, stream=stream)
+    launches = iblb.iblb_kernel_launch_count() - n0
+
+    def dtheta(a, b):
+        d = [abs(x["theta_deg"] - y["theta_deg"]) for x, y in zip(a["obs"], b["obs"])
+             if np.isfinite(x["theta_deg"]) and np.isfinite(y["theta_deg"])]
+        return max(d) if d else None, len(d)
+
+    cells_steps = sum(w.fluid_cells * w.steps for w in wls)
+    d16, n16 = dtheta(b16, seq)
+    d32, n32 = dtheta(b32, seq)
+    line = {
+        "metric": "sims_per_hour", "value": len(wls) / b16["wall_s"] * 3600, "unit": "sims/h",
+        "n_gpus": 1, "higher_is_better": True, "data": "synthetic", "dtype": "f32 (binary16 storage)",
+        "config": {"workload": f"{len(wls)} D2Q9 drops, widths 64-1024 log-uniform, height w/4, "
+                               f"steps U[{5000 // args.step_div}, {50000 // args.step_div}]",
+                   "mode": "batch"},
+        "sequential_fp32": {"sims_per_hour": len(wls) / seq["wall_s"] * 3600, "wall_s": seq["wall_s"],
+                            "mlups": cells_steps / seq["wall_s"] / 1e6},
+        "batched_fp32": {"sims_per_hour": len(wls) / b32["wall_s"] * 3600, "wall_s": b32["wall_s"],
+                         "mlups": cells_steps / b32["wall_s"] / 1e6, "max_dtheta_deg_vs_seq": d32,
+                         "compared": n32},
+        "batched_fp16": {"sims_per_hour": len(wls) / b16["wall_s"] * 3600, "wall_s": b16["wall_s"],
+                         "mlups": cells_steps / b16["wall_s"] / 1e6, "max_dtheta_deg_vs_seq": d16,
+                         "compared": n16},
+        "gpu_launches": int(launches),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve_mode(args):
+    """Serving loop on a Poisson stream of wetting requests (80 % 2D as the
+    batched workload, 20 % D3Q19 between 64^3 and 192x192x96; step counts
+    scaled by 1/step_div); contact angles of a sample of the smallest 2D
+    requests compared with the FP64 oracle."""
+    import torch
+    from paper_2604_17463_gb300 import iblb, serve
+    from paper_2604_17463_gb300 import workloads as W
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    reqs = W.config5(count=args.count, rate_per_s=args.rate, steps_lo=5000 // args.step_div,
+                     steps_hi=50000 // args.step_div)
+    storage = {"fp32": iblb.FP32_DEV, "fp16": iblb.FP16_DEV, "fp64": iblb.FP64}[args.storage]
+    n0 = iblb.iblb_kernel_launch_count()
+    out = serve.serve(reqs, storage, budget_2d=24 << 30, budget_3d=96 << 30, chunk=args.chunk)
+    launches = iblb.iblb_kernel_launch_count() - n0
+    # oracle check on the smallest 2D requests
+    import oracle
+    small = sorted([i for i, r in enumerate(reqs) if r.work.lattice == 9],
+                   key=lambda i: reqs[i].work.cells * reqs[i].work.steps)[:args.oracle_sample]
+    errs = []
+    for i in small:
+        wl = reqs[i].work
+        o = oracle.Sim(9, wl.nx, wl.ny, tau=wl.tau, sigma=wl.sigma, xi=wl.xi,
+                       theta_eq_deg=wl.theta_eq_deg, pi_n=wl.pi_n, pi_m=wl.pi_m)
+        o.set_interface(wl.nodes)
+        o.step(wl.steps)
+        th = o.observables()["theta_deg"]
+        o.close()
+        got = out["results"][i]["theta_deg"]
+        if np.isfinite(th) and np.isfinite(got):
+            errs.append(abs(th - got))
+    line = {
+        "metric": "sims_per_hour", "value": out["sims_per_hour"], "unit": "sims/h", "n_gpus": 1,
+        "higher_is_better": True, "data": "synthetic",
+        "dtype": {"fp32": "f32", "fp16": "f32 (binary16 storage)", "fp64": "f64"}[args.storage],
+        "config": {"workload": f"{len(reqs)} Poisson requests at {args.rate}/s, 80% D2Q9 "
+                               f"(w 64-1024), 20% D3Q19 (64^3-192x192x96), steps "
+                               f"U[{5000 // args.step_div}, {50000 // args.step_div}]",
+                   "mode": "serve", "chunk_steps": args.chunk},
+        "p50_s": out["p50_s"], "p99_s": out["p99_s"], "wall_s": out["wall_s"],
+        "completed": out["completed"], "mlups": out["mlups"], "max_queue": out["max_queue"],
+        "oracle_dtheta_deg": {"max": max(errs) if errs else None, "compared": len(errs)},
+        "gpu_launches": int(launches),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -335,12 +428,25 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve"],
+                    help="step: the 3D workload (default); batch / serve: the batched "
+                         "and served engines")
+    ap.add_argument("--count", type=int, default=256, help="batch / serve: simulations")
+    ap.add_argument("--step-div", type=int, default=10,
+                    help="batch / serve: divide the 5k-50k step counts by this")
+    ap.add_argument("--rate", type=float, default=20.0, help="serve: arrivals per second")
+    ap.add_argument("--chunk", type=int, default=500, help="serve: steps per scheduling round")
+    ap.add_argument("--oracle-sample", type=int, default=4, help="serve: oracle-checked requests")
     ap.add_argument("--tuning", default="",
                     help="fixed stream-collide launch shape 'variant,block_x,rows,ctas,warps' "
                          "instead of the autotuner (used for profiler runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.mode == "batch":
+        return run_batch_mode(args)
+    if args.mode == "serve":
+        return run_serve_mode(args)
     from paper_2604_17463_gb300 import workloads as W
     wl = W.config3()
     if args.impl == "reference":
