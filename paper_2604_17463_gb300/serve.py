@@ -127,6 +127,7 @@ def serve(requests, storage: int, budget_2d: int, budget_3d: int, chunk: int = 5
                 r = requests[i]
                 results[i].update({"done_s": t_done, "latency_s": t_done - r.arrival_s,
                                    "theta_deg": o["theta_deg"], "volume": o["volume"],
+                                   "height": o["height"],
                                    "name": r.work.name, "lattice": r.work.lattice,
                                    "cells": r.work.cells, "steps": r.work.steps})
     wall = time.perf_counter() - t0

@@ -52,7 +52,8 @@ def test_batch_slots_match_single_engine(storage, tol):
         m = fluid_mask(rho_s.shape, 2)
         assert rel_l2(u_b[:, m], u_s[:, m]) < tol
         assert rel_l2(rho_b[m] - 1, rho_s[m] - 1) < 10 * tol
-        assert np.max(np.abs(q_b - q_s)) < 1e-9
+        # node positions: FP64 agrees to round-off, FP32 to its own rounding
+        assert np.max(np.abs(q_b - q_s)) < (1e-11 if storage == iblb.FP64 else 1e-6)
         o_b = b.observables(s)
         assert abs(o_b["volume"] - o_s["volume"]) < 1e-8 * abs(o_s["volume"])
     b.close()
