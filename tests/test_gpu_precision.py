@@ -19,7 +19,7 @@ from helpers import fluid_mask, oracle_from_workload, rel_l2
 pytestmark = pytest.mark.gpu
 
 CHECKPOINTS = 8
-STEPS_PER = 2500
+STEPS_PER = 10000   # 80k steps, about 10 viscous times mu R / sigma
 
 
 def trajectory(wl, storage):

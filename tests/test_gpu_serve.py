@@ -30,11 +30,15 @@ def test_serving_completes_and_matches_alone():
 
 
 def test_small_budget_queues_requests():
-    # a budget that holds only a few requests at a time: the rest wait in the
-    # queue and are admitted as slots finish
-    reqs = W.config5(count=12, rate_per_s=1000.0, steps_lo=100, steps_hi=300, frac_3d=0.0)
-    big = max(iblb.Batch.footprint(iblb.make_config(9, r.work.nx, r.work.ny, storage=iblb.FP32_DEV),
-                                   r.work.nodes.shape[0]) for r in reqs)
-    out = serve.serve(reqs, iblb.FP32_DEV, budget_2d=3 * big, budget_3d=1 << 20, chunk=50)
+    # identical requests that all arrive at once, with a budget for two: the
+    # others wait in the queue and are admitted as slots finish
+    wl = W.droplet_2d(256, 60.0, 1.0, 200, name="q")
+    reqs = [W.Request(0.0, wl) for _ in range(6)]
+    fp = iblb.Batch.footprint(iblb.make_config(9, wl.nx, wl.ny, storage=iblb.FP32_DEV),
+                              wl.nodes.shape[0])
+    out = serve.serve(reqs, iblb.FP32_DEV, budget_2d=int(2.5 * fp), budget_3d=1 << 20, chunk=50)
     assert out["completed"] == len(reqs)
-    assert out["max_queue"] > 0
+    assert out["max_queue"] >= 4
+    done = sorted(r["done_s"] for r in out["results"])
+    # completions come in waves of two
+    assert done[2] > done[1] and done[4] > done[3]
