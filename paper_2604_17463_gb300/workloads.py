@@ -185,23 +185,26 @@ def config3() -> Workload:
 def droplet_2d(width: int, theta_eq_deg: float, tau: float, steps: int,
                name: str = "d2q9") -> Workload:
     """Batched / served 2D member: height = width / 4, R = height / 3,
-    10 nodes per unit radius, xi = max(0.05 R, 1 lu)."""
+    10 nodes per unit radius, xi = max(0.05 R, 1 lu); the lowest node starts
+    at the film distance xi from the wall (as the paper's drop placed at
+    d ~ eps from the wall, Sec. 4)."""
     ny = max(width // 4, 12)
     R = ny / 3.0
     xi = max(0.05 * R, 1.0)
     n = int(round(10 * R))
-    nodes = circle(n, R, (width / 2.0, WALL_PLANE + R + 2.0 * xi))
+    nodes = circle(n, R, (width / 2.0, WALL_PLANE + R + xi))
     return Workload(f"{name}_{width}x{ny}", 9, width, ny, 1, tau, 1e-3, xi, theta_eq_deg, 9, 3,
                     steps, nodes, None)
 
 
 def droplet_3d(nx: int, ny: int, nz: int, theta_eq_deg: float, tau: float, steps: int,
                name: str = "d3q19") -> Workload:
-    """Served 3D member: R = nz / 3, icosphere refined to mean edge <= 1.5 lu."""
+    """Served 3D member: R = nz / 3, icosphere refined to mean edge <= 1.5 lu,
+    lowest node at the film distance xi from the wall."""
     R = nz / 3.0
     xi = max(0.05 * R, 1.0)
     lvl = icosphere_level_for(R)
-    nodes, faces = icosphere(lvl, R, (nx / 2.0, ny / 2.0, WALL_PLANE + R + 2.0 * xi))
+    nodes, faces = icosphere(lvl, R, (nx / 2.0, ny / 2.0, WALL_PLANE + R + xi))
     return Workload(f"{name}_{nx}x{ny}x{nz}", 19, nx, ny, nz, tau, 1e-3, xi, theta_eq_deg, 9, 3,
                     steps, nodes, faces)
 
