@@ -133,6 +133,23 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(value: float, world: int, device: str = "cpu") -> float:
+    """The maximum of a per-rank time over all ranks (replicas: the job ends
+    when the slowest rank ends)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(cells_per_rank: int, steps: int, ms: float, world: int) -> float:
+    """Whole-job throughput: every rank updates its own replica's cells."""
+    return world * cells_per_rank * steps / (ms / 1e3) / 1e6
+
+
 def cpu_baseline_oracle(wl, steps):
     """FP64 CPU oracle on `steps` full time steps of the workload (1 thread)."""
     import oracle
@@ -239,14 +256,9 @@ def run_ours(args, wl):
     barrier()
     launches = iblb.iblb_kernel_launch_count() - n0
     sim.sync()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, device="cuda")
     ms_per_step = ms / args.steps
-    value = world * cells * args.steps / (ms / 1e3) / 1e6
+    value = whole_job_mlups(cells, args.steps, ms, world)
 
     # ---- per-kernel device times (CUDA events around each launch)
     prof_steps = max(5, min(args.steps, 200))
