@@ -161,6 +161,9 @@ iblb_status iblb_step_profiled(iblb_handle h, int n_steps, double* kernel_ms);
  *   variant 0: the plain kernel, one cell per thread, block_x threads per
  *              block along x (64, 128 or 256), evict-first stores of the new
  *              populations when streaming_stores != 0;
+ *   variant 2: two x-adjacent cells per thread with 8 / 4-byte population
+ *              loads and stores and packed FP32x2 arithmetic (FP32 and
+ *              binary16 storage, even nx), block_x threads per block;
  *   variant 1: the pipelined kernel: persistent CTAs in which a producer warp
  *              stages the source rows in shared memory with bulk asynchronous
  *              copies and consumer_warps warps collide from there;
@@ -182,14 +185,14 @@ iblb_status iblb_set_tuning(iblb_handle h, const iblb_tuning* t);
 iblb_status iblb_get_tuning(iblb_handle h, iblb_tuning* t);
 
 /* Autotuner: time every applicable launch shape (plain kernel with 64, 128
- * and 256-thread blocks; pipelined kernel with 1, 2 or 4 rows per tile and
+ * and 256-thread blocks; pair kernel likewise; pipelined kernel with 1, 2 or 4 rows per tile and
  * 8, 16 or 24 consumer warps) over `trials` launches each and keep the
  * fastest.  The trial launches read the current populations and write only
  * the second (scratch) population buffer, so the simulation state is left
  * unchanged.  `chosen` (may be NULL) receives the kept shape.  Synchronises. */
 iblb_status iblb_autotune(iblb_handle h, int trials, iblb_tuning* chosen);
 
-/* The stream-collide variant in use (0 plain, 1 pipelined). */
+/* The stream-collide variant in use (0 plain, 1 pipelined, 2 pairs). */
 int iblb_stream_collide_variant(iblb_handle h);
 
 /* Algorithmic HBM bytes of one stream-collide launch: populations read once

@@ -93,7 +93,7 @@ struct ForceParams {
 
 // Launch shape of the stream-collide kernel (chosen by the autotuner).
 struct Tuning {
-    int variant = 1;            // 0: plain kernel; 1: pipelined kernel where the shape allows
+    int variant = 1;            // 0: plain kernel; 1: pipelined kernel; 2: cell pairs (where the shape allows)
     int block_x = 128;          // plain kernel: threads per block along x (64, 128, 256)
     int streaming_stores = 0;   // plain kernel: evict-first stores of the new populations
     int rows_per_tile = 2;      // pipelined kernel, rows mode: rows per tile
@@ -136,6 +136,13 @@ enum Storage : int { ST_FP64 = 0, ST_FP32 = 1, ST_FP16 = 2 };
 void launch_stream_collide(int Q, int storage, bool write_all, const void* fin, void* fout,
                            void* moments, void* F, uint8_t* flags, const StreamParams& p,
                            const Tuning& tu, cudaStream_t s);
+
+// Pair variant (lbm.cu): two x-adjacent cells per thread, packed FP32x2
+// arithmetic; FP32 / binary16 storage with an even nx.
+bool pair_kernel_ok(int storage, const GridParams& g);
+void launch_stream_collide_pairs(int Q, int storage, bool write_all, const void* fin, void* fout,
+                                 void* moments, void* F, uint8_t* flags, const StreamParams& p,
+                                 const Tuning& tu, cudaStream_t s);
 
 // Pipelined variant (lbm_pipe.cu): usable when pipe_shape() returns true.
 bool pipe_shape(int Q, int storage, const GridParams& g, int sm_count, const SmemLimits& lim,

@@ -105,6 +105,11 @@ int kernels_per_step(const iblb_sim* h) { return h->N > 0 ? 3 + force_kernels(h)
 
 cudaError_t launch_sc(iblb_sim* h, cudaStream_t s, bool write_all)
 {
+    if (h->tune.variant == 2 && pair_kernel_ok(h->storage, h->g)) {
+        launch_stream_collide_pairs(h->Q, h->storage, write_all, h->f[h->cur], h->f[h->cur ^ 1],
+                                    h->mom, h->F, h->flags, h->sp, h->tune, s);
+        return cudaPeekAtLastError();
+    }
     if (h->tune.variant == 1 && h->pipe_ok)
         return launch_stream_collide_pipe(h->Q, h->storage, write_all, h->f[h->cur],
                                           h->f[h->cur ^ 1], h->mom, h->F, h->flags, h->sp,
@@ -628,7 +633,7 @@ iblb_status iblb_step_profiled(iblb_handle h, int n_steps, double* kernel_ms)
 iblb_status iblb_set_tuning(iblb_handle h, const iblb_tuning* t)
 {
     if (!h || !t) return IBLB_EINVAL;
-    if (t->variant != 0 && t->variant != 1) return fail(h, IBLB_EINVAL, "variant must be 0 or 1");
+    if (t->variant < 0 || t->variant > 2) return fail(h, IBLB_EINVAL, "variant must be 0, 1 or 2");
     if (t->block_x != 64 && t->block_x != 128 && t->block_x != 256)
         return fail(h, IBLB_EINVAL, "block_x must be 64, 128 or 256");
     if (t->rows_per_tile < 1 || t->rows_per_tile > 64)
@@ -652,7 +657,9 @@ iblb_status iblb_set_tuning(iblb_handle h, const iblb_tuning* t)
 iblb_status iblb_get_tuning(iblb_handle h, iblb_tuning* t)
 {
     if (!h || !t) return IBLB_EINVAL;
-    t->variant = (h->tune.variant == 1 && h->pipe_ok) ? 1 : 0;
+    t->variant = (h->tune.variant == 1 && h->pipe_ok)
+                     ? 1
+                     : ((h->tune.variant == 2 && pair_kernel_ok(h->storage, h->g)) ? 2 : 0);
     t->block_x = h->tune.block_x;
     t->streaming_stores = h->tune.streaming_stores;
     t->rows_per_tile = h->tune.rows_per_tile;
@@ -665,11 +672,14 @@ iblb_status iblb_autotune(iblb_handle h, int trials, iblb_tuning* chosen)
 {
     if (!h || trials < 1) return h ? fail(h, IBLB_EINVAL, "trials must be >= 1") : IBLB_EINVAL;
     std::vector<Tuning> cands;
-    for (int bx : {64, 128, 256}) {
-        Tuning t;
-        t.variant = 0;
-        t.block_x = bx;
-        cands.push_back(t);
+    for (int v : {0, 2}) {
+        if (v == 2 && !pair_kernel_ok(h->storage, h->g)) continue;
+        for (int bx : {64, 128, 256}) {
+            Tuning t;
+            t.variant = v;
+            t.block_x = bx;
+            cands.push_back(t);
+        }
     }
     const int shapes[3][2] = {{2, 8}, {1, 16}, {1, 24}};
     for (const auto& sh : shapes)
@@ -728,7 +738,9 @@ iblb_status iblb_autotune(iblb_handle h, int trials, iblb_tuning* chosen)
 int iblb_stream_collide_variant(iblb_handle h)
 {
     if (!h) return -1;
-    return (h->tune.variant == 1 && h->pipe_ok) ? 1 : 0;
+    if (h->tune.variant == 1 && h->pipe_ok) return 1;
+    if (h->tune.variant == 2 && pair_kernel_ok(h->storage, h->g)) return 2;
+    return 0;
 }
 
 double iblb_stream_bytes_per_step(iblb_handle h)

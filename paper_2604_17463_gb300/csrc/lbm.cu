@@ -193,6 +193,204 @@ void launch_stream_collide(int Q, int storage, bool write_all, const void* fin, 
     }
 }
 
+// ------------------------------------------------------------------ pairs
+// Variant 2: two x-adjacent cells per thread.  Populations move as float2 /
+// half2 (8 / 4 bytes per thread and plane); for the directions with c_x = +1
+// (-1) the source pair (x-1, x) ((x+1, x+2)) is assembled from the aligned
+// pair of the same source row and the neighbouring lane's value by a warp
+// shuffle, with one scalar load at warp and row ends (periodic wrap in x).
+// Moments and collision run in packed FP32x2 arithmetic.  Needs an even nx.
+template <int ST> struct Pair;
+
+template <> struct Pair<ST_FP32> {
+    __device__ __forceinline__ static float2 load2(const float* p, long long i, float)
+    {
+        return *reinterpret_cast<const float2*>(p + i);
+    }
+    __device__ __forceinline__ static float load1(const float* p, long long i, float) { return p[i]; }
+    __device__ __forceinline__ static void store2(float* p, long long i, float2 v, float)
+    {
+        *reinterpret_cast<float2*>(p + i) = v;
+    }
+};
+
+template <> struct Pair<ST_FP16> {
+    __device__ __forceinline__ static float2 load2(const __half* p, long long i, float inv_scale)
+    {
+        return mul2(__half22float2(*reinterpret_cast<const __half2*>(p + i)), p2(inv_scale));
+    }
+    __device__ __forceinline__ static float load1(const __half* p, long long i, float inv_scale)
+    {
+        return __half2float(p[i]) * inv_scale;
+    }
+    __device__ __forceinline__ static void store2(__half* p, long long i, float2 v, float scale)
+    {
+        *reinterpret_cast<__half2*>(p + i) = __float22half2_rn(mul2(v, p2(scale)));
+    }
+};
+
+template <int Q, int ST, bool WRITE_ALL, int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+k_stream_collide2(const typename StorageT<ST>::S* __restrict__ fin,
+                  typename StorageT<ST>::S* __restrict__ fout, float* __restrict__ mom,
+                  float* __restrict__ F, uint8_t* __restrict__ flags, const StreamParams p)
+{
+    using L = Stencil<Q>;
+    using P = Pair<ST>;
+    constexpr int D = L::D;
+    const int nx = p.g.nx, ny = p.g.ny;
+    const long long nc = p.g.ncell;
+    const int walls = p.g.walls;
+    const int woff = walls ? 1 : 0;
+    const float inv = p.inv_scale;
+
+    const int x0 = 2 * (blockIdx.x * BLOCK + threadIdx.x);
+    int y, z;
+    if (D == 2) {
+        y = blockIdx.y + woff;
+        z = 0;
+    } else {
+        y = blockIdx.y;
+        z = blockIdx.z + woff;
+    }
+    const int lane = threadIdx.x & 31;
+    const bool active = x0 < nx;
+    const long long row = (long long)z * ny + y;
+    const long long cell = row * nx + x0;
+    // band flags: lanes 0-15 share one 32-cell segment, lanes 16-31 the next
+    const long long seg = row * p.g.nseg_x + (x0 >> 5);
+    int fl = 0;
+    if ((lane & 15) == 0 && active) fl = flags[seg];
+    const int band = __shfl_sync(0xffffffffu, fl, lane & 16);
+
+    const int Lw = (D == 2) ? ny : p.g.nz;
+    const int a = (D == 2) ? y : z;
+    int am = a - 1, ap = a + 1;
+    bool solid_m = false, solid_p = false;
+    if (walls) {
+        solid_m = (am == 0);
+        solid_p = (ap == Lw - 1);
+    } else {
+        if (am < 0) am = Lw - 1;
+        if (ap >= Lw) ap = 0;
+    }
+    int ym = y, yp = y;
+    if (D == 3) {
+        ym = (y == 0) ? ny - 1 : y - 1;
+        yp = (y == ny - 1) ? 0 : y + 1;
+    }
+
+    float2 g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        const int cx = L::cx(i), cy = L::cy(i);
+        const int cw = (D == 2) ? cy : L::cz(i);
+        const bool solid = cw == 0 ? false : (cw > 0 ? solid_m : solid_p);  // uniform per row
+        if (solid) {
+            g[i] = active ? P::load2(fin, (long long)L::opp(i) * nc + cell, inv) : p2(0.f);
+            continue;
+        }
+        const int sa = cw == 0 ? a : (cw > 0 ? am : ap);
+        long long srow;
+        if (D == 2) {
+            srow = sa;
+        } else {
+            const int sy = cy == 0 ? y : (cy > 0 ? ym : yp);
+            srow = (long long)sa * ny + sy;
+        }
+        const long long base = (long long)i * nc + srow * nx;
+        const float2 A = active ? P::load2(fin, base + x0, inv) : p2(0.f);
+        if (cx == 0) {
+            g[i] = A;
+        } else if (cx > 0) {  // source x - 1
+            float left = __shfl_up_sync(0xffffffffu, A.y, 1);
+            if ((lane == 0 || x0 == 0) && active)
+                left = P::load1(fin, base + (x0 == 0 ? nx - 1 : x0 - 1), inv);
+            g[i] = make_float2(left, A.x);
+        } else {              // source x + 1
+            float right = __shfl_down_sync(0xffffffffu, A.x, 1);
+            if ((lane == 31 || x0 + 2 >= nx) && active)
+                right = P::load1(fin, base + (x0 + 2 >= nx ? 0 : x0 + 2), inv);
+            g[i] = make_float2(A.y, right);
+        }
+    }
+    if (!active) return;
+
+    float2 Fx = p2((float)p.body[0]), Fy = p2((float)p.body[1]), Fz = p2((float)p.body[2]);
+    if (band) {
+        Fx = add2(Fx, *reinterpret_cast<const float2*>(F + cell));
+        Fy = add2(Fy, *reinterpret_cast<const float2*>(F + nc + cell));
+        *reinterpret_cast<float2*>(F + cell) = p2(0.f);
+        *reinterpret_cast<float2*>(F + nc + cell) = p2(0.f);
+        if (D == 3) {
+            Fz = add2(Fz, *reinterpret_cast<const float2*>(F + 2 * nc + cell));
+            *reinterpret_cast<float2*>(F + 2 * nc + cell) = p2(0.f);
+        }
+    }
+    const CellMoments2 mo = cell_moments2<Q>(g, Fx, Fy, Fz);
+    cell_collide2<Q>(g, mo, (float)p.omega, Fx, Fy, Fz);
+#pragma unroll
+    for (int i = 0; i < Q; i++) P::store2(fout, (long long)i * nc + cell, g[i], p.scale);
+    if (WRITE_ALL || band) {
+        *reinterpret_cast<float2*>(mom + cell) = mo.drho;
+        *reinterpret_cast<float2*>(mom + nc + cell) = mo.ux;
+        *reinterpret_cast<float2*>(mom + 2 * nc + cell) = mo.uy;
+        if (D == 3) *reinterpret_cast<float2*>(mom + 3 * nc + cell) = mo.uz;
+    }
+    if (!isfinite(mo.drho.x) || !isfinite(mo.drho.y)) atomicOr(p.err, ERR_NONFINITE);
+    if ((lane & 15) == 0 && band) flags[seg] = 0;
+}
+
+template <int Q, int ST, int BLOCK>
+static void launch_sc2_b(bool write_all, const void* fin, void* fout, void* mom, void* F,
+                         uint8_t* flags, const StreamParams& p, cudaStream_t s)
+{
+    using T = StorageT<ST>;
+    const int woff = p.g.walls ? 1 : 0;
+    dim3 grid((p.g.nx / 2 + BLOCK - 1) / BLOCK, 1, 1);
+    if (Q == 9) {
+        grid.y = p.g.ny - 2 * woff;
+    } else {
+        grid.y = p.g.ny;
+        grid.z = p.g.nz - 2 * woff;
+    }
+    auto* a = (const typename T::S*)fin;
+    auto* b = (typename T::S*)fout;
+    if (write_all)
+        k_stream_collide2<Q, ST, true, BLOCK><<<grid, BLOCK, 0, s>>>(a, b, (float*)mom, (float*)F, flags, p);
+    else
+        k_stream_collide2<Q, ST, false, BLOCK><<<grid, BLOCK, 0, s>>>(a, b, (float*)mom, (float*)F, flags, p);
+}
+
+template <int Q, int ST>
+static void launch_sc2_t(bool write_all, const void* fin, void* fout, void* mom, void* F,
+                         uint8_t* flags, const StreamParams& p, const Tuning& tu, cudaStream_t s)
+{
+    switch (tu.block_x) {
+        case 64: launch_sc2_b<Q, ST, 64>(write_all, fin, fout, mom, F, flags, p, s); break;
+        case 256: launch_sc2_b<Q, ST, 256>(write_all, fin, fout, mom, F, flags, p, s); break;
+        default: launch_sc2_b<Q, ST, 128>(write_all, fin, fout, mom, F, flags, p, s); break;
+    }
+}
+
+bool pair_kernel_ok(int storage, const GridParams& g)
+{
+    return storage != ST_FP64 && g.nx % 2 == 0;
+}
+
+void launch_stream_collide_pairs(int Q, int storage, bool write_all, const void* fin, void* fout,
+                                 void* moments, void* F, uint8_t* flags, const StreamParams& p,
+                                 const Tuning& tu, cudaStream_t s)
+{
+    if (Q == 9) {
+        if (storage == ST_FP32) launch_sc2_t<9, ST_FP32>(write_all, fin, fout, moments, F, flags, p, tu, s);
+        else launch_sc2_t<9, ST_FP16>(write_all, fin, fout, moments, F, flags, p, tu, s);
+    } else {
+        if (storage == ST_FP32) launch_sc2_t<19, ST_FP32>(write_all, fin, fout, moments, F, flags, p, tu, s);
+        else launch_sc2_t<19, ST_FP16>(write_all, fin, fout, moments, F, flags, p, tu, s);
+    }
+}
+
 // ------------------------------------------------------------------ conversions
 __device__ double weight_q(int Q, int i)
 {

@@ -131,6 +131,88 @@ __device__ __forceinline__ void cell_collide(R* g, const CellMoments<Q, R>& m, R
     }
 }
 
+// ------------------------------------------------------------------ packed pairs
+// Two cells at once in packed FP32x2 arithmetic (Blackwell FFMA2 / FADD2 /
+// FMUL2): the same moments and pair-symmetric collision as above, with the
+// fused multiply-adds written out.
+__device__ __forceinline__ float2 p2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, p2(-1.0f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+struct CellMoments2 {
+    float2 drho, rho, ux, uy, uz;
+};
+
+template <int Q>
+__device__ __forceinline__ CellMoments2 cell_moments2(const float2* g, float2 Fx, float2 Fy,
+                                                      float2 Fz)
+{
+    using L = Stencil<Q>;
+    constexpr int D = L::D;
+    float2 drho = g[0], jx = p2(0.f), jy = p2(0.f), jz = p2(0.f);
+#pragma unroll
+    for (int i = 1; i < Q; i++) {
+        drho = add2(drho, g[i]);
+        if (L::cx(i) > 0) jx = add2(jx, g[i]);
+        if (L::cx(i) < 0) jx = sub2(jx, g[i]);
+        if (L::cy(i) > 0) jy = add2(jy, g[i]);
+        if (L::cy(i) < 0) jy = sub2(jy, g[i]);
+        if (D == 3) {
+            if (L::cz(i) > 0) jz = add2(jz, g[i]);
+            if (L::cz(i) < 0) jz = sub2(jz, g[i]);
+        }
+    }
+    CellMoments2 m;
+    m.drho = drho;
+    m.rho = add2(p2(1.f), drho);
+    const float2 inv_rho = make_float2(1.0f / m.rho.x, 1.0f / m.rho.y);
+    m.ux = mul2(fma2(p2(0.5f), Fx, jx), inv_rho);
+    m.uy = mul2(fma2(p2(0.5f), Fy, jy), inv_rho);
+    m.uz = (D == 3) ? mul2(fma2(p2(0.5f), Fz, jz), inv_rho) : p2(0.f);
+    return m;
+}
+
+template <int Q>
+__device__ __forceinline__ void cell_collide2(float2* g, const CellMoments2& m, float omega,
+                                              float2 Fx, float2 Fy, float2 Fz)
+{
+    using L = Stencil<Q>;
+    constexpr int D = L::D;
+    const float pref = 1.0f - 0.5f * omega;
+    const float2 om1 = p2(1.0f - omega);
+    const float2 uF = fma2(m.uz, Fz, fma2(m.uy, Fy, mul2(m.ux, Fx)));
+    const float2 usq = fma2(m.uz, m.uz, fma2(m.uy, m.uy, mul2(m.ux, m.ux)));
+    const float2 base = mul2(p2(omega), fma2(mul2(p2(-1.5f), m.rho), usq, m.drho));
+    const float2 sym0 = fma2(p2(-3.0f * pref), uF, base);
+    const float2 k2 = mul2(p2(omega * 4.5f), m.rho);
+    const float2 k1 = mul2(p2(omega * 3.0f), m.rho);
+    const float2 p3 = p2(3.0f * pref), p9 = p2(9.0f * pref);
+    g[0] = fma2(om1, g[0], mul2(p2((float)L::w(0)), sym0));
+#pragma unroll
+    for (int i = 1; i < Q; i++) {
+        if (L::opp(i) < i) continue;
+        const int o = L::opp(i);
+        const float2 w = p2((float)L::w(i));
+        float2 cu = p2(0.f), cF = p2(0.f);
+        if (L::cx(i) > 0) { cu = add2(cu, m.ux); cF = add2(cF, Fx); }
+        if (L::cx(i) < 0) { cu = sub2(cu, m.ux); cF = sub2(cF, Fx); }
+        if (L::cy(i) > 0) { cu = add2(cu, m.uy); cF = add2(cF, Fy); }
+        if (L::cy(i) < 0) { cu = sub2(cu, m.uy); cF = sub2(cF, Fy); }
+        if (D == 3) {
+            if (L::cz(i) > 0) { cu = add2(cu, m.uz); cF = add2(cF, Fz); }
+            if (L::cz(i) < 0) { cu = sub2(cu, m.uz); cF = sub2(cF, Fz); }
+        }
+        const float2 t = fma2(k2, cu, mul2(p9, cF));
+        const float2 sym = mul2(w, fma2(cu, t, sym0));
+        const float2 asym = mul2(w, fma2(k1, cu, mul2(p3, cF)));
+        const float2 gi = g[i], go = g[o];
+        g[i] = fma2(om1, gi, add2(sym, asym));
+        g[o] = fma2(om1, go, sub2(sym, asym));
+    }
+}
+
 // Pull streaming of one fluid cell (x, y, z) with halfway bounce-back at the
 // solid first/last layer of the wall axis (y in 2D, z in 3D) when walls != 0
 // and periodic wrap elsewhere: g_i = g*_i(x - c_i), or g*_opp(i)(x) when
