@@ -280,12 +280,16 @@ k_stream_collide2(const typename StorageT<ST>::S* __restrict__ fin,
         yp = (y == ny - 1) ? 0 : y + 1;
     }
 
+    // pass 1: every load of the thread (aligned pairs and the edge values)
+    // is issued before any shuffle, so that the loads overlap
     float2 g[Q];
+    float edge[Q];
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         const int cx = L::cx(i), cy = L::cy(i);
         const int cw = (D == 2) ? cy : L::cz(i);
         const bool solid = cw == 0 ? false : (cw > 0 ? solid_m : solid_p);  // uniform per row
+        edge[i] = 0.f;
         if (solid) {
             g[i] = active ? P::load2(fin, (long long)L::opp(i) * nc + cell, inv) : p2(0.f);
             continue;
@@ -299,18 +303,28 @@ k_stream_collide2(const typename StorageT<ST>::S* __restrict__ fin,
             srow = (long long)sa * ny + sy;
         }
         const long long base = (long long)i * nc + srow * nx;
-        const float2 A = active ? P::load2(fin, base + x0, inv) : p2(0.f);
-        if (cx == 0) {
-            g[i] = A;
-        } else if (cx > 0) {  // source x - 1
+        g[i] = active ? P::load2(fin, base + x0, inv) : p2(0.f);
+        if (cx > 0 && (lane == 0 || x0 == 0) && active)
+            edge[i] = P::load1(fin, base + (x0 == 0 ? nx - 1 : x0 - 1), inv);
+        if (cx < 0 && (lane == 31 || x0 + 2 >= nx) && active)
+            edge[i] = P::load1(fin, base + (x0 + 2 >= nx ? 0 : x0 + 2), inv);
+    }
+    // pass 2: the x-shifted directions take one value from the neighbouring
+    // lane (or the edge load at warp and row ends)
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        const int cx = L::cx(i);
+        const int cw = (D == 2) ? L::cy(i) : L::cz(i);
+        const bool solid = cw == 0 ? false : (cw > 0 ? solid_m : solid_p);
+        if (solid || cx == 0) continue;
+        const float2 A = g[i];
+        if (cx > 0) {  // source x - 1
             float left = __shfl_up_sync(0xffffffffu, A.y, 1);
-            if ((lane == 0 || x0 == 0) && active)
-                left = P::load1(fin, base + (x0 == 0 ? nx - 1 : x0 - 1), inv);
+            if (lane == 0 || x0 == 0) left = edge[i];
             g[i] = make_float2(left, A.x);
-        } else {              // source x + 1
+        } else {       // source x + 1
             float right = __shfl_down_sync(0xffffffffu, A.x, 1);
-            if ((lane == 31 || x0 + 2 >= nx) && active)
-                right = P::load1(fin, base + (x0 + 2 >= nx ? 0 : x0 + 2), inv);
+            if (lane == 31 || x0 + 2 >= nx) right = edge[i];
             g[i] = make_float2(A.y, right);
         }
     }

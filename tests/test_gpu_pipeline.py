@@ -108,7 +108,7 @@ def test_autotune_leaves_state_unchanged():
     a.step(5)
     b.step(5)
     pick = b.autotune(trials=3)
-    assert pick["variant"] in (0, 1)
+    assert pick["variant"] in (0, 1, 2)
     a.step(5)
     b.step(5)
     fa, fb = a.populations(), b.populations()
