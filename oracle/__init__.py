@@ -45,6 +45,7 @@ class Params(ctypes.Structure):
         ("pi_n", ctypes.c_int),
         ("pi_m", ctypes.c_int),
         ("body_force", ctypes.c_double * 3),
+        ("tau_out", ctypes.c_double),
     ]
 
 
@@ -126,6 +127,7 @@ def _load():
     lib.or_sim_spread.argtypes = [vp, dp, dp]
     lib.or_sim_nodal_forces.argtypes = [vp, dp, dp, dp]
     lib.or_sim_observables.argtypes = [vp, ctypes.POINTER(Obs)]
+    lib.or_sim_inside_mask.argtypes = [vp, ctypes.POINTER(ctypes.c_ubyte)]
     lib.or_sim_A.argtypes = [vp]
     lib.or_sim_A.restype = ctypes.c_double
     _lib = lib
@@ -208,7 +210,7 @@ class Sim:
 
     def __init__(self, lattice: int, nx: int, ny: int, nz: int = 1, *, tau=1.0, walls=True,
                  wetting=True, sigma=1e-3, xi=1.0, theta_eq_deg=90.0, pi_n=9, pi_m=3,
-                 body_force=(0.0, 0.0, 0.0)):
+                 body_force=(0.0, 0.0, 0.0), tau_out=0.0):
         self._lib = _load()
         p = Params()
         p.lattice = lattice
@@ -222,6 +224,7 @@ class Sim:
         p.pi_n, p.pi_m = pi_n, pi_m
         for k in range(3):
             p.body_force[k] = body_force[k] if k < len(body_force) else 0.0
+        p.tau_out = tau_out
         self.params = p
         self.Q = lattice
         self.dim = 2 if lattice == D2Q9 else 3
@@ -301,6 +304,11 @@ class Sim:
         n = self.N * self.dim
         return (phi[:n].reshape(self.N, self.dim), nrm[:n].reshape(self.N, self.dim),
                 chi[: self.N], bool(bad))
+
+    def inside_mask(self) -> np.ndarray:
+        m = np.zeros(self.ncell, dtype=np.uint8)
+        self._lib.or_sim_inside_mask(self._h, m.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
+        return m.reshape(self.shape)
 
     def observables(self) -> dict:
         o = Obs()

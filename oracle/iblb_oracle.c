@@ -285,6 +285,7 @@ struct or_sim {
     int* tri;        /* [M][3] */
     double* phi;     /* [N][dim] */
     double* qdot;    /* [N][dim] */
+    unsigned char* inside;  /* [ncell] 1 inside the interface */
 };
 
 static long cell_index(const or_sim* s, int x, int y, int z)
@@ -327,6 +328,7 @@ or_sim* or_sim_create(const or_params* p)
     s->rho = (double*)calloc(s->ncell, sizeof(double));
     s->u = (double*)calloc(3 * s->ncell, sizeof(double));
     s->F = (double*)calloc(3 * s->ncell, sizeof(double));
+    s->inside = (unsigned char*)calloc(s->ncell, 1);
     /* rest state: f = w_i (rho = 1, u = 0) */
     for (int i = 0; i < s->Q; i++)
         for (long x = 0; x < s->ncell; x++) s->f[i * s->ncell + x] = s->w[i];
@@ -346,6 +348,7 @@ void or_sim_destroy(or_sim* s)
     free(s->tri);
     free(s->phi);
     free(s->qdot);
+    free(s->inside);
     free(s);
 }
 
@@ -481,6 +484,125 @@ void or_sim_interpolate(const or_sim* s, const double* u, double* qdot)
     }
 }
 
+/* ------------------------------------------------------------------------ */
+/* Inside / outside classification (ray tracing, Sec. 2).  Rays run along the */
+/* wall axis through the lattice columns (x in 2D; (x, y) in 3D); a cell is   */
+/* inside when an odd number of interface crossings lie below it.  Ties:     */
+/* a 2D segment crosses column X when min(x_a, x_b) <= X < max(x_a, x_b);    */
+/* a 3D triangle, projected on the xy plane and made counter-clockwise,      */
+/* covers column (X, Y) when every edge function is positive, or zero on a   */
+/* top-left edge (horizontal going -x, or going -y), so that a column line   */
+/* through a shared edge or vertex of a closed mesh is counted once.         */
+/* Column indices wrap periodically.                                          */
+/* ------------------------------------------------------------------------ */
+static int cmp_double(const void* a, const void* b)
+{
+    double x = *(const double*)a, y = *(const double*)b;
+    return (x > y) - (x < y);
+}
+
+static double edge_fn(double ax, double ay, double bx, double by, double px, double py)
+{
+    return (bx - ax) * (py - ay) - (by - ay) * (px - ax);
+}
+
+static int top_left(double ax, double ay, double bx, double by)
+{
+    return (ay == by && bx < ax) || (by < ay);
+}
+
+void or_sim_inside_mask(const or_sim* s, unsigned char* mask)
+{
+    const int dim = s->dim;
+    const int ncol = (dim == 2) ? s->L[0] : s->L[0] * s->L[1];
+    const int Lw = s->L[s->wall_axis];
+    memset(mask, 0, (size_t)s->ncell);
+    if (s->N == 0) return;
+    /* crossings per column */
+    int* cnt = (int*)calloc(ncol, sizeof(int));
+    int cap = 64;
+    double** cz = (double**)calloc(ncol, sizeof(double*));
+    int* ccap = (int*)calloc(ncol, sizeof(int));
+    #define OR_ADD_CROSSING(col, z)                                                   \
+        do {                                                                          \
+            if (cnt[col] == ccap[col]) {                                              \
+                ccap[col] = ccap[col] ? 2 * ccap[col] : cap;                          \
+                cz[col] = (double*)realloc(cz[col], sizeof(double) * ccap[col]);      \
+            }                                                                         \
+            cz[col][cnt[col]++] = (z);                                                \
+        } while (0)
+    if (dim == 2) {
+        for (int j = 0; j < s->N; j++) {
+            const int jn = (j + 1) % s->N;
+            const double ax = s->q[2 * j], ay = s->q[2 * j + 1];
+            const double bx = s->q[2 * jn], by = s->q[2 * jn + 1];
+            const double lo = ax < bx ? ax : bx, hi = ax < bx ? bx : ax;
+            for (long X = (long)ceil(lo); (double)X < hi; X++) {
+                const double y = ay + ((double)X - ax) * (by - ay) / (bx - ax);
+                OR_ADD_CROSSING(wrap((int)X, s->L[0]), y);
+            }
+        }
+    } else {
+        for (int f = 0; f < s->M; f++) {
+            const double* P[3] = {s->q + 3 * s->tri[3 * f], s->q + 3 * s->tri[3 * f + 1],
+                                  s->q + 3 * s->tri[3 * f + 2]};
+            double area = edge_fn(P[0][0], P[0][1], P[1][0], P[1][1], P[2][0], P[2][1]);
+            if (area == 0.0) continue; /* vertical face: no column crosses it */
+            if (area < 0.0) {
+                const double* t = P[1];
+                P[1] = P[2];
+                P[2] = t;
+                area = -area;
+            }
+            double xmin = P[0][0], xmax = P[0][0], ymin = P[0][1], ymax = P[0][1];
+            for (int k = 1; k < 3; k++) {
+                if (P[k][0] < xmin) xmin = P[k][0];
+                if (P[k][0] > xmax) xmax = P[k][0];
+                if (P[k][1] < ymin) ymin = P[k][1];
+                if (P[k][1] > ymax) ymax = P[k][1];
+            }
+            for (long Y = (long)ceil(ymin); (double)Y <= ymax; Y++)
+                for (long X = (long)ceil(xmin); (double)X <= xmax; X++) {
+                    const double px = (double)X, py = (double)Y;
+                    double w[3];
+                    int in = 1;
+                    for (int k = 0; k < 3; k++) {
+                        const double* a = P[(k + 1) % 3];
+                        const double* b = P[(k + 2) % 3];
+                        w[k] = edge_fn(a[0], a[1], b[0], b[1], px, py);
+                        if (!(w[k] > 0.0 || (w[k] == 0.0 && top_left(a[0], a[1], b[0], b[1]))))
+                            in = 0;
+                    }
+                    if (!in) continue;
+                    /* barycentric height of the face above the column */
+                    const double z = (w[0] * P[0][2] + w[1] * P[1][2] + w[2] * P[2][2]) /
+                                     (w[0] + w[1] + w[2]);
+                    const int col = wrap((int)X, s->L[0]) + s->L[0] * wrap((int)Y, s->L[1]);
+                    OR_ADD_CROSSING(col, z);
+                }
+        }
+    }
+    #undef OR_ADD_CROSSING
+    for (int col = 0; col < ncol; col++) {
+        if (cnt[col] == 0) continue;
+        qsort(cz[col], cnt[col], sizeof(double), cmp_double);
+        for (int a = 0; a < Lw; a++) {
+            int below = 0;
+            for (int k = 0; k < cnt[col]; k++)
+                if (cz[col][k] < (double)a) below++;
+            if (below & 1) {
+                long cell = (dim == 2) ? cell_index(s, col, a, 0)
+                                       : cell_index(s, col % s->L[0], col / s->L[0], a);
+                mask[cell] = 1;
+            }
+        }
+        free(cz[col]);
+    }
+    free(cz);
+    free(cnt);
+    free(ccap);
+}
+
 /* Total force density of the current state: body force on fluid cells plus
  * the spread interface forces. Returns 1 if a node lies in the wall. */
 static int build_force(or_sim* s)
@@ -518,6 +640,9 @@ int or_sim_step(or_sim* s, int nsteps)
     for (int t = 0; t < nsteps; t++) {
         /* forces at q(t), spread to F(t) */
         if (build_force(s)) return 1;
+        /* viscosity ratio: inside cells relax with tau, outside with tau_out */
+        const int two_tau = s->p.tau_out > 0.0 && s->p.tau_out != s->p.tau;
+        if (two_tau) or_sim_inside_mask(s, s->inside);
 
         for (int z = 0; z < s->L[2]; z++)
             for (int y = 0; y < s->L[1]; y++) {
@@ -554,12 +679,15 @@ int or_sim_step(or_sim* s, int nsteps)
                     double Fc[3] = {s->F[cell], s->F[nc + cell], s->F[2 * nc + cell]};
                     double u[3];
                     for (int k = 0; k < 3; k++) u[k] = (mom[k] + 0.5 * Fc[k]) / rho;
-                    /* collision, Eq. 1-4 */
+                    /* collision, Eq. 1-4, with tau(x, t) */
+                    const double tau =
+                        (!two_tau || s->inside[cell]) ? s->p.tau
+                                                      : (s->p.tau_out > 0.0 ? s->p.tau_out : s->p.tau);
                     double feq[19], S[19];
                     equilibrium_tab(Q, s->c, s->w, rho, u, feq);
-                    guo_source_tab(Q, s->c, s->w, s->p.tau, u, Fc, S);
+                    guo_source_tab(Q, s->c, s->w, tau, u, Fc, S);
                     for (int i = 0; i < Q; i++)
-                        s->fnew[i * nc + cell] = fi[i] - (fi[i] - feq[i]) / s->p.tau + S[i];
+                        s->fnew[i * nc + cell] = fi[i] - (fi[i] - feq[i]) / tau + S[i];
                     s->rho[cell] = rho;
                     for (int k = 0; k < 3; k++) s->u[k * nc + cell] = u[k];
                 }

@@ -40,6 +40,8 @@ typedef struct {
     double theta_eq_deg;  /* equilibrium contact angle (degrees) */
     int pi_n, pi_m;       /* exponents of Pi, n > m > 1 */
     double body_force[3]; /* uniform force density on every fluid cell */
+    double tau_out;       /* relaxation time outside the interface; 0 = tau
+                             (viscosity ratio 1).  Inside cells use tau. */
 } or_params;
 
 /* Fixed-size observables block (every entry FP64). */
@@ -92,6 +94,9 @@ void    or_sim_interpolate(const or_sim* s, const double* u, double* qdot /*[N][
 /* Spread arbitrary nodal vectors phi [N][dim] at the current nodes. */
 void    or_sim_spread(const or_sim* s, const double* phi, double* F /*[3][cells]*/);
 int     or_sim_nodal_forces(const or_sim* s, double* phi, double* normal, double* chi);
+/* Inside / outside classification of every cell by the current interface
+ * (1 = inside), the ray-tracing step behind tau(x, t) (Sec. 2). */
+void    or_sim_inside_mask(const or_sim* s, unsigned char* mask /*[cells]*/);
 void    or_sim_observables(const or_sim* s, or_obs* o);
 double  or_sim_A(const or_sim* s);
 
