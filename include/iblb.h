@@ -48,7 +48,9 @@ typedef enum {
     IBLB_ENODE_IN_WALL = 4,   /* an interface node reached d <= 0 */
     IBLB_ENONFINITE = 5,      /* a density became NaN / Inf */
     IBLB_ETIMEOUT = 6,        /* a bounded device wait gave up */
-    IBLB_EAGAIN = 7           /* batch: no room for this request right now */
+    IBLB_EAGAIN = 7,          /* batch: no room for this request right now */
+    IBLB_ECLASSIFY = 8        /* a lattice column crosses the interface more than
+                                 16 times (inside / outside test) */
 } iblb_status;
 
 typedef enum { IBLB_D2Q9 = 9, IBLB_D3Q19 = 19 } iblb_lattice;
@@ -72,6 +74,17 @@ typedef struct {
     double body_force[3];   /* uniform force density on every fluid cell */
     int storage;            /* iblb_storage */
     int fp16_scale_exp;     /* binary16 scale exponent (0 selects 16) */
+    double tau_out;         /* relaxation time outside the interface (Sec. 2:
+                               viscosity ratio lambda = (tau - 1/2) /
+                               (tau_out - 1/2)); 0 = tau.  Inside / outside is
+                               found each step by ray tracing along the wall
+                               axis through every lattice column. */
+    double wall_u_lo[3];    /* velocity of the lower / upper wall (moving-wall */
+    double wall_u_hi[3];    /* bounce-back, 2 w_i (c_i . u_w) / c_s^2 with
+                               rho_w = 1; used for the drop in shear, Sec. 4).
+                               Tangential components only (the wall-axis
+                               component, and z in 2D, must be 0), |u| <= 0.3;
+                               needs walls = 1.  All zero = resting walls. */
 } iblb_config;
 
 typedef struct {
@@ -128,6 +141,23 @@ iblb_status iblb_get_populations(iblb_handle h, double* f);
 iblb_status iblb_observables(iblb_handle h, iblb_obs* out);
 
 /* ---- single-stage entry points (each runs one kernel of the step) ---- */
+
+/* Set every population to the equilibrium (Eq. 3) of the given fields:
+ * rho [cells] (NULL: 1 everywhere), u [dim][cells], host buffers, layout
+ * [component][z][y][x].  E.g. a fully developed shear flow.  Synchronises. */
+iblb_status iblb_set_equilibrium(iblb_handle h, const double* rho, const double* u);
+
+/* Deformation of the current interface in the shear plane (x and the wall
+ * axis), Sec. 4, Eq. 12: out[5] = {D = (r1 - r3)/(r1 + r3), r1, r3,
+ * inclination of the r1 axis to x (degrees), enclosed area / volume}.  r1, r3
+ * are the semi-axes of the ellipse (ellipsoid) with the same central second
+ * moments as the enclosed region.  Needs a CCW ring / outward mesh of >= 3
+ * nodes (IBLB_EINVAL otherwise).  Synchronises. */
+iblb_status iblb_deformation(iblb_handle h, double* out);
+
+/* Inside / outside classification of every cell by the current interface
+ * (1 = inside), mask [cells].  Synchronises. */
+iblb_status iblb_inside_mask(iblb_handle h, unsigned char* mask);
 
 /* Nodal forces phi [N][dim], normals [N][dim] and 1-ring measures chi [N]
  * at the current interface (any pointer may be NULL). Synchronises. */

@@ -46,6 +46,8 @@ class Params(ctypes.Structure):
         ("pi_m", ctypes.c_int),
         ("body_force", ctypes.c_double * 3),
         ("tau_out", ctypes.c_double),
+        ("wall_u_lo", ctypes.c_double * 3),
+        ("wall_u_hi", ctypes.c_double * 3),
     ]
 
 
@@ -128,6 +130,8 @@ def _load():
     lib.or_sim_nodal_forces.argtypes = [vp, dp, dp, dp]
     lib.or_sim_observables.argtypes = [vp, ctypes.POINTER(Obs)]
     lib.or_sim_inside_mask.argtypes = [vp, ctypes.POINTER(ctypes.c_ubyte)]
+    lib.or_sim_set_equilibrium.argtypes = [vp, dp, dp]
+    lib.or_deformation.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ip, dp]
     lib.or_sim_A.argtypes = [vp]
     lib.or_sim_A.restype = ctypes.c_double
     _lib = lib
@@ -204,13 +208,25 @@ def nodal_forces(q, tri=None, *, sigma, wetting=False, A=0.0, xi=1.0, n=9, m=3,
     return out
 
 
+def deformation(q, tri=None) -> dict:
+    """Deformation index D = (r1 - r3)/(r1 + r3) of a closed ring (q [N, 2])
+    or outward mesh (q [N, 3], tri [M, 3]) in the shear plane (Sec. 4, Eq. 12)."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    N, dim = q.shape
+    t = None if tri is None else np.ascontiguousarray(tri, dtype=np.int32)
+    out = np.zeros(5)
+    _load().or_deformation(dim, N, _dptr(q), 0 if t is None else t.shape[0], _iptr(t), _dptr(out))
+    return dict(D=out[0], r1=out[1], r3=out[2], angle_deg=out[3], volume=out[4])
+
+
 # ---------------------------------------------------------------- simulation
 class Sim:
     """One oracle simulation. Fields use the layout [component][z][y][x]."""
 
     def __init__(self, lattice: int, nx: int, ny: int, nz: int = 1, *, tau=1.0, walls=True,
                  wetting=True, sigma=1e-3, xi=1.0, theta_eq_deg=90.0, pi_n=9, pi_m=3,
-                 body_force=(0.0, 0.0, 0.0), tau_out=0.0):
+                 body_force=(0.0, 0.0, 0.0), tau_out=0.0, wall_u_lo=(0.0, 0.0, 0.0),
+                 wall_u_hi=(0.0, 0.0, 0.0)):
         self._lib = _load()
         p = Params()
         p.lattice = lattice
@@ -225,6 +241,9 @@ class Sim:
         for k in range(3):
             p.body_force[k] = body_force[k] if k < len(body_force) else 0.0
         p.tau_out = tau_out
+        for k in range(3):
+            p.wall_u_lo[k] = wall_u_lo[k] if k < len(wall_u_lo) else 0.0
+            p.wall_u_hi[k] = wall_u_hi[k] if k < len(wall_u_hi) else 0.0
         self.params = p
         self.Q = lattice
         self.dim = 2 if lattice == D2Q9 else 3
@@ -254,6 +273,7 @@ class Sim:
     def set_interface(self, q, tri=None):
         q = np.ascontiguousarray(q, dtype=np.float64).reshape(-1, self.dim)
         t = None if tri is None else np.ascontiguousarray(tri, dtype=np.int32).reshape(-1, 3)
+        self._tri = t
         self.N = q.shape[0]
         self.M = self.N if self.dim == 2 else (0 if t is None else t.shape[0])
         self._lib.or_sim_set_interface(self._h, self.N, _dptr(q), 0 if t is None else t.shape[0],
@@ -304,6 +324,16 @@ class Sim:
         n = self.N * self.dim
         return (phi[:n].reshape(self.N, self.dim), nrm[:n].reshape(self.N, self.dim),
                 chi[: self.N], bool(bad))
+
+    def set_equilibrium(self, u, rho=None):
+        """f = f_eq(rho, u) (Eq. 3); u [dim] + lattice shape, rho lattice shape or None (1)."""
+        u = np.ascontiguousarray(u, dtype=np.float64).reshape(self.dim, self.ncell)
+        r = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64).reshape(self.ncell)
+        self._lib.or_sim_set_equilibrium(self._h, None if r is None else _dptr(r), _dptr(u))
+
+    def deformation(self) -> dict:
+        """Deformation index of the current interface (Sec. 4, Eq. 12)."""
+        return deformation(self.fields()[2], getattr(self, "_tri", None))
 
     def inside_mask(self) -> np.ndarray:
         m = np.zeros(self.ncell, dtype=np.uint8)

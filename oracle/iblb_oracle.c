@@ -379,6 +379,18 @@ void or_sim_set_populations(or_sim* s, const double* f)
     memcpy(s->f, f, sizeof(double) * s->Q * s->ncell);
 }
 
+void or_sim_set_equilibrium(or_sim* s, const double* rho, const double* u)
+{
+    const long nc = s->ncell;
+    for (long cell = 0; cell < nc; cell++) {
+        double uc[3] = {0.0, 0.0, 0.0};
+        for (int k = 0; k < s->dim; k++) uc[k] = u[k * nc + cell];
+        double feq[19];
+        equilibrium_tab(s->Q, s->c, s->w, rho ? rho[cell] : 1.0, uc, feq);
+        for (int i = 0; i < s->Q; i++) s->f[i * nc + cell] = feq[i];
+    }
+}
+
 void or_sim_get_populations(const or_sim* s, double* f)
 {
     memcpy(f, s->f, sizeof(double) * s->Q * s->ncell);
@@ -662,7 +674,13 @@ int or_sim_step(or_sim* s, int nsteps)
                         int src[3] = {x - s->c[3 * i], y - s->c[3 * i + 1], z - s->c[3 * i + 2]};
                         int src_layer = src[s->wall_axis];
                         if (solid_layer(s, src_layer)) {
-                            fi[i] = s->f[s->opp[i] * nc + cell];
+                            /* halfway bounce-back off the wall the population
+                               came from; a moving wall adds 2 w_i rho_w
+                               (c_i . u_w) / c_s^2 with rho_w = 1 */
+                            const double* uw = (src_layer <= 0) ? s->p.wall_u_lo : s->p.wall_u_hi;
+                            const double cu = s->c[3 * i] * uw[0] + s->c[3 * i + 1] * uw[1] +
+                                              s->c[3 * i + 2] * uw[2];
+                            fi[i] = s->f[s->opp[i] * nc + cell] + 2.0 * s->w[i] * cu / (1.0 / 3.0);
                         } else {
                             int sx = wrap(src[0], s->L[0]);
                             int sy = wrap(src[1], s->L[1]);
@@ -868,4 +886,77 @@ void or_sim_observables(const or_sim* s, or_obs* o)
         }
     }
     o->film = fc ? fsum / fc : NAN;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Deformation index D = (r1 - r3) / (r1 + r3) (drop in shear, Sec. 4, Eq. 12) */
+/* The enclosed region is split into simplices from a reference point p0     */
+/* (the node mean): triangles (p0, a, b) of the ring in 2D, tetrahedra        */
+/* (p0, a, b, c) of the mesh in 3D, each with a signed measure.  Over a       */
+/* simplex with vertices v_k (relative to p0) and measure |K|:                */
+/*   int x dK = |K| (sum v_k) / (d + 1),                                      */
+/*   int x x^T dK = |K| / ((d + 1)(d + 2)) (sum v_k v_k^T + s s^T), s = sum v_k */
+/* (the vertex p0 = 0 drops out).  An ellipse with semi-axes a, b has central */
+/* second moments area a^2 / 4, area b^2 / 4; an ellipsoid volume a^2 / 5 ... */
+/* so the semi-axes in the shear plane (x and the wall axis) are              */
+/* sqrt(4 lambda / area) (2D) and sqrt(5 lambda / volume) (3D), lambda the    */
+/* eigenvalues of the central second-moment block of that plane.              */
+/* ------------------------------------------------------------------------ */
+void or_deformation(int dim, int N, const double* q, int M, const int* tri, double* out)
+{
+    double p0[3] = {0.0, 0.0, 0.0};
+    for (int j = 0; j < N; j++)
+        for (int k = 0; k < dim; k++) p0[k] += q[dim * j + k];
+    for (int k = 0; k < dim; k++) p0[k] /= N;
+    double vol = 0.0, m1[3] = {0.0, 0.0, 0.0}, m2[3][3] = {{0}};
+    const int nsimp = (dim == 2) ? N : M;
+    for (int t = 0; t < nsimp; t++) {
+        double v[3][3] = {{0}};
+        int nv;
+        double meas;
+        if (dim == 2) {
+            const int ja = t, jb = (t + 1) % N;
+            for (int k = 0; k < 2; k++) {
+                v[0][k] = q[2 * ja + k] - p0[k];
+                v[1][k] = q[2 * jb + k] - p0[k];
+            }
+            nv = 2;
+            meas = 0.5 * (v[0][0] * v[1][1] - v[0][1] * v[1][0]);
+        } else {
+            for (int c = 0; c < 3; c++)
+                for (int k = 0; k < 3; k++) v[c][k] = q[3 * tri[3 * t + c] + k] - p0[k];
+            nv = 3;
+            const double cx = v[1][1] * v[2][2] - v[1][2] * v[2][1];
+            const double cy = v[1][2] * v[2][0] - v[1][0] * v[2][2];
+            const double cz = v[1][0] * v[2][1] - v[1][1] * v[2][0];
+            meas = (v[0][0] * cx + v[0][1] * cy + v[0][2] * cz) / 6.0;
+        }
+        double sv[3] = {0.0, 0.0, 0.0};
+        for (int c = 0; c < nv; c++)
+            for (int k = 0; k < 3; k++) sv[k] += v[c][k];
+        vol += meas;
+        for (int k = 0; k < 3; k++) m1[k] += meas * sv[k] / (dim + 1);
+        const double f2 = meas / ((dim + 1) * (dim + 2));
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++) {
+                double acc = sv[a] * sv[b];
+                for (int c = 0; c < nv; c++) acc += v[c][a] * v[c][b];
+                m2[a][b] += f2 * acc;
+            }
+    }
+    const int w = dim - 1; /* wall axis */
+    const double gx = m1[0] / vol, gw = m1[w] / vol;
+    const double sxx = m2[0][0] - vol * gx * gx;
+    const double sww = m2[w][w] - vol * gw * gw;
+    const double sxw = m2[0][w] - vol * gx * gw;
+    const double mean = 0.5 * (sxx + sww);
+    const double rad = sqrt(0.25 * (sxx - sww) * (sxx - sww) + sxw * sxw);
+    const double k = (dim == 2) ? 4.0 : 5.0;
+    const double r1 = sqrt(k * (mean + rad) / vol);
+    const double r3 = sqrt(k * (mean - rad) / vol);
+    out[0] = (r1 - r3) / (r1 + r3);
+    out[1] = r1;
+    out[2] = r3;
+    out[3] = 0.5 * atan2(2.0 * sxw, sxx - sww) * 180.0 / M_PI;
+    out[4] = vol;
 }

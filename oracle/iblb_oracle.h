@@ -42,6 +42,8 @@ typedef struct {
     double body_force[3]; /* uniform force density on every fluid cell */
     double tau_out;       /* relaxation time outside the interface; 0 = tau
                              (viscosity ratio 1).  Inside cells use tau. */
+    double wall_u_lo[3];  /* velocity of the lower / upper wall (tangential; */
+    double wall_u_hi[3];  /* the wall-axis component must be 0)              */
 } or_params;
 
 /* Fixed-size observables block (every entry FP64). */
@@ -74,6 +76,14 @@ int or_nodal_forces(int dim, int N, const double* q, int M, const int* tri,
                     double* phi, double* phi_sigma, double* phi_pi,
                     double* normal, double* chi);
 
+/* Deformation of a closed interface (the drop-in-shear test of Sec. 4, Eq. 12):
+ * the second moment S of the enclosed region about its centroid, restricted
+ * to the shear plane (x and the wall axis), gives the semi-axes r1 >= r3 of
+ * the ellipse (2D) / ellipsoid section (3D) with the same moments, and
+ * D = (r1 - r3) / (r1 + r3).  out = {D, r1, r3, inclination of the r1 axis
+ * to x in degrees, enclosed area / volume}. */
+void or_deformation(int dim, int N, const double* q, int M, const int* tri, double* out /*[5]*/);
+
 /* ---- a whole simulation ---- */
 typedef struct or_sim or_sim;
 
@@ -81,6 +91,8 @@ or_sim* or_sim_create(const or_params* p);
 void    or_sim_destroy(or_sim* s);
 int     or_sim_set_interface(or_sim* s, int N, const double* q, int M, const int* tri);
 void    or_sim_set_populations(or_sim* s, const double* f /*[Q][cells]*/);
+/* f = f_eq(rho, u) everywhere (Eq. 3); rho [cells] (NULL: 1), u [dim][cells]. */
+void    or_sim_set_equilibrium(or_sim* s, const double* rho, const double* u);
 void    or_sim_get_populations(const or_sim* s, double* f);
 /* Advance n steps; returns 0, 1 (node in wall) or 2 (non-finite population). */
 int     or_sim_step(or_sim* s, int n);

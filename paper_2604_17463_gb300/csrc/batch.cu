@@ -641,6 +641,11 @@ iblb_status check_cfg(const iblb_batch_s* b, const iblb_config& c)
     if (c.wetting && (!(c.xi > 0.0) || !(c.pi_n > c.pi_m) || c.pi_m < 2)) return IBLB_EINVAL;
     if (c.body_force[0] != 0.0 || c.body_force[1] != 0.0 || c.body_force[2] != 0.0)
         return IBLB_EINVAL;  // the batched kernel has no body force
+    if (c.tau_out != 0.0 && c.tau_out != c.tau)
+        return IBLB_EINVAL;  // nor a viscosity ratio
+    for (int k = 0; k < 3; k++)
+        if (c.wall_u_lo[k] != 0.0 || c.wall_u_hi[k] != 0.0)
+            return IBLB_EINVAL;  // nor moving walls
     return IBLB_OK;
 }
 

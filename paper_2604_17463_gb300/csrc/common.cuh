@@ -62,7 +62,10 @@ template <> struct Stencil<19> {
 };
 
 // Device error flags (bitwise OR).
-enum : int { ERR_NODE_IN_WALL = 1, ERR_NONFINITE = 2, ERR_TIMEOUT = 4 };
+enum : int { ERR_NODE_IN_WALL = 1, ERR_NONFINITE = 2, ERR_TIMEOUT = 4, ERR_CLASSIFY = 8 };
+
+// Interface crossings kept per lattice column for the inside / outside test.
+constexpr int COL_MAX = 16;
 
 // ------------------------------------------------------------------ params
 struct GridParams {
@@ -79,6 +82,14 @@ struct StreamParams {
     double body[3];        // uniform force density
     float omega_f;         // the same in FP32 (no per-thread conversion on the FP32 paths)
     float body_f[3];
+    // viscosity ratio: cells outside the interface relax with omega_out
+    int two_tau;
+    double omega_out;
+    const int* col_cnt;    // crossings per column
+    const double* col_z;   // [column][COL_MAX] crossing heights
+    // moving walls (tangential velocities of the lower / upper wall)
+    int moving;
+    double uw_lo[3], uw_hi[3];
     float scale, inv_scale;  // binary16 storage scale (1 for other storage)
     int* err;
 };
@@ -194,6 +205,34 @@ void launch_interp(int storage, int dim, double* q, const void* moments, int N, 
 void launch_observables(int dim, const double* q, int N, const int* tri, int M,
                         const double* mass_partial, int n_partial, double xi, double wall_plane,
                         double* out, cudaStream_t s);
+
+// f = f_eq(rho, u) in storage form (deviation from w, scaled); rho may be null (1).
+void launch_set_equilibrium(int Q, int storage, int dim, const double* rho, const double* u,
+                            void* dst, long long ncell, float scale, cudaStream_t s);
+// Deformation index of the interface in the shear plane: out[5] =
+// {D, r1, r3, inclination (deg), enclosed area / volume}.
+void launch_deformation(int dim, const double* q, int N, const int* tri, int M, double* out,
+                        cudaStream_t s);
+
+// Inside / outside test of the cell at wall-axis coordinate a in column col:
+// an odd number of interface crossings below it.
+__device__ __forceinline__ bool inside_cell(const int* __restrict__ cnt,
+                                            const double* __restrict__ cz, int col, int a)
+{
+    int c = cnt[col];
+    if (c == 0) return false;
+    if (c > COL_MAX) c = COL_MAX;
+    bool in = false;
+    for (int k = 0; k < c; k++) in ^= (cz[(long long)col * COL_MAX + k] < (double)a);
+    return in;
+}
+
+// Column crossings of the current interface (classify.cu); the column count
+// array is cleared first.
+void launch_classify(int dim, const double* q, int N, const int* tri, int M, const GridParams& g,
+                     int* cnt, double* cz, int* err, cudaStream_t s);
+void launch_inside_mask(const GridParams& g, const int* cnt, const double* cz,
+                        unsigned char* mask, cudaStream_t s);
 
 // Kernel-launch accounting shared by the engines (iblb_kernel_launch_count).
 void add_launches(long long n);

@@ -64,6 +64,11 @@ struct iblb_sim {
     int* csr_ptr = nullptr;
     int* entry_pos = nullptr;    // CSR position of each (face, corner) (3D)
     double* entry_rec = nullptr; // per-(face, corner) geometry records in CSR order (3D)
+    double* defo = nullptr;      // deformation output [8]
+    bool moving = false;         // walls with a tangential velocity
+    int* col_cnt = nullptr;      // viscosity ratio: crossings per lattice column
+    double* col_z = nullptr;     // [column][COL_MAX] crossing heights
+    bool two_tau = false;
     std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;  // (parity, steps, last)
     std::string msg;
 };
@@ -101,10 +106,24 @@ void clear_graphs(iblb_sim* h)
 }
 
 int force_kernels(const iblb_sim* h) { return h->dim == 3 ? 2 : 1; }
-int kernels_per_step(const iblb_sim* h) { return h->N > 0 ? 3 + force_kernels(h) : 1; }
+int kernels_per_step(const iblb_sim* h)
+{
+    return (h->N > 0 ? 3 + force_kernels(h) : 1) + ((h->two_tau && h->N > 0) ? 1 : 0);
+}
+
+void enqueue_classify(iblb_sim* h, cudaStream_t s)
+{
+    if (h->two_tau)
+        launch_classify(h->dim, h->q, h->N, h->tri, h->M, h->g, h->col_cnt, h->col_z, h->err, s);
+}
 
 cudaError_t launch_sc(iblb_sim* h, cudaStream_t s, bool write_all)
 {
+    if (h->two_tau || h->moving) {  // the plain kernel carries tau(x) and moving walls
+        launch_stream_collide(h->Q, h->storage, write_all, h->f[h->cur], h->f[h->cur ^ 1], h->mom,
+                              h->F, h->flags, h->sp, h->tune, s);
+        return cudaPeekAtLastError();
+    }
     if (h->tune.variant == 2 && pair_kernel_ok(h->storage, h->g)) {
         launch_stream_collide_pairs(h->Q, h->storage, write_all, h->f[h->cur], h->f[h->cur ^ 1],
                                     h->mom, h->F, h->flags, h->sp, h->tune, s);
@@ -127,6 +146,7 @@ void enqueue_step(iblb_sim* h, cudaStream_t s, bool write_all)
                       nullptr, h->err, s);
         launch_spread(h->storage, h->dim, h->q, h->phi, h->N, h->F, h->flags, h->g, s);
     }
+    enqueue_classify(h, s);
     launch_sc(h, s, write_all);
     if (h->N > 0)
         launch_interp(h->storage, h->dim, h->q, h->mom, h->N, nullptr, true, h->g, s);
@@ -166,6 +186,8 @@ iblb_status check_device_flag(iblb_sim* h)
         return fail(h, IBLB_ENODE_IN_WALL, "an interface node reached the wall (d <= 0)");
     if (e & ERR_NONFINITE) return fail(h, IBLB_ENONFINITE, "non-finite density");
     if (e & ERR_TIMEOUT) return fail(h, IBLB_ETIMEOUT, "a bounded device wait gave up");
+    if (e & ERR_CLASSIFY)
+        return fail(h, IBLB_ECLASSIFY, "a lattice column crosses the interface too often");
     return IBLB_OK;
 }
 
@@ -200,6 +222,7 @@ const char* iblb_status_string(iblb_status s)
         case IBLB_ENONFINITE: return "non-finite density";
         case IBLB_ETIMEOUT: return "device wait timed out";
         case IBLB_EAGAIN: return "no room, try again";
+        case IBLB_ECLASSIFY: return "inside/outside classification overflow";
     }
     return "unknown status";
 }
@@ -228,6 +251,20 @@ iblb_status iblb_create(const iblb_config* cfg, void* cuda_stream, iblb_handle* 
     if (dim == 3 && (c.ny > 65535 || nz > 65535)) return IBLB_EINVAL;
     if (dim == 2 && c.ny > 65535) return IBLB_EINVAL;
     if (c.fp16_scale_exp < 0 || c.fp16_scale_exp > 24) return IBLB_EINVAL;
+    if (c.tau_out != 0.0 && (!(c.tau_out > 0.5) || !std::isfinite(c.tau_out))) return IBLB_EINVAL;
+    {
+        const int wax = c.lattice == 9 ? 1 : 2;
+        bool mv = false;
+        for (int k = 0; k < 3; k++) {
+            for (double u : {c.wall_u_lo[k], c.wall_u_hi[k]}) {
+                if (!std::isfinite(u) || std::fabs(u) > 0.3) return IBLB_EINVAL;
+                if (u != 0.0) mv = true;
+            }
+        }
+        if (mv && (!c.walls || c.wall_u_lo[wax] != 0.0 || c.wall_u_hi[wax] != 0.0 ||
+                   (c.lattice == 9 && (c.wall_u_lo[2] != 0.0 || c.wall_u_hi[2] != 0.0))))
+            return IBLB_EINVAL;  // tangential wall velocities only
+    }
 
     iblb_sim* h = new iblb_sim();
     h->cfg = c;
@@ -253,6 +290,15 @@ iblb_status iblb_create(const iblb_config* cfg, void* cuda_stream, iblb_handle* 
     for (int k = 0; k < 3; k++) sp.body[k] = (k < dim) ? c.body_force[k] : 0.0;
     sp.omega_f = (float)sp.omega;
     for (int k = 0; k < 3; k++) sp.body_f[k] = (float)sp.body[k];
+    h->two_tau = c.tau_out != 0.0 && c.tau_out != c.tau;
+    for (int k = 0; k < 3; k++) {
+        sp.uw_lo[k] = c.wall_u_lo[k];
+        sp.uw_hi[k] = c.wall_u_hi[k];
+        if (c.wall_u_lo[k] != 0.0 || c.wall_u_hi[k] != 0.0) h->moving = true;
+    }
+    sp.moving = h->moving ? 1 : 0;
+    sp.two_tau = h->two_tau ? 1 : 0;
+    sp.omega_out = h->two_tau ? 1.0 / c.tau_out : sp.omega;
     const int sexp = c.fp16_scale_exp ? c.fp16_scale_exp : 16;
     sp.scale = c.storage == IBLB_FP16_DEV ? std::ldexp(1.0f, sexp) : 1.0f;
     sp.inv_scale = 1.0f / sp.scale;
@@ -284,6 +330,16 @@ iblb_status iblb_create(const iblb_config* cfg, void* cuda_stream, iblb_handle* 
     if ((e = cudaMalloc(&h->partial, sizeof(double) * h->npartial)) != cudaSuccess)
         return bail(e, "partial");
     if ((e = cudaMalloc(&h->obs, sizeof(double) * 12)) != cudaSuccess) return bail(e, "obs");
+    if ((e = cudaMalloc(&h->defo, sizeof(double) * 8)) != cudaSuccess) return bail(e, "obs");
+    if (h->two_tau) {
+        const size_t ncol = dim == 2 ? (size_t)c.nx : (size_t)c.nx * c.ny;
+        if ((e = cudaMalloc(&h->col_cnt, sizeof(int) * ncol)) != cudaSuccess) return bail(e, "columns");
+        if ((e = cudaMalloc(&h->col_z, sizeof(double) * COL_MAX * ncol)) != cudaSuccess)
+            return bail(e, "columns");
+        cudaMemsetAsync(h->col_cnt, 0, sizeof(int) * ncol, h->stream);
+        sp.col_cnt = h->col_cnt;
+        sp.col_z = h->col_z;
+    }
     if ((e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking)) != cudaSuccess)
         return bail(e, "stream");
     // rest state: deviations are zero in every storage form
@@ -331,6 +387,9 @@ void iblb_destroy(iblb_handle h)
     free_dev(h->csr_ptr);
     free_dev(h->entry_pos);
     free_dev(h->entry_rec);
+    free_dev(h->col_cnt);
+    free_dev(h->col_z);
+    free_dev(h->defo);
     if (h->cap) cudaStreamDestroy(h->cap);
     delete h;
 }
@@ -596,6 +655,73 @@ iblb_status iblb_interpolate(iblb_handle h, const double* u, double* qdot)
     return IBLB_OK;
 }
 
+iblb_status iblb_set_equilibrium(iblb_handle h, const double* rho, const double* u)
+{
+    if (!h || !u) return IBLB_EINVAL;
+    const long long nc = h->g.ncell;
+    double* d = nullptr;
+    const size_t nu = (size_t)h->dim * nc;
+    const size_t n = nu + (rho ? (size_t)nc : 0);
+    CK(h, cudaMalloc(&d, sizeof(double) * n));
+    cudaError_t e = cudaMemcpyAsync(d, u, sizeof(double) * nu, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && rho)
+        e = cudaMemcpyAsync(d + nu, rho, sizeof(double) * nc, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) {
+        launch_set_equilibrium(h->Q, h->storage, h->dim, rho ? d + nu : nullptr, d, h->f[h->cur],
+                               nc, h->sp.scale, h->stream);
+        g_launches++;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_equilibrium");
+    return IBLB_OK;
+}
+
+iblb_status iblb_deformation(iblb_handle h, double* out)
+{
+    if (!h || !out) return IBLB_EINVAL;
+    if (h->N < 3) return fail(h, IBLB_EINVAL, "deformation needs an interface");
+    launch_deformation(h->dim, h->q, h->N, h->tri, h->M, h->defo, h->stream);
+    g_launches++;
+    CK(h, cudaGetLastError());
+    CK(h, cudaMemcpyAsync(out, h->defo, sizeof(double) * 5, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return IBLB_OK;
+}
+
+iblb_status iblb_inside_mask(iblb_handle h, unsigned char* mask)
+{
+    if (!h || !mask) return IBLB_EINVAL;
+    const long long nc = h->g.ncell;
+    const size_t ncol = h->dim == 2 ? (size_t)h->g.nx : (size_t)h->g.nx * h->g.ny;
+    int* cnt = h->col_cnt;
+    double* cz = h->col_z;
+    bool own = false;
+    if (!cnt) {
+        CK(h, cudaMalloc(&cnt, sizeof(int) * ncol));
+        CK(h, cudaMalloc(&cz, sizeof(double) * COL_MAX * ncol));
+        own = true;
+    }
+    unsigned char* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, (size_t)nc);
+    if (e == cudaSuccess) {
+        launch_classify(h->dim, h->q, h->N, h->tri, h->M, h->g, cnt, cz, h->err, h->stream);
+        launch_inside_mask(h->g, cnt, cz, d, h->stream);
+        g_launches += 2;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(mask, d, (size_t)nc, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(d);
+    if (own) {
+        cudaFree(cnt);
+        cudaFree(cz);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "inside_mask");
+    return check_device_flag(h);
+}
+
 iblb_status iblb_step_profiled(iblb_handle h, int n_steps, double* kernel_ms)
 {
     if (!h || !kernel_ms || n_steps < 0) return IBLB_EINVAL;
@@ -611,6 +737,7 @@ iblb_status iblb_step_profiled(iblb_handle h, int n_steps, double* kernel_ms)
                           nullptr, nullptr, h->err, h->stream);
         cudaEventRecord(ev[1], h->stream);
         if (ib) launch_spread(h->storage, h->dim, h->q, h->phi, h->N, h->F, h->flags, h->g, h->stream);
+        enqueue_classify(h, h->stream);
         cudaEventRecord(ev[2], h->stream);
         launch_sc(h, h->stream, last);
         cudaEventRecord(ev[3], h->stream);

@@ -381,6 +381,88 @@ k_observables(int dim, const double* __restrict__ q, int N, const int* __restric
     }
 }
 
+// Deformation index (Sec. 4, Eq. 12): the enclosed region is split into
+// simplices from the node mean p0 (triangles of the ring in 2D, tetrahedra of
+// the mesh in 3D).  Over a simplex with vertices v_k relative to p0 and
+// signed measure |K|: int x = |K| sum(v_k) / (d + 1) and
+// int x x^T = |K| (sum v_k v_k^T + s s^T) / ((d + 1)(d + 2)), s = sum v_k.
+// The central second moments in the shear plane (x and the wall axis) give
+// the semi-axes sqrt(4 lambda / area) (2D) or sqrt(5 lambda / volume) (3D).
+__global__ void __launch_bounds__(OBS_BLOCK)
+k_deformation(int dim, const double* __restrict__ q, int N, const int* __restrict__ tri, int M,
+              double* out)
+{
+    __shared__ double sh[6][OBS_BLOCK / 32];
+    __shared__ double p0s[3];
+    const int t = threadIdx.x;
+    const int w = dim - 1;
+    double v[6];
+    for (int k = 0; k < 6; k++) v[k] = 0.0;
+    for (int j = t; j < N; j += OBS_BLOCK)
+        for (int k = 0; k < dim; k++) v[k] += q[dim * j + k];
+    block_sum(v, 3, sh);
+    if (t == 0)
+        for (int k = 0; k < 3; k++) p0s[k] = k < dim ? v[k] / N : 0.0;
+    __syncthreads();
+    const double p0[3] = {p0s[0], p0s[1], p0s[2]};
+    for (int k = 0; k < 6; k++) v[k] = 0.0;
+    const int nsimp = dim == 2 ? N : M;
+    for (int e = t; e < nsimp; e += OBS_BLOCK) {
+        double a[3] = {0, 0, 0}, b[3] = {0, 0, 0}, c[3] = {0, 0, 0};
+        double meas;
+        if (dim == 2) {
+            const int jn = (e + 1 == N) ? 0 : e + 1;
+            for (int k = 0; k < 2; k++) {
+                a[k] = q[2 * e + k] - p0[k];
+                b[k] = q[2 * jn + k] - p0[k];
+            }
+            meas = 0.5 * (a[0] * b[1] - a[1] * b[0]);
+        } else {
+            const double* A = q + 3 * tri[3 * e];
+            const double* B = q + 3 * tri[3 * e + 1];
+            const double* C = q + 3 * tri[3 * e + 2];
+            for (int k = 0; k < 3; k++) {
+                a[k] = A[k] - p0[k];
+                b[k] = B[k] - p0[k];
+                c[k] = C[k] - p0[k];
+            }
+            meas = (a[0] * (b[1] * c[2] - b[2] * c[1]) + a[1] * (b[2] * c[0] - b[0] * c[2]) +
+                    a[2] * (b[0] * c[1] - b[1] * c[0])) / 6.0;
+        }
+        const double sx = a[0] + b[0] + c[0], sw = a[w] + b[w] + c[w];
+        const double f2 = meas / ((dim + 1) * (dim + 2));
+        v[0] += meas;
+        v[1] += meas * sx / (dim + 1);
+        v[2] += meas * sw / (dim + 1);
+        v[3] += f2 * (a[0] * a[0] + b[0] * b[0] + c[0] * c[0] + sx * sx);
+        v[4] += f2 * (a[w] * a[w] + b[w] * b[w] + c[w] * c[w] + sw * sw);
+        v[5] += f2 * (a[0] * a[w] + b[0] * b[w] + c[0] * c[w] + sx * sw);
+    }
+    block_sum(v, 6, sh);
+    if (t == 0) {
+        const double vol = v[0];
+        const double gx = v[1] / vol, gw = v[2] / vol;
+        const double sxx = v[3] - vol * gx * gx;
+        const double sww = v[4] - vol * gw * gw;
+        const double sxw = v[5] - vol * gx * gw;
+        const double mean = 0.5 * (sxx + sww);
+        const double rad = sqrt(0.25 * (sxx - sww) * (sxx - sww) + sxw * sxw);
+        const double kk = dim == 2 ? 4.0 : 5.0;
+        const double r1 = sqrt(kk * (mean + rad) / vol), r3 = sqrt(kk * (mean - rad) / vol);
+        out[0] = (r1 - r3) / (r1 + r3);
+        out[1] = r1;
+        out[2] = r3;
+        out[3] = 0.5 * atan2(2.0 * sxw, sxx - sww) * (180.0 / 3.141592653589793);
+        out[4] = vol;
+    }
+}
+
+void launch_deformation(int dim, const double* q, int N, const int* tri, int M, double* out,
+                        cudaStream_t s)
+{
+    k_deformation<<<1, OBS_BLOCK, 0, s>>>(dim, q, N, tri, M, out);
+}
+
 void launch_observables(int dim, const double* q, int N, const int* tri, int M,
                         const double* mass_partial, int n_partial, double xi, double wall_plane,
                         double* out, cudaStream_t s)

@@ -25,7 +25,7 @@
 
 namespace iblb {
 
-template <int Q, int ST, bool WRITE_ALL, int BLOCK, bool CS>
+template <int Q, int ST, bool WRITE_ALL, int BLOCK, bool CS, bool EXT = false>
 __global__ void __launch_bounds__(BLOCK)
 k_stream_collide(const typename StorageT<ST>::S* __restrict__ fin,
                  typename StorageT<ST>::S* __restrict__ fout,
@@ -96,10 +96,15 @@ k_stream_collide(const typename StorageT<ST>::S* __restrict__ fin,
             const int sy = cy == 0 ? y : (cy > 0 ? ym : yp);
             src = ((long long)sa * ny + sy) * nx + sx;
         }
-        if (solid)
+        if (solid) {
             g[i] = T::load(fin, (long long)L::opp(i) * nc + cell, p.inv_scale);
-        else
+            if (EXT && p.moving) {  // moving wall: + 2 w_i (c_i . u_w) / c_s^2 (rho_w = 1)
+                const double* uw = cw > 0 ? p.uw_lo : p.uw_hi;
+                g[i] += (R)(6.0 * L::w(i) * (cx * uw[0] + cy * uw[1] + cz * uw[2]));
+            }
+        } else {
             g[i] = T::load(fin, (long long)i * nc + src, p.inv_scale);
+        }
     }
 
     R Fx = (R)p.body[0], Fy = (R)p.body[1], Fz = (R)p.body[2];
@@ -114,7 +119,12 @@ k_stream_collide(const typename StorageT<ST>::S* __restrict__ fin,
         }
     }
     const CellMoments<Q, R> mo = cell_moments<Q, R>(g, Fx, Fy, Fz);
-    cell_collide<Q, R>(g, mo, (R)p.omega, Fx, Fy, Fz);
+    double om = p.omega;
+    if (EXT && p.two_tau) {  // viscosity ratio: outside the interface relax with omega_out
+        const int col = (D == 2) ? x : x + nx * y;
+        if (!inside_cell(p.col_cnt, p.col_z, col, a)) om = p.omega_out;
+    }
+    cell_collide<Q, R>(g, mo, (R)om, Fx, Fy, Fz);
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         if (CS)
@@ -158,9 +168,36 @@ static void launch_sc_b(bool write_all, const void* fin, void* fout, void* mom, 
 }
 
 template <int Q, int ST>
+static void launch_sc_ext(bool write_all, const void* fin, void* fout, void* mom, void* F,
+                              uint8_t* flags, const StreamParams& p, cudaStream_t s)
+{
+    using T = StorageT<ST>;
+    const int woff = p.g.walls ? 1 : 0;
+    dim3 grid((p.g.nx + 127) / 128, 1, 1);
+    if (Q == 9) {
+        grid.y = p.g.ny - 2 * woff;
+    } else {
+        grid.y = p.g.ny;
+        grid.z = p.g.nz - 2 * woff;
+    }
+    auto* a = (const typename T::S*)fin;
+    auto* b = (typename T::S*)fout;
+    auto* m = (typename T::R*)mom;
+    auto* f = (typename T::R*)F;
+    if (write_all)
+        k_stream_collide<Q, ST, true, 128, false, true><<<grid, 128, 0, s>>>(a, b, m, f, flags, p);
+    else
+        k_stream_collide<Q, ST, false, 128, false, true><<<grid, 128, 0, s>>>(a, b, m, f, flags, p);
+}
+
+template <int Q, int ST>
 static void launch_sc_t(bool write_all, const void* fin, void* fout, void* mom, void* F,
                         uint8_t* flags, const StreamParams& p, const Tuning& tu, cudaStream_t s)
 {
+    if (p.two_tau || p.moving) {  // the variant with per-cell tau and moving walls
+        launch_sc_ext<Q, ST>(write_all, fin, fout, mom, F, flags, p, s);
+        return;
+    }
     const bool cs = tu.streaming_stores != 0;
     switch (tu.block_x) {
         case 64:
@@ -460,6 +497,47 @@ void launch_unpack_populations(int Q, int storage, const void* src, double* f, l
     if (storage == ST_FP64) k_unpack<ST_FP64><<<gb, 256, 0, s>>>(Q, (const double*)src, f, ncell, inv_scale);
     else if (storage == ST_FP32) k_unpack<ST_FP32><<<gb, 256, 0, s>>>(Q, (const float*)src, f, ncell, inv_scale);
     else k_unpack<ST_FP16><<<gb, 256, 0, s>>>(Q, (const __half*)src, f, ncell, inv_scale);
+}
+
+template <int Q, int ST>
+__global__ void k_set_equilibrium(int dim, const double* __restrict__ rho,
+                                  const double* __restrict__ u, typename StorageT<ST>::S* dst,
+                                  long long ncell, float scale)
+{
+    using L = Stencil<Q>;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+         c += (long long)gridDim.x * blockDim.x) {
+        const double r = rho ? rho[c] : 1.0;
+        const double ux = u[c], uy = u[ncell + c], uz = dim == 3 ? u[2 * ncell + c] : 0.0;
+        const double uu = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            const double cu = L::cx(i) * ux + L::cy(i) * uy + L::cz(i) * uz;
+            // f_eq - w_i (Eq. 3 written for the deviation)
+            const double dev = L::w(i) * ((r - 1.0) + r * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu));
+            StorageT<ST>::store(dst, (long long)i * ncell + c, (typename StorageT<ST>::R)dev, scale);
+        }
+    }
+}
+
+template <int Q>
+static void launch_set_eq_q(int storage, int dim, const double* rho, const double* u, void* dst,
+                            long long ncell, float scale, cudaStream_t s)
+{
+    const int gb = grid_for(ncell);
+    if (storage == ST_FP64)
+        k_set_equilibrium<Q, ST_FP64><<<gb, 256, 0, s>>>(dim, rho, u, (double*)dst, ncell, scale);
+    else if (storage == ST_FP32)
+        k_set_equilibrium<Q, ST_FP32><<<gb, 256, 0, s>>>(dim, rho, u, (float*)dst, ncell, scale);
+    else
+        k_set_equilibrium<Q, ST_FP16><<<gb, 256, 0, s>>>(dim, rho, u, (__half*)dst, ncell, scale);
+}
+
+void launch_set_equilibrium(int Q, int storage, int dim, const double* rho, const double* u,
+                            void* dst, long long ncell, float scale, cudaStream_t s)
+{
+    if (Q == 9) launch_set_eq_q<9>(storage, dim, rho, u, dst, ncell, scale, s);
+    else launch_set_eq_q<19>(storage, dim, rho, u, dst, ncell, scale, s);
 }
 
 __device__ __forceinline__ bool is_solid_cell(const GridParams& g, long long c)

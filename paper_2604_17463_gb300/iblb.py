@@ -24,7 +24,8 @@ STORAGE_NAMES = {"fp64": FP64, "fp32": FP32_DEV, "fp16": FP16_DEV}
 
 IBLB_OK = 0
 STATUS = {0: "IBLB_OK", 1: "IBLB_EINVAL", 2: "IBLB_ENOMEM", 3: "IBLB_ECUDA",
-          4: "IBLB_ENODE_IN_WALL", 5: "IBLB_ENONFINITE", 6: "IBLB_ETIMEOUT", 7: "IBLB_EAGAIN"}
+          4: "IBLB_ENODE_IN_WALL", 5: "IBLB_ENONFINITE", 6: "IBLB_ETIMEOUT", 7: "IBLB_EAGAIN",
+          8: "IBLB_ECLASSIFY"}
 K_FORCES, K_SPREAD, K_STREAM_COLLIDE, K_INTERP_ADVECT, K_COUNT = 0, 1, 2, 3, 4
 KERNEL_NAMES = ["forces", "spread", "stream_collide", "interp_advect"]
 
@@ -52,6 +53,9 @@ class Config(ctypes.Structure):
         ("body_force", ctypes.c_double * 3),
         ("storage", ctypes.c_int),
         ("fp16_scale_exp", ctypes.c_int),
+        ("tau_out", ctypes.c_double),
+        ("wall_u_lo", ctypes.c_double * 3),
+        ("wall_u_hi", ctypes.c_double * 3),
     ]
 
 
@@ -129,6 +133,9 @@ def load():
         "iblb_nodal_forces": (st, [vp, dp, dp, dp]),
         "iblb_force_field": (st, [vp, dp]),
         "iblb_interpolate": (st, [vp, dp, dp]),
+        "iblb_inside_mask": (st, [vp, ctypes.POINTER(ctypes.c_ubyte)]),
+        "iblb_set_equilibrium": (st, [vp, dp, dp]),
+        "iblb_deformation": (st, [vp, dp]),
         "iblb_step_profiled": (st, [vp, ip, dp]),
         "iblb_set_tuning": (st, [vp, ctypes.POINTER(Tuning)]),
         "iblb_get_tuning": (st, [vp, ctypes.POINTER(Tuning)]),
@@ -189,7 +196,8 @@ def current_stream_handle() -> int:
 
 def make_config(lattice, nx, ny, nz=1, *, tau=1.0, walls=True, wetting=True, sigma=1e-3, xi=1.0,
                 theta_eq_deg=90.0, pi_n=9, pi_m=3, body_force=(0.0, 0.0, 0.0), storage=FP64,
-                fp16_scale_exp=0) -> Config:
+                fp16_scale_exp=0, tau_out=0.0, wall_u_lo=(0.0, 0.0, 0.0),
+                wall_u_hi=(0.0, 0.0, 0.0)) -> Config:
     c = Config()
     c.lattice = lattice
     c.nx, c.ny, c.nz = nx, ny, (1 if lattice == D2Q9 else nz)
@@ -204,6 +212,10 @@ def make_config(lattice, nx, ny, nz=1, *, tau=1.0, walls=True, wetting=True, sig
         c.body_force[k] = body_force[k] if k < len(body_force) else 0.0
     c.storage = STORAGE_NAMES.get(storage, storage) if isinstance(storage, str) else storage
     c.fp16_scale_exp = fp16_scale_exp
+    c.tau_out = tau_out
+    for k in range(3):
+        c.wall_u_lo[k] = wall_u_lo[k] if k < len(wall_u_lo) else 0.0
+        c.wall_u_hi[k] = wall_u_hi[k] if k < len(wall_u_hi) else 0.0
     return c
 
 
@@ -417,6 +429,25 @@ class Simulation:
     @property
     def variant(self):
         return iblb_stream_collide_variant(self.h)
+
+    def set_equilibrium(self, u, rho=None):
+        """Populations = f_eq(rho, u) (Eq. 3); u [dim] + lattice shape."""
+        u = np.ascontiguousarray(u, dtype=np.float64).reshape(self.dim, self.ncell)
+        r = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64).reshape(self.ncell)
+        _check(self.h, load().iblb_set_equilibrium(self.h, None if r is None else _dptr(r),
+                                                    _dptr(u)))
+
+    def deformation(self):
+        """Deformation index of the interface in the shear plane (Sec. 4, Eq. 12)."""
+        out = np.zeros(5)
+        _check(self.h, load().iblb_deformation(self.h, _dptr(out)))
+        return dict(D=out[0], r1=out[1], r3=out[2], angle_deg=out[3], volume=out[4])
+
+    def inside_mask(self):
+        m = np.zeros(self.ncell, dtype=np.uint8)
+        _check(self.h, load().iblb_inside_mask(
+            self.h, m.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))))
+        return m.reshape(self.shape)
 
     def step_profiled(self, n):
         return iblb_step_profiled(self.h, n)

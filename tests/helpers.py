@@ -48,3 +48,29 @@ def small_2d(nx=40, ny=30, R=7.0, theta=60.0, tau=0.9, sigma=5e-3, xi=1.0, N=Non
 def small_3d(n=24, nz=20, R=6.0, level=2, theta=75.0, tau=0.8, sigma=5e-3, xi=1.0):
     nodes, faces = W.icosphere(level, R, (n / 2.0 + 0.31, n / 2.0 - 0.22, W.WALL_PLANE + R + 2 * xi))
     return W.Workload("small3d", 19, n, n, nz, tau, sigma, xi, theta, 9, 3, 100, nodes, faces)
+
+
+def star(n_arms, r_in, r_out, centre, per_arm=24, phase=0.17):
+    pts = []
+    for k in range(n_arms * 2):
+        r0 = r_out if k % 2 == 0 else r_in
+        r1 = r_in if k % 2 == 0 else r_out
+        a0 = phase + math.pi * k / n_arms
+        a1 = phase + math.pi * (k + 1) / n_arms
+        for t in np.linspace(0, 1, per_arm, endpoint=False):
+            p0 = np.array([r0 * math.cos(a0), r0 * math.sin(a0)])
+            p1 = np.array([r1 * math.cos(a1), r1 * math.sin(a1)])
+            pts.append(centre + (1 - t) * p0 + t * p1)
+    return np.array(pts)
+
+
+def box_mesh(lo, hi):
+    x0, y0, z0 = lo
+    x1, y1, z1 = hi
+    v = np.array([[x0, y0, z0], [x1, y0, z0], [x1, y1, z0], [x0, y1, z0],
+                  [x0, y0, z1], [x1, y0, z1], [x1, y1, z1], [x0, y1, z1]])
+    quads = [(0, 3, 2, 1), (4, 5, 6, 7), (0, 1, 5, 4), (1, 2, 6, 5), (2, 3, 7, 6), (3, 0, 4, 7)]
+    tri = []
+    for a, b, c, d in quads:   # outward orientation
+        tri += [(a, b, c), (a, c, d)]
+    return v, np.array(tri, dtype=np.int32)
