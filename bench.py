@@ -436,6 +436,62 @@ def run_serve_mode(args):
     return 0
 
 
+def run_shear_mode(args):
+    """Drop in shear at the paper's parameters (Sec. 4: Re = 0.01, Ca = 0.05,
+    R0 = 19, tau = 1, lambda from --shear-lam): moving-wall bounce-back, the
+    fully developed linear profile as initial state, D (Eq. 12) sampled 24
+    times, the last sample against Eq. 13.  Throughput is fluid-cell updates
+    per second over the whole run (every step, every sample)."""
+    import torch
+    from paper_2604_17463_gb300 import iblb
+    from paper_2604_17463_gb300 import workloads as W
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    tau = 1.0
+    tau_out = 0.5 + (tau - 0.5) / args.shear_lam
+    case = W.shear_drop(tau=tau, tau_out=tau_out, t_mu_count=args.shear_t_mu)
+    wl = case.work
+    storage = {"fp32": iblb.FP32_DEV, "fp16": iblb.FP16_DEV, "fp64": iblb.FP64}[args.storage]
+    stream = torch.cuda.current_stream()
+    g = iblb.Simulation.from_workload(wl, storage=storage, stream=stream.cuda_stream,
+                                      tau_out=case.tau_out, wall_u_lo=case.wall_u_lo,
+                                      wall_u_hi=case.wall_u_hi)
+    g.set_equilibrium(case.initial_velocity())
+    samples = 24
+    per = wl.steps // samples
+    n0 = iblb.iblb_kernel_launch_count()
+    hist = []
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    ev0.record(stream)
+    for k in range(samples):
+        g.step(per)
+        d = g.deformation()
+        hist.append([round((k + 1) * per / case.t_mu, 3), d["D"], d["angle_deg"]])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ms = ev0.elapsed_time(ev1)
+    launches = iblb.iblb_kernel_launch_count() - n0
+    g.close()
+    steps = per * samples
+    D_end, D_inf = hist[-1][1], case.d_inf()
+    line = {
+        "metric": "mlups", "value": wl.fluid_cells * steps / (ms * 1e-3) / 1e6, "unit": "MLUPS",
+        "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+        "dtype": {"fp32": "f32", "fp16": "f32 (binary16 storage)", "fp64": "f64"}[args.storage],
+        "config": {"workload": f"drop in shear, D3Q19 {wl.nx}x{wl.ny}x{wl.nz}, R0 = {case.R0:g}, "
+                               f"{len(wl.nodes)} nodes, Re = {case.Re:g}, Ca = {case.Ca:g}, "
+                               f"lambda = {case.lam:g}, {steps} steps ({args.shear_t_mu:g} t_mu)",
+                   "mode": "shear"},
+        "D_end": D_end, "D_inf_eq13": D_inf, "rel_distance": abs(D_end - D_inf) / D_inf,
+        "inclination_deg": hist[-1][2], "device_s": ms * 1e-3, "wall_s": wall,
+        "history_t_over_t_mu_D_angle": hist, "gpu_launches": int(launches),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -444,7 +500,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve"],
+    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve", "shear"],
                     help="step: the 3D workload (default); batch / serve: the batched "
                          "and served engines")
     ap.add_argument("--count", type=int, default=256, help="batch / serve: simulations")
@@ -454,6 +510,8 @@ def main():
     ap.add_argument("--chunk", type=int, default=500, help="serve: steps per scheduling round")
     ap.add_argument("--oracle-sample", type=int, default=6, help="serve: oracle-checked requests")
     ap.add_argument("--serve-storage", default="fp16", choices=["fp32", "fp16", "fp64"])
+    ap.add_argument("--shear-lam", type=float, default=1.0, help="shear: viscosity ratio")
+    ap.add_argument("--shear-t-mu", type=float, default=12.0, help="shear: run length in t_mu")
     ap.add_argument("--tuning", default="",
                     help="fixed stream-collide launch shape 'variant,block_x,rows,ctas,warps' "
                          "instead of the autotuner (used for profiler runs)")
@@ -464,6 +522,8 @@ def main():
         return run_batch_mode(args)
     if args.mode == "serve":
         return run_serve_mode(args)
+    if args.mode == "shear":
+        return run_shear_mode(args)
     from paper_2604_17463_gb300 import workloads as W
     wl = W.config3()
     if args.impl == "reference":

@@ -258,3 +258,89 @@ def random_perturbation(shape, seed: int, scale: float = 1.0) -> np.ndarray:
     """Seeded uniform noise in [-scale, scale]."""
     rng = np.random.default_rng(seed)
     return rng.uniform(-scale, scale, size=shape)
+
+
+# --------------------------------------------------------- drop in shear flow
+@dataclasses.dataclass
+class ShearDrop:
+    """A free drop at the centre of a wall-bounded shear flow (Sec. 4): walls
+    at z = 1/2 and z = nz - 3/2 (y in 2D) moving at -/+ gamma_dot H / 2 along
+    x, the fluid initially in the fully developed linear profile.  Re and Ca
+    use the outer (matrix) viscosity mu = (tau_out - 1/2) / 3 and rho = 1:
+    Re = gamma_dot R0^2 / nu, Ca = mu gamma_dot R0 / sigma; the viscosity
+    ratio is lambda = (tau - 1/2) / (tau_out - 1/2)."""
+    work: Workload
+    gamma_dot: float
+    tau_out: float
+    Re: float
+    Ca: float
+    R0: float
+
+    @property
+    def lam(self) -> float:
+        return (self.work.tau - 0.5) / (self.tau_out - 0.5)
+
+    @property
+    def height(self) -> float:
+        wl = self.work
+        return float((wl.ny if wl.dim == 2 else wl.nz) - 2)
+
+    @property
+    def wall_u_lo(self):
+        return (-0.5 * self.gamma_dot * self.height, 0.0, 0.0)
+
+    @property
+    def wall_u_hi(self):
+        return (0.5 * self.gamma_dot * self.height, 0.0, 0.0)
+
+    @property
+    def t_mu(self) -> float:
+        """Capillary time mu R0 / sigma = Ca / gamma_dot (steps)."""
+        return self.Ca / self.gamma_dot
+
+    def d_inf(self) -> float:
+        """Small-deformation steady deformation of an unbounded 3D drop
+        (Sec. 4, Eq. 13): (19 lambda + 16) / (16 lambda + 16) Ca."""
+        lam = self.lam
+        return (19.0 * lam + 16.0) / (16.0 * lam + 16.0) * self.Ca
+
+    def initial_velocity(self) -> np.ndarray:
+        """Linear shear profile u_x = gamma_dot (a - a_c) on the fluid layers
+        (zero in the solid layers), [dim][nz][ny][nx]."""
+        wl = self.work
+        u = np.zeros((wl.dim, wl.nz, wl.ny, wl.nx))
+        La = wl.ny if wl.dim == 2 else wl.nz
+        ac = 0.5 + 0.5 * self.height
+        prof = self.gamma_dot * (np.arange(La) - ac)
+        prof[0] = prof[-1] = 0.0
+        if wl.dim == 2:
+            u[0] = prof[None, :, None]
+        else:
+            u[0] = prof[:, None, None]
+        return u
+
+
+def shear_drop(R0: float = 19.0, Re: float = 0.01, Ca: float = 0.05, tau: float = 1.0,
+               tau_out: Optional[float] = None, nx: int = 160, ny: int = 128, nz: int = 242,
+               level: Optional[int] = None, t_mu_count: float = 12.0,
+               lattice: int = 19) -> ShearDrop:
+    """The drop-in-shear case of Sec. 4 (defaults: Re = 0.01, Ca = 0.05,
+    R0 = 19, tau = 1, lambda = 1) in a channel of nz - 2 fluid layers.  The
+    drop centre is offset by a fraction of a lattice spacing from the
+    lattice's symmetry planes.  Steps: t_mu_count capillary times."""
+    tau_out = tau if tau_out is None else tau_out
+    nu = (tau_out - 0.5) / 3.0
+    gamma_dot = Re * nu / (R0 * R0)
+    sigma = nu * gamma_dot * R0 / Ca
+    if lattice == 19:
+        lvl = icosphere_level_for(R0, 0.8) if level is None else level
+        nodes, faces = icosphere(lvl, R0, (nx / 2.0 + 0.13, ny / 2.0 - 0.21, 0.5 + 0.5 * (nz - 2) + 0.07))
+    else:
+        n = int(round(2 * math.pi * R0 / 0.7))
+        nodes = circle(n, R0, (nx / 2.0 + 0.13, 0.5 + 0.5 * (ny - 2) + 0.07))
+        faces = None
+        nz = 1
+    steps = int(round(t_mu_count * Ca / gamma_dot))
+    wl = Workload(f"shear_drop_R{R0:g}_Ca{Ca:g}_Re{Re:g}", lattice, nx, ny, nz, tau, sigma,
+                  0.05 * R0, 90.0, 9, 3, steps, nodes, faces, walls=True, wetting=False)
+    return ShearDrop(wl, gamma_dot, tau_out, Re, Ca, R0)

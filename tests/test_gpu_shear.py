@@ -1,0 +1,150 @@
+"""GPU parity and validation of the drop-in-shear pieces (Sec. 4): moving-wall
+bounce-back, equilibrium initialisation, the deformation index D (Eq. 12),
+and the steady deformation of the paper's case against Eq. 13.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_17463_gb300 import iblb
+from paper_2604_17463_gb300 import workloads as W
+from helpers import fluid_mask, oracle_from_workload, rel_l2, small_2d, small_3d
+
+pytestmark = pytest.mark.gpu
+
+
+def couette_profile(u_lo, u_hi, L):
+    a = np.arange(1, L - 1)
+    return u_lo + (u_hi - u_lo) * (a - 0.5) / (L - 2)
+
+
+@pytest.mark.parametrize("storage,tol", [(iblb.FP64, 1e-13), (iblb.FP32_DEV, 2e-7)])
+def test_couette_2d_and_3d(storage, tol):
+    # exact steady solution of BGK with halfway bounce-back (closed form)
+    g = iblb.Simulation(9, 37, 14, tau=0.8, wetting=False, sigma=0.0, storage=storage,
+                        wall_u_lo=(-0.01, 0.0), wall_u_hi=(0.02, 0.0))
+    g.step(12000)
+    _, u, _ = g.fields()
+    assert np.max(np.abs(u[0, 0, 1:-1, :] - couette_profile(-0.01, 0.02, 14)[:, None])) < tol
+    assert np.max(np.abs(u[1, 0, 1:-1, :])) < tol
+    g.close()
+    g = iblb.Simulation(19, 33, 5, 12, tau=0.9, wetting=False, sigma=0.0, storage=storage,
+                        wall_u_lo=(0.01, -0.005, 0.0), wall_u_hi=(-0.02, 0.015, 0.0))
+    g.step(12000)
+    _, u, _ = g.fields()
+    for k, (lo, hi) in enumerate([(0.01, -0.02), (-0.005, 0.015)]):
+        assert np.max(np.abs(u[k, 1:-1] - couette_profile(lo, hi, 12)[:, None, None])) < tol
+    g.close()
+
+
+@pytest.mark.parametrize("Q,dims", [(9, (45, 17, 1)), (19, (13, 9, 7))])
+@pytest.mark.parametrize("storage,tol", [(iblb.FP64, 1e-16), (iblb.FP32_DEV, 1e-8),
+                                         (iblb.FP16_DEV, 1e-4)])
+def test_set_equilibrium_matches_oracle(Q, dims, storage, tol):
+    nx, ny, nz = dims
+    dim = 2 if Q == 9 else 3
+    rng = np.random.default_rng(11)
+    rho = 1.0 + 0.02 * rng.standard_normal((nz, ny, nx))
+    u = 0.03 * rng.standard_normal((dim, nz, ny, nx))
+    o = oracle.Sim(Q, nx, ny, nz, walls=False, wetting=False, sigma=0.0)
+    g = iblb.Simulation(Q, nx, ny, nz, walls=False, wetting=False, sigma=0.0, storage=storage)
+    o.set_equilibrium(u, rho)
+    g.set_equilibrium(u, rho)
+    assert np.max(np.abs(g.populations() - o.populations())) < tol
+    o.set_equilibrium(u)
+    g.set_equilibrium(u)
+    assert np.max(np.abs(g.populations() - o.populations())) < tol
+    g.close()
+
+
+@pytest.mark.parametrize("which,steps,tau_out", [("2d", 60, 0.0), ("2d", 60, 0.65),
+                                                 ("3d", 12, 0.0), ("3d", 12, 1.15)])
+def test_moving_walls_with_a_drop_fp64(which, steps, tau_out):
+    wl = small_2d(tau=0.9) if which == "2d" else small_3d(tau=0.8)
+    lo = (-0.004, 0.0, 0.0) if which == "2d" else (-0.004, 0.002, 0.0)
+    hi = (0.004, 0.0, 0.0) if which == "2d" else (0.003, -0.001, 0.0)
+    o = oracle_from_workload(wl, tau_out=tau_out, wall_u_lo=lo, wall_u_hi=hi)
+    g = iblb.Simulation.from_workload(wl, tau_out=tau_out, wall_u_lo=lo, wall_u_hi=hi)
+    assert o.step(steps) == 0
+    g.step(steps)
+    ro, uo, qo = o.fields()
+    rg, ug, qg = g.fields()
+    m = fluid_mask(o.shape, wl.dim)
+    assert rel_l2(rg[m] - 1.0, ro[m] - 1.0) < 1e-9
+    assert rel_l2(ug[:, m], uo[: wl.dim, m]) < 1e-10
+    assert np.max(np.abs(qg - qo)) < 1e-11
+    assert abs(g.deformation()["D"] - o.deformation()["D"]) < 1e-12
+    g.close()
+
+
+def test_deformation_matches_oracle():
+    t = np.linspace(0, 2 * math.pi, 240, endpoint=False)
+    r = 9.0 + 2.5 * np.sin(2 * t + 0.3) + 1.5 * np.cos(3 * t)
+    ring = np.stack([r * np.cos(t) + 30.2, r * np.sin(t) + 20.7], 1)
+    g = iblb.Simulation(9, 64, 48, walls=False, wetting=False)
+    g.set_interface(ring)
+    dg, do = g.deformation(), oracle.deformation(ring)
+    for k in ("D", "r1", "r3", "angle_deg", "volume"):
+        assert math.isclose(dg[k], do[k], rel_tol=1e-12, abs_tol=1e-12), k
+    g.close()
+    q, tri = W.icosphere(4, 1.0, (0.0, 0.0, 0.0))
+    q = q * np.array([9.0, 7.0, 6.0])
+    th = math.radians(25.0)
+    Rm = np.array([[math.cos(th), 0, -math.sin(th)], [0, 1, 0], [math.sin(th), 0, math.cos(th)]])
+    q = q @ Rm.T + np.array([16.3, 15.1, 14.2])
+    g = iblb.Simulation(19, 32, 32, 30, walls=False, wetting=False)
+    g.set_interface(q, tri)
+    dg, do = g.deformation(), oracle.deformation(q, tri)
+    for k in ("D", "r1", "r3", "angle_deg", "volume"):
+        assert math.isclose(dg[k], do[k], rel_tol=1e-12, abs_tol=1e-12), k
+    assert abs(dg["D"] - 3.0 / 15.0) < 1e-12
+    g.close()
+
+
+def test_moving_wall_validation():
+    with pytest.raises(iblb.IBLBError):   # wall-normal component
+        iblb.Simulation(9, 16, 12, wall_u_lo=(0.0, 0.01))
+    with pytest.raises(iblb.IBLBError):   # no walls
+        iblb.Simulation(9, 16, 12, walls=False, wall_u_hi=(0.01, 0.0))
+    with pytest.raises(iblb.IBLBError):   # too fast
+        iblb.Simulation(19, 8, 8, 8, wall_u_hi=(0.5, 0.0, 0.0))
+    b = iblb.Batch(iblb.D2Q9, iblb.FP32_DEV, 1 << 28, max_slots=4)
+    with pytest.raises(iblb.IBLBError):
+        b.admit_workload(small_2d(), wall_u_hi=(0.01, 0.0, 0.0))
+    b.close()
+
+
+def run_shear(case, storage, samples=24):
+    wl = case.work
+    g = iblb.Simulation.from_workload(wl, storage=storage, tau_out=case.tau_out,
+                                      wall_u_lo=case.wall_u_lo, wall_u_hi=case.wall_u_hi)
+    g.set_equilibrium(case.initial_velocity())
+    per = wl.steps // samples
+    hist = []
+    for k in range(samples):
+        g.step(per)
+        d = g.deformation()
+        hist.append(((k + 1) * per / case.t_mu, d["D"], d["angle_deg"]))
+    obs = g.observables()
+    g.close()
+    return hist, obs
+
+
+def test_shear_drop_paper_case_fp32():
+    # Sec. 4: Re = 0.01, Ca = 0.05, R0 = 19, tau = 1 (lambda = 1), 12 t_mu
+    case = W.shear_drop()
+    hist, obs = run_shear(case, iblb.FP32_DEV)
+    D_end = hist[-1][1]
+    err = abs(D_end - case.d_inf()) / case.d_inf()
+    print(f"shear drop: D(12 t_mu) = {D_end:.5f}, Eq. 13 {case.d_inf():.5f}, "
+          f"rel. distance {err * 100:.2f} %, inclination {hist[-1][2]:.1f} deg")
+    assert err < 0.05
+    # steady: the last quarter changes by < 1 %
+    assert abs(hist[-1][1] - hist[-6][1]) < 0.01 * D_end
+    # D grows from 0 monotonically in the transient
+    Ds = [h[1] for h in hist[:8]]
+    assert all(b > a for a, b in zip(Ds, Ds[1:]))
+    # small deformation: the long axis leans towards 45 degrees
+    assert 20.0 < hist[-1][2] < 50.0
