@@ -436,6 +436,119 @@ def run_serve_mode(args):
     return 0
 
 
+def _oracle_spread_trajectory(job):
+    """Oracle trajectory of one downscaled spreading case (runs in a spawned
+    worker process): observables at each checkpoint."""
+    theta, tau, steps, checkpoints = job
+    import oracle
+    from paper_2604_17463_gb300 import workloads as W
+    wl = W.config2(theta_eq_deg=theta, tau=tau, downscale=4)
+    o = oracle.Sim(9, wl.nx, wl.ny, tau=wl.tau, sigma=wl.sigma, xi=wl.xi,
+                   theta_eq_deg=wl.theta_eq_deg, pi_n=wl.pi_n, pi_m=wl.pi_m)
+    o.set_interface(wl.nodes)
+    out = []
+    for _ in range(checkpoints):
+        o.step(steps // checkpoints)
+        out.append(o.observables())
+    o.close()
+    return out
+
+
+def run_spread2d_mode(args):
+    """The 2D spreading sweep (2048x512 D2Q9, R = 200, 2000 nodes, initial
+    angle 150 deg; theta_eq in {30, 60, 90, 120}, tau in {0.6, 1.0}; 200k
+    steps / step_div): FP64, FP32 and binary16 storage on the GPU, contact
+    angle, contact-line radius and film against the FP64 GPU run along the
+    whole run; and the 4x-downscaled copy (512x128, 200k/16 steps / step_div,
+    the same number of viscous times) in FP32 / binary16 against the FP64
+    oracle, whose runs go to spawned worker processes started before the
+    first GPU call."""
+    import multiprocessing as mp
+    thetas, taus = (30.0, 60.0, 90.0, 120.0), (0.6, 1.0)
+    combos = [(t, tau) for t in thetas for tau in taus]
+    cps = 20
+    steps_full = 200000 // args.step_div
+    steps_ds = 200000 // 16 // args.step_div
+    ctx = mp.get_context("spawn")
+    pool = ctx.Pool(min(len(combos), os.cpu_count() or 1))
+    t_or = time.perf_counter()
+    pending = pool.map_async(_oracle_spread_trajectory,
+                             [(t, tau, steps_ds, cps) for t, tau in combos])
+    import torch
+    from paper_2604_17463_gb300 import iblb
+    from paper_2604_17463_gb300 import workloads as W
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+    names = {iblb.FP64: "fp64", iblb.FP32_DEV: "fp32", iblb.FP16_DEV: "fp16"}
+    n0 = iblb.iblb_kernel_launch_count()
+
+    def traj(wl, storage, steps):
+        g = iblb.Simulation.from_workload(wl, storage=storage, stream=stream.cuda_stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        out = []
+        e0.record(stream)
+        for _ in range(cps):
+            g.step(steps // cps)
+            out.append(g.observables())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        g.close()
+        return out, e0.elapsed_time(e1) * 1e-3
+
+    def compare(got, ref, xi):
+        dth = [abs(a["theta_deg"] - b["theta_deg"]) for a, b in zip(got, ref)
+               if np.isfinite(a["theta_deg"]) and np.isfinite(b["theta_deg"])]
+        drc = [abs(a["r_cl"] - b["r_cl"]) / max(b["r_cl"], 1.0) for a, b in zip(got, ref)]
+        dfilm = [abs(a["film"] - b["film"]) / xi for a, b in zip(got, ref)
+                 if np.isfinite(a["film"]) and np.isfinite(b["film"])]
+        return {"max_dtheta_deg": max(dth) if dth else None,
+                "max_rel_dr_cl": max(drc), "max_dfilm_over_xi": max(dfilm) if dfilm else None}
+
+    full, ds = [], []
+    dev_s = {n: 0.0 for n in names.values()}
+    for theta, tau in combos:
+        wl = W.config2(theta_eq_deg=theta, tau=tau)
+        runs = {}
+        for st in (iblb.FP64, iblb.FP32_DEV, iblb.FP16_DEV):
+            runs[st], sec = traj(wl, st, steps_full)
+            dev_s[names[st]] += sec
+        ref = runs[iblb.FP64]
+        full.append({"theta_eq": theta, "tau": tau,
+                     "fp32_vs_fp64": compare(runs[iblb.FP32_DEV], ref, wl.xi),
+                     "fp16_vs_fp64": compare(runs[iblb.FP16_DEV], ref, wl.xi),
+                     "final": {n: {k: runs[st][-1][k] for k in ("theta_deg", "r_cl", "film")}
+                               for st, n in names.items()},
+                     "theta_t_fp16": [round(o["theta_deg"], 3) for o in runs[iblb.FP16_DEV]]})
+        wd = W.config2(theta_eq_deg=theta, tau=tau, downscale=4)
+        ds.append({"theta_eq": theta, "tau": tau, "wl": wd,
+                   "gpu": {st: traj(wd, st, steps_ds)[0] for st in (iblb.FP32_DEV, iblb.FP16_DEV)}})
+    launches = iblb.iblb_kernel_launch_count() - n0
+    oracle_runs = pending.get()
+    pool.close()
+    t_or = time.perf_counter() - t_or
+    for d, orc in zip(ds, oracle_runs):
+        d["fp32_vs_oracle"] = compare(d["gpu"][iblb.FP32_DEV], orc, d["wl"].xi)
+        d["fp16_vs_oracle"] = compare(d["gpu"][iblb.FP16_DEV], orc, d["wl"].xi)
+        d["oracle_final_theta"] = orc[-1]["theta_deg"]
+        del d["gpu"], d["wl"]
+    cells = 2048 * 510
+    worst16 = max(f["fp16_vs_fp64"]["max_dtheta_deg"] or 0.0 for f in full)
+    line = {
+        "metric": "max_dtheta_deg_fp16_vs_fp64", "value": worst16, "unit": "deg", "n_gpus": 1,
+        "higher_is_better": False, "data": "synthetic", "dtype": "f32 (fp64 / fp32 / binary16 storage)",
+        "config": {"workload": f"D2Q9 2048x512 spreading, R = 200, 2000 nodes, 150 deg start, "
+                               f"theta_eq {list(thetas)}, tau {list(taus)}, {steps_full} steps; "
+                               f"oracle on the 512x128 copy, {steps_ds} steps",
+                   "mode": "spread2d", "checkpoints": cps},
+        "mlups": {n: len(combos) * cells * steps_full / dev_s[n] / 1e6 for n in names.values()},
+        "full_size": full, "downscaled_vs_oracle": ds, "oracle_wall_s": t_or,
+        "oracle_processes": min(len(combos), os.cpu_count() or 1),
+        "gpu_launches": int(launches),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_shear_mode(args):
     """Drop in shear at the paper's parameters (Sec. 4: Re = 0.01, Ca = 0.05,
     R0 = 19, tau = 1, lambda from --shear-lam): moving-wall bounce-back, the
@@ -500,7 +613,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve", "shear"],
+    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve", "shear", "spread2d"],
                     help="step: the 3D workload (default); batch / serve: the batched "
                          "and served engines")
     ap.add_argument("--count", type=int, default=256, help="batch / serve: simulations")
@@ -524,6 +637,8 @@ def main():
         return run_serve_mode(args)
     if args.mode == "shear":
         return run_shear_mode(args)
+    if args.mode == "spread2d":
+        return run_spread2d_mode(args)
     from paper_2604_17463_gb300 import workloads as W
     wl = W.config3()
     if args.impl == "reference":

@@ -73,3 +73,24 @@ def test_reduced_precision_contact_angle(runs, storage):
 
 def wl_xi():
     return W.config2(downscale=4).xi
+
+
+def test_full_size_spreading_fp16_vs_fp64():
+    # the full 2048 x 512 spreading drop, the most-spreading corner of the
+    # sweep (theta_eq = 30 deg, tau = 0.6), all 200k steps
+    wl = W.config2(theta_eq_deg=30.0, tau=0.6)
+    runs = {}
+    for st in (iblb.FP64, iblb.FP16_DEV):
+        g = iblb.Simulation.from_workload(wl, storage=st)
+        out = []
+        for _ in range(10):
+            g.step(wl.steps // 10)
+            out.append(g.observables())
+        g.close()
+        runs[st] = out
+    worst = max(abs(a["theta_deg"] - b["theta_deg"])
+                for a, b in zip(runs[iblb.FP16_DEV], runs[iblb.FP64]))
+    print(f"2048x512 theta_eq 30 tau 0.6: max |d theta| fp16 vs fp64 = {worst:.4f} deg; "
+          f"final {runs[iblb.FP16_DEV][-1]['theta_deg']:.2f} deg")
+    assert worst < 0.1
+    assert runs[iblb.FP64][-1]["theta_deg"] < 100.0
