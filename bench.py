@@ -513,7 +513,11 @@ def run_spread2d_mode(args):
             runs[st], sec = traj(wl, st, steps_full)
             dev_s[names[st]] += sec
         ref = runs[iblb.FP64]
+        # a second FP64 run: the spread's atomics add in a different order, so
+        # this is the run-to-run spread of the FP64 path itself
+        rep, _ = traj(wl, iblb.FP64, steps_full)
         full.append({"theta_eq": theta, "tau": tau,
+                     "fp64_repeat_vs_fp64": compare(rep, ref, wl.xi),
                      "fp32_vs_fp64": compare(runs[iblb.FP32_DEV], ref, wl.xi),
                      "fp16_vs_fp64": compare(runs[iblb.FP16_DEV], ref, wl.xi),
                      "final": {n: {k: runs[st][-1][k] for k in ("theta_deg", "r_cl", "film")}
@@ -544,6 +548,75 @@ def run_spread2d_mode(args):
         "full_size": full, "downscaled_vs_oracle": ds, "oracle_wall_s": t_or,
         "oracle_processes": min(len(combos), os.cpu_count() or 1),
         "gpu_launches": int(launches),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_spread3d_mode(args):
+    """Paper-scale 3D spreading (Sec. 3: 250x250x150, a hemisphere of R0 = 50
+    on its film spreading to 60 deg, about 120 000 triangles, tau in {0.56,
+    0.59, 0.732, 1.1}; Sec. 4: 300x300x250, a sphere at the film distance
+    spreading to 45 deg at tau = 0.56), FP32 storage: h(t)/R0 over
+    --spread3d-t-mu capillary times, throughput per run, and the per-kernel
+    split of one step on the first lattice."""
+    import torch
+    from paper_2604_17463_gb300 import iblb
+    from paper_2604_17463_gb300 import workloads as W
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+    storage = {"fp32": iblb.FP32_DEV, "fp16": iblb.FP16_DEV, "fp64": iblb.FP64}[args.storage]
+    taus = [float(t) for t in args.spread3d_taus.split(",") if t]
+    cases = [W.spread3d_cap(t, t_mu_count=args.spread3d_t_mu) for t in taus]
+    if args.spread3d_sphere:
+        cases.append(W.spread3d_sphere(t_mu_count=args.spread3d_t_mu))
+    n0 = iblb.iblb_kernel_launch_count()
+    runs = []
+    gp = iblb.Simulation.from_workload(cases[0].work, storage=storage, stream=stream.cuda_stream)
+    ms = gp.step_profiled(50)
+    gp.close()
+    tot = float(ms.sum())
+    split = {k: float(v) / tot for k, v in zip(iblb.KERNEL_NAMES, ms)}
+    split["ms_per_step"] = tot / 50
+    for case in cases:
+        wl = case.work
+        g = iblb.Simulation.from_workload(wl, storage=storage, stream=stream.cuda_stream)
+        samples = 100
+        per = max(1, wl.steps // samples)
+        hist = []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for k in range(samples):
+            g.step(per)
+            o = g.observables()
+            hist.append([round((k + 1) * per / case.t_mu, 3), round(o["height"] / case.R0, 5),
+                         round(o["theta_deg"], 3)])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) * 1e-3
+        o = g.observables()
+        g.close()
+        hs = [h[1] for h in hist]
+        runs.append({"workload": wl.name, "tau": wl.tau, "Re": case.Re, "t_mu_steps": case.t_mu,
+                     "steps": per * samples, "nodes": len(wl.nodes), "faces": len(wl.faces),
+                     "mlups": wl.fluid_cells * per * samples / sec / 1e6, "device_s": sec,
+                     "h_over_R0_final": hs[-1], "h_over_R0_min": min(hs),
+                     "theta_final_deg": o["theta_deg"],
+                     "h_over_R0_t": hist})
+    launches = iblb.iblb_kernel_launch_count() - n0
+    cells = sum(c.work.fluid_cells * r["steps"] for c, r in zip(cases, runs))
+    secs = sum(r["device_s"] for r in runs)
+    line = {
+        "metric": "mlups", "value": cells / secs / 1e6, "unit": "MLUPS", "n_gpus": 1,
+        "higher_is_better": True, "data": "synthetic",
+        "dtype": {"fp32": "f32", "fp16": "f32 (binary16 storage)", "fp64": "f64"}[args.storage],
+        "config": {"workload": "paper-scale 3D spreading: 250x250x150 hemisphere R0 = 50 -> 60 deg, "
+                               f"tau {taus}" + (", 300x300x250 sphere -> 45 deg, tau 0.56"
+                                                if args.spread3d_sphere else "")
+                               + f", ~120k triangles, {args.spread3d_t_mu:g} t_mu each",
+                   "mode": "spread3d"},
+        "step_split_first_lattice": split, "runs": runs, "gpu_launches": int(launches),
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -613,7 +686,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve", "shear", "spread2d"],
+    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve", "shear", "spread2d", "spread3d"],
                     help="step: the 3D workload (default); batch / serve: the batched "
                          "and served engines")
     ap.add_argument("--count", type=int, default=256, help="batch / serve: simulations")
@@ -624,6 +697,12 @@ def main():
     ap.add_argument("--oracle-sample", type=int, default=6, help="serve: oracle-checked requests")
     ap.add_argument("--serve-storage", default="fp16", choices=["fp32", "fp16", "fp64"])
     ap.add_argument("--shear-lam", type=float, default=1.0, help="shear: viscosity ratio")
+    ap.add_argument("--spread3d-taus", default="0.56,0.59,0.732,1.1",
+                    help="spread3d: relaxation times of the 250x250x150 runs")
+    ap.add_argument("--spread3d-sphere", type=int, default=1,
+                    help="spread3d: also run the 300x300x250 sphere case")
+    ap.add_argument("--spread3d-t-mu", type=float, default=50.0,
+                    help="spread3d: run length in capillary times")
     ap.add_argument("--shear-t-mu", type=float, default=12.0, help="shear: run length in t_mu")
     ap.add_argument("--tuning", default="",
                     help="fixed stream-collide launch shape 'variant,block_x,rows,ctas,warps' "
@@ -639,6 +718,8 @@ def main():
         return run_shear_mode(args)
     if args.mode == "spread2d":
         return run_spread2d_mode(args)
+    if args.mode == "spread3d":
+        return run_spread3d_mode(args)
     from paper_2604_17463_gb300 import workloads as W
     wl = W.config3()
     if args.impl == "reference":

@@ -41,6 +41,7 @@ struct SlotDev {
     double omega;
     float omega_f, scale, inv_scale;
     int cur_base;          // current buffer = cur_base ^ batch parity
+    unsigned* rng;         // two-entry step counter for binary16 stochastic rounding
     int cpt;               // cells per thread of this slot's tiles
     double* q;
     double* phi;
@@ -77,6 +78,9 @@ k_b_stream_collide(const SlotDev* __restrict__ slots, const int2* __restrict__ t
         const int2 td = tiles[t];
         const SlotDev& sd = slots[td.x];
         const int cur = sd.cur_base ^ par;
+        unsigned step = 0;
+        if constexpr (ST == ST_FP16)  // the slot's first tile advances its counter
+            step = sr_step(sd.rng + cur, sd.rng + (cur ^ 1), td.y == 0 && threadIdx.x == 0);
         const S* fin = (const S*)sd.f[cur];
         S* fout = (S*)sd.f[cur ^ 1];
         R* mom = (R*)sd.mom;
@@ -118,8 +122,8 @@ k_b_stream_collide(const SlotDev* __restrict__ slots, const int2* __restrict__ t
             const R omega = (R)sd.omega;
             const CellMoments<Q, R> mo = cell_moments<Q, R>(gv, Fx, Fy, Fz);
             cell_collide<Q, R>(gv, mo, omega, Fx, Fy, Fz);
-#pragma unroll
-            for (int i = 0; i < Q; i++) T::store(fout, (long long)i * nc + cell, gv[i], sd.scale);
+            store_cell<Q, ST, false>(fout, nc, cell, gv, sd.scale,
+                                     ST == ST_FP16 ? sr_seed(step, cell) : 0u);
             if (WRITE_ALL || band) {
                 mom[cell] = mo.drho;
                 mom[nc + cell] = mo.ux;
@@ -353,7 +357,7 @@ struct Arena {
 };
 
 struct Layout {
-    size_t pop[2], mom, F, flags, err, q, phi, tri, csr, epos, erec, total;
+    size_t pop[2], mom, F, flags, err, rng, q, phi, tri, csr, epos, erec, total;
 };
 
 Layout slot_layout(int Q, int dim, size_t elt, size_t relt, long long ncell, long long nfluid,
@@ -372,6 +376,7 @@ Layout slot_layout(int Q, int dim, size_t elt, size_t relt, long long ncell, lon
     L.F = take((size_t)dim * ncell * relt);
     L.flags = take((size_t)((nfluid + 31) / 32));
     L.err = take(sizeof(int));
+    L.rng = take(2 * sizeof(unsigned));
     L.q = take(sizeof(double) * (size_t)N * dim);
     L.phi = take(sizeof(double) * (size_t)N * dim);
     if (dim == 3) {
@@ -789,6 +794,7 @@ iblb_status iblb_batch_admit(iblb_batch b, const iblb_config* cfg, const double*
     d.F = base + L.F;
     d.flags = base + L.flags;
     d.err = (int*)(base + L.err);
+    d.rng = (unsigned*)(base + L.rng);
     d.g = g;
     d.nfluid = nfluid;
     d.fluid_off = dim == 2 ? (long long)cfg->nx : (long long)cfg->nx * cfg->ny;

@@ -90,6 +90,10 @@ struct StreamParams {
     // moving walls (tangential velocities of the lower / upper wall)
     int moving;
     double uw_lo[3], uw_hi[3];
+    // time-step counter for the stochastic rounding of binary16 stores:
+    // read rng_in, one thread writes rng_out = rng_in + 1
+    const unsigned* rng_in;
+    unsigned* rng_out;
     float scale, inv_scale;  // binary16 storage scale (1 for other storage)
     int* err;
 };

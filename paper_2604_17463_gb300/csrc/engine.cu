@@ -65,6 +65,7 @@ struct iblb_sim {
     int* entry_pos = nullptr;    // CSR position of each (face, corner) (3D)
     double* entry_rec = nullptr; // per-(face, corner) geometry records in CSR order (3D)
     double* defo = nullptr;      // deformation output [8]
+    unsigned* rng = nullptr;     // two-entry step counter (binary16 stochastic rounding)
     bool moving = false;         // walls with a tangential velocity
     int* col_cnt = nullptr;      // viscosity ratio: crossings per lattice column
     double* col_z = nullptr;     // [column][COL_MAX] crossing heights
@@ -119,22 +120,26 @@ void enqueue_classify(iblb_sim* h, cudaStream_t s)
 
 cudaError_t launch_sc(iblb_sim* h, cudaStream_t s, bool write_all)
 {
+    // the step counter of the binary16 rounding follows the buffer parity
+    StreamParams sp = h->sp;
+    sp.rng_in = h->rng + h->cur;
+    sp.rng_out = h->rng + (h->cur ^ 1);
     if (h->two_tau || h->moving) {  // the plain kernel carries tau(x) and moving walls
         launch_stream_collide(h->Q, h->storage, write_all, h->f[h->cur], h->f[h->cur ^ 1], h->mom,
-                              h->F, h->flags, h->sp, h->tune, s);
+                              h->F, h->flags, sp, h->tune, s);
         return cudaPeekAtLastError();
     }
     if (h->tune.variant == 2 && pair_kernel_ok(h->storage, h->g)) {
         launch_stream_collide_pairs(h->Q, h->storage, write_all, h->f[h->cur], h->f[h->cur ^ 1],
-                                    h->mom, h->F, h->flags, h->sp, h->tune, s);
+                                    h->mom, h->F, h->flags, sp, h->tune, s);
         return cudaPeekAtLastError();
     }
     if (h->tune.variant == 1 && h->pipe_ok)
         return launch_stream_collide_pipe(h->Q, h->storage, write_all, h->f[h->cur],
-                                          h->f[h->cur ^ 1], h->mom, h->F, h->flags, h->sp,
+                                          h->f[h->cur ^ 1], h->mom, h->F, h->flags, sp,
                                           h->pipe, s);
     launch_stream_collide(h->Q, h->storage, write_all, h->f[h->cur], h->f[h->cur ^ 1], h->mom,
-                          h->F, h->flags, h->sp, h->tune, s);
+                          h->F, h->flags, sp, h->tune, s);
     return cudaPeekAtLastError();
 }
 
@@ -331,6 +336,8 @@ iblb_status iblb_create(const iblb_config* cfg, void* cuda_stream, iblb_handle* 
         return bail(e, "partial");
     if ((e = cudaMalloc(&h->obs, sizeof(double) * 12)) != cudaSuccess) return bail(e, "obs");
     if ((e = cudaMalloc(&h->defo, sizeof(double) * 8)) != cudaSuccess) return bail(e, "obs");
+    if ((e = cudaMalloc(&h->rng, sizeof(unsigned) * 2)) != cudaSuccess) return bail(e, "obs");
+    cudaMemsetAsync(h->rng, 0, sizeof(unsigned) * 2, h->stream);
     if (h->two_tau) {
         const size_t ncol = dim == 2 ? (size_t)c.nx : (size_t)c.nx * c.ny;
         if ((e = cudaMalloc(&h->col_cnt, sizeof(int) * ncol)) != cudaSuccess) return bail(e, "columns");
@@ -390,6 +397,7 @@ void iblb_destroy(iblb_handle h)
     free_dev(h->col_cnt);
     free_dev(h->col_z);
     free_dev(h->defo);
+    free_dev(h->rng);
     if (h->cap) cudaStreamDestroy(h->cap);
     delete h;
 }

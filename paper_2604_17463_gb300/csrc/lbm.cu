@@ -57,6 +57,10 @@ k_stream_collide(const typename StorageT<ST>::S* __restrict__ fin,
     int band = 0;
     if (lane == 0 && (x >> 5) < p.g.nseg_x) band = flags[seg];
     band = __shfl_sync(0xffffffffu, band, 0);
+    unsigned step = 0;
+    if constexpr (ST == ST_FP16)
+        step = sr_step(p.rng_in, p.rng_out,
+                       blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0);
     if (x >= nx) return;
     const long long cell = row * nx + x;
 
@@ -125,13 +129,7 @@ k_stream_collide(const typename StorageT<ST>::S* __restrict__ fin,
         if (!inside_cell(p.col_cnt, p.col_z, col, a)) om = p.omega_out;
     }
     cell_collide<Q, R>(g, mo, (R)om, Fx, Fy, Fz);
-#pragma unroll
-    for (int i = 0; i < Q; i++) {
-        if (CS)
-            T::store_cs(fout, (long long)i * nc + cell, g[i], p.scale);
-        else
-            T::store(fout, (long long)i * nc + cell, g[i], p.scale);
-    }
+    store_cell<Q, ST, CS>(fout, nc, cell, g, p.scale, ST == ST_FP16 ? sr_seed(step, cell) : 0u);
 
     if (WRITE_ALL || band) {
         mom[cell] = mo.drho;
@@ -245,7 +243,7 @@ template <> struct Pair<ST_FP32> {
         return *reinterpret_cast<const float2*>(p + i);
     }
     __device__ __forceinline__ static float load1(const float* p, long long i, float) { return p[i]; }
-    __device__ __forceinline__ static void store2(float* p, long long i, float2 v, float)
+    __device__ __forceinline__ static void store2(float* p, long long i, float2 v, float, unsigned)
     {
         *reinterpret_cast<float2*>(p + i) = v;
     }
@@ -260,9 +258,13 @@ template <> struct Pair<ST_FP16> {
     {
         return __half2float(p[i]) * inv_scale;
     }
-    __device__ __forceinline__ static void store2(__half* p, long long i, float2 v, float scale)
+    // two neighbouring cells of one population, stochastically rounded
+    // (cell x in the low half, x + 1 in the high half of the stored pair)
+    __device__ __forceinline__ static void store2(__half* p, long long i, float2 v, float scale,
+                                                  unsigned rbits)
     {
-        *reinterpret_cast<__half2*>(p + i) = __float22half2_rn(mul2(v, p2(scale)));
+        const float2 w = mul2(v, p2(scale));
+        *reinterpret_cast<unsigned*>(p + i) = cvt_rs_f16x2(w.y, w.x, rbits);
     }
 };
 
@@ -299,6 +301,10 @@ k_stream_collide2(const typename StorageT<ST>::S* __restrict__ fin,
     int fl = 0;
     if ((lane & 15) == 0 && active) fl = flags[seg];
     const int band = __shfl_sync(0xffffffffu, fl, lane & 16);
+    unsigned step = 0;
+    if constexpr (ST == ST_FP16)
+        step = sr_step(p.rng_in, p.rng_out,
+                       blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0);
 
     const int Lw = (D == 2) ? ny : p.g.nz;
     const int a = (D == 2) ? y : z;
@@ -380,8 +386,9 @@ k_stream_collide2(const typename StorageT<ST>::S* __restrict__ fin,
     }
     const CellMoments2 mo = cell_moments2<Q>(g, Fx, Fy, Fz);
     cell_collide2<Q>(g, mo, (float)p.omega, Fx, Fy, Fz);
+    const unsigned seed = ST == ST_FP16 ? sr_seed(step, cell) : 0u;
 #pragma unroll
-    for (int i = 0; i < Q; i++) P::store2(fout, (long long)i * nc + cell, g[i], p.scale);
+    for (int i = 0; i < Q; i++) P::store2(fout, (long long)i * nc + cell, g[i], p.scale, sr_bits(seed, i));
     if (WRITE_ALL || band) {
         *reinterpret_cast<float2*>(mom + cell) = mo.drho;
         *reinterpret_cast<float2*>(mom + nc + cell) = mo.ux;

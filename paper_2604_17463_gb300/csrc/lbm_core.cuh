@@ -44,6 +44,95 @@ template <> struct StorageT<ST_FP16> {
     }
 };
 
+// ---------------------------------------------------------------------------
+// Stochastic rounding of the binary16 population stores.  Round-to-nearest
+// gives every stored population a deterministic error; in a slowly evolving
+// flow the same errors recur step after step and act like a small constant
+// forcing, which the slow hydrodynamic modes integrate over their long
+// relaxation times (the spreading drop then moves measurably slower than in
+// FP64).  Rounding up or down at random, with the probability that makes the
+// expected stored value exact, turns that error into zero-mean noise that is
+// independent between steps.  The conversion is the sm_100-family
+// cvt.rs.f16x2.f32 instruction; its random bits come from a counter-based
+// hash of (time step, cell, population pair), so runs are deterministic.
+//
+// mix32 is the 32-bit integer hash "lowbias32" published by C. Wellons
+// (xor-shift / multiply rounds with constants 0x7feb352d, 0x846ca68b).
+__device__ __forceinline__ unsigned mix32(unsigned x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352dU;
+    x ^= x >> 15;
+    x *= 0x846ca68bU;
+    x ^= x >> 16;
+    return x;
+}
+
+// Per-cell seed for time step `step`.
+__device__ __forceinline__ unsigned sr_seed(unsigned step, long long cell)
+{
+    return mix32((unsigned)cell ^ mix32(step + 0x9e3779b9U));
+}
+
+// Random bits for population pair k of a cell (uniform whenever the seed is).
+__device__ __forceinline__ unsigned sr_bits(unsigned seed, int k)
+{
+    return (seed ^ ((unsigned)k * 0x9e3779b9U)) * 0x85ebca6bU;
+}
+
+// hi -> bits 31:16, lo -> bits 15:0, stochastically rounded.
+__device__ __forceinline__ unsigned cvt_rs_f16x2(float hi, float lo, unsigned rbits)
+{
+    unsigned d;
+    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
+    return d;
+}
+
+// Store all Q populations of one cell (deviation form): binary16 with
+// stochastic rounding, population pairs (2k, 2k+1) sharing one conversion;
+// FP32 / FP64 as they are.  CS: streaming (evict-first) stores.
+template <int Q, int ST, bool CS>
+__device__ __forceinline__ void store_cell(typename StorageT<ST>::S* __restrict__ fout,
+                                           long long nc, long long cell,
+                                           const typename StorageT<ST>::R* g, float scale,
+                                           unsigned seed)
+{
+    using T = StorageT<ST>;
+    if constexpr (ST == ST_FP16) {
+        unsigned short* o = reinterpret_cast<unsigned short*>(fout);
+#pragma unroll
+        for (int i = 0; i < Q; i += 2) {
+            const float lo = (i + 1 < Q) ? g[i + 1] * scale : 0.0f;
+            const unsigned h = cvt_rs_f16x2(g[i] * scale, lo, sr_bits(seed, i >> 1));
+            if (CS) {
+                __stcs(o + (long long)i * nc + cell, (unsigned short)(h >> 16));
+                if (i + 1 < Q) __stcs(o + (long long)(i + 1) * nc + cell, (unsigned short)(h & 0xffffu));
+            } else {
+                o[(long long)i * nc + cell] = (unsigned short)(h >> 16);
+                if (i + 1 < Q) o[(long long)(i + 1) * nc + cell] = (unsigned short)(h & 0xffffu);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            if (CS)
+                T::store_cs(fout, (long long)i * nc + cell, g[i], scale);
+            else
+                T::store(fout, (long long)i * nc + cell, g[i], scale);
+        }
+    }
+}
+
+// Time-step number for the rounding hash: read from the current slot of a
+// two-entry device counter; one thread of the launch writes the next value
+// into the other slot (read and written entries never coincide in a launch).
+__device__ __forceinline__ unsigned sr_step(const unsigned* in, unsigned* out, bool writer)
+{
+    const unsigned s = in ? __ldg(in) : 0u;
+    if (writer && out) *out = s + 1u;
+    return s;
+}
+
 // Relaxation rate and body force in the compute precision.
 template <typename R>
 __device__ __forceinline__ R param_omega(const StreamParams& p);

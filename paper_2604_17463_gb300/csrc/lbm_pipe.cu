@@ -206,6 +206,9 @@ k_sc_pipe(const typename StorageT<ST>::S* __restrict__ fin,
     const long long nc = p.g.ncell;
     const int walls = p.g.walls;
     const bool rows_mode = ps.mode == PIPE_ROWS;
+    unsigned step = 0;
+    if constexpr (ST == ST_FP16)
+        step = sr_step(p.rng_in, p.rng_out, blockIdx.x == 0 && threadIdx.x == 0);
 
     if (threadIdx.x == 0) {
         abort_flag = 0;
@@ -346,8 +349,8 @@ k_sc_pipe(const typename StorageT<ST>::S* __restrict__ fin,
             }
             const CellMoments<Q, R> mo = cell_moments<Q, R>(g, Fx, Fy, Fz);
             cell_collide<Q, R>(g, mo, omega, Fx, Fy, Fz);
-#pragma unroll
-            for (int i = 0; i < Q; i++) T::store(fout, (long long)i * nc + cell, g[i], p.scale);
+            store_cell<Q, ST, false>(fout, nc, cell, g, p.scale,
+                                     ST == ST_FP16 ? sr_seed(step, cell) : 0u);
             if (WRITE_ALL || band) {
                 mom[cell] = mo.drho;
                 mom[nc + cell] = mo.ux;

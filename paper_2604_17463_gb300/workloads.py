@@ -344,3 +344,132 @@ def shear_drop(R0: float = 19.0, Re: float = 0.01, Ca: float = 0.05, tau: float 
     wl = Workload(f"shear_drop_R{R0:g}_Ca{Ca:g}_Re{Re:g}", lattice, nx, ny, nz, tau, sigma,
                   0.05 * R0, 90.0, 9, 3, steps, nodes, faces, walls=True, wetting=False)
     return ShearDrop(wl, gamma_dot, tau_out, Re, Ca, R0)
+
+
+# ------------------------------------------------- paper-scale 3D spreading
+def _icosahedron():
+    g = (1.0 + math.sqrt(5.0)) / 2.0
+    v = []
+    for s1 in (-1.0, 1.0):
+        for s2 in (-1.0, 1.0):
+            v += [(0.0, s1, s2 * g), (s1, s2 * g, 0.0), (s2 * g, 0.0, s1)]
+    verts = np.array(v)
+    verts /= np.linalg.norm(verts, axis=1, keepdims=True)
+    d = np.linalg.norm(verts[:, None, :] - verts[None, :, :], axis=2)
+    edge = np.min(d[d > 1e-9])
+    adj = np.abs(d - edge) < 1e-6
+    faces = []
+    for a in range(12):
+        for b in range(a + 1, 12):
+            if not adj[a, b]:
+                continue
+            for c in range(b + 1, 12):
+                if adj[a, c] and adj[b, c]:
+                    n = np.cross(verts[b] - verts[a], verts[c] - verts[a])
+                    faces.append((a, c, b) if np.dot(n, verts[a] + verts[b] + verts[c]) < 0
+                                 else (a, b, c))
+    return verts, faces
+
+
+def geodesic_sphere(freq: int, radius: float, centre: Tuple[float, float, float]):
+    """Class-I geodesic sphere: every icosahedron face cut into freq^2
+    triangles on a barycentric grid, points projected to the sphere.  Shared
+    edge and corner points are merged exactly (keyed by their integer
+    barycentric combination of icosahedron vertices).  Faces outward.
+    Returns (nodes [10 freq^2 + 2, 3], faces [20 freq^2, 3] int32)."""
+    verts, ico = _icosahedron()
+    index = {}
+    pts = []
+
+    def node(combo):
+        key = tuple(sorted((v, w) for v, w in combo if w > 0))
+        k = index.get(key)
+        if k is None:
+            p = sum(w * verts[v] for v, w in key) / freq
+            k = index[key] = len(pts)
+            pts.append(p / np.linalg.norm(p))
+        return k
+
+    faces = []
+    for a, b, c in ico:
+        grid = {}
+        for i in range(freq + 1):
+            for j in range(freq + 1 - i):
+                grid[(i, j)] = node(((a, freq - i - j), (b, i), (c, j)))
+        for i in range(freq):
+            for j in range(freq - i):
+                faces.append((grid[(i, j)], grid[(i + 1, j)], grid[(i, j + 1)]))
+                if i + j < freq - 1:
+                    faces.append((grid[(i + 1, j)], grid[(i + 1, j + 1)], grid[(i, j + 1)]))
+    nodes = np.asarray(pts) * radius + np.asarray(centre)[None, :]
+    return nodes, np.asarray(faces, dtype=np.int32)
+
+
+def truncated_sphere(freq: int, radius: float, theta0_deg: float, base_z: float,
+                     centre_xy: Tuple[float, float]):
+    """Closed mesh of a spherical cap of radius `radius` meeting the plane
+    z = base_z at the angle theta0 (a drop resting on its film), from the
+    geodesic sphere: a point at polar angle beta from the top pole goes to
+    the cap at polar angle beta theta0 / (pi/2) for beta <= pi/2, and to the
+    flat base disc at radius R sin(theta0) (pi - beta) / (pi/2) below the
+    equator.  Topology and outward orientation are those of the sphere."""
+    unit, faces = geodesic_sphere(freq, 1.0, (0.0, 0.0, 0.0))
+    th0 = math.radians(theta0_deg)
+    beta = np.arccos(np.clip(unit[:, 2], -1.0, 1.0))
+    phi = np.arctan2(unit[:, 1], unit[:, 0])
+    zc = base_z - radius * math.cos(th0)          # sphere centre height
+    out = np.zeros_like(unit)
+    up = beta <= 0.5 * math.pi
+    b = beta[up] * th0 / (0.5 * math.pi)
+    out[up, 0] = radius * np.sin(b) * np.cos(phi[up])
+    out[up, 1] = radius * np.sin(b) * np.sin(phi[up])
+    out[up, 2] = zc + radius * np.cos(b)
+    r = radius * math.sin(th0) * (math.pi - beta[~up]) / (0.5 * math.pi)
+    out[~up, 0] = r * np.cos(phi[~up])
+    out[~up, 1] = r * np.sin(phi[~up])
+    out[~up, 2] = base_z
+    out[:, 0] += centre_xy[0]
+    out[:, 1] += centre_xy[1]
+    return out, faces
+
+
+@dataclasses.dataclass
+class Spread3D:
+    """A paper-scale 3D spreading run (Sec. 3 and 4) with its capillary time
+    t_mu = mu_in R0 / sigma and the Reynolds number rho sigma R0 / mu_in^2."""
+    work: Workload
+    R0: float
+    t_mu: float
+    Re: float
+    t_mu_count: float
+
+
+def spread3d_cap(tau: float, R0: float = 50.0, sigma: float = 1e-3, freq: int = 77,
+                 t_mu_count: float = 50.0) -> Spread3D:
+    """Sec. 3: 250 x 250 x 150 lattice, a drop resting as a hemisphere of
+    radius R0 (contact angle 90 deg) on its film spreads towards
+    theta_eq = 60 deg; xi / R0 = 0.05; about 120 000 triangles
+    (20 freq^2 = 118 580 at freq 77); run t_mu_count capillary times."""
+    xi = 0.05 * R0
+    nodes, faces = truncated_sphere(freq, R0, 90.0, WALL_PLANE + xi, (125.0 + 0.17, 125.0 - 0.11))
+    mu = (tau - 0.5) / 3.0
+    t_mu = mu * R0 / sigma
+    steps = int(round(t_mu_count * t_mu))
+    wl = Workload(f"spread3d_cap_250x250x150_tau{tau:g}", 19, 250, 250, 150, tau, sigma, xi,
+                  60.0, 9, 3, steps, nodes, faces)
+    return Spread3D(wl, R0, t_mu, sigma * R0 / mu ** 2, t_mu_count)
+
+
+def spread3d_sphere(R0: float = 50.0, sigma: float = 1e-3, tau: float = 0.56, freq: int = 77,
+                    t_mu_count: float = 50.0) -> Spread3D:
+    """Sec. 4: 300 x 300 x 250 lattice, a sphere of radius R0 whose lowest
+    node sits at the film distance xi from the wall, theta_eq = 45 deg,
+    tau = 0.56 (mu_in = 0.02), xi / R0 = 0.05, about 120 000 triangles."""
+    xi = 0.05 * R0
+    nodes, faces = geodesic_sphere(freq, R0, (150.0 + 0.17, 150.0 - 0.11, WALL_PLANE + xi + R0))
+    mu = (tau - 0.5) / 3.0
+    t_mu = mu * R0 / sigma
+    steps = int(round(t_mu_count * t_mu))
+    wl = Workload("spread3d_sphere_300x300x250", 19, 300, 300, 250, tau, sigma, xi, 45.0, 9, 3,
+                  steps, nodes, faces)
+    return Spread3D(wl, R0, t_mu, sigma * R0 / mu ** 2, t_mu_count)
