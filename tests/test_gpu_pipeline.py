@@ -58,8 +58,12 @@ def test_kernel_variants_match_plain_and_oracle(Q, dims, walls, storage):
         out[variant] = g.populations()
         g.close()
     m = fluid_mask(shape, 2 if Q == 9 else 3, walls)
-    # same arithmetic up to FMA placement: agreement to the storage format's last bits
-    tol = {iblb.FP64: 1e-15, iblb.FP32_DEV: 2e-7, iblb.FP16_DEV: 2e-6}[storage]
+    # same arithmetic up to FMA placement: agreement to the storage format's
+    # last bits; binary16 stores round stochastically with random bits that
+    # differ between kernels, so up to one unit in the last place there
+    # (populations here have |g| < 1/32, i.e. below 2048 once scaled by 2^16,
+    # where the binary16 spacing is at most 1: one ulp <= 2^-16 unscaled)
+    tol = {iblb.FP64: 1e-15, iblb.FP32_DEV: 2e-7, iblb.FP16_DEV: 2.0 ** -16 * 1.01}[storage]
     for variant in (1, 2):
         assert np.max(np.abs(out[variant][:, m] - out[0][:, m])) < tol, variant
     if storage == iblb.FP64:
