@@ -13,6 +13,14 @@ end-to-end figure through the C-ABI with host buffers, and the FP64 CPU oracle
 timed on a bounded sample of the same workload.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Other modes (--mode), each printing one JSON line of its own:
+  batch     256 uneven 2D drops: sequential FP32 vs batched FP32 / binary16
+  serve     Poisson stream of 2D / 3D requests through the serving loop
+  spread2d  2048x512 spreading sweep in FP64 / FP32 / binary16 storage, and
+            the 4x-downscaled copy against the FP64 oracle
+  spread3d  paper-scale 3D spreading (250x250x150 tau sweep, 300x300x250)
+  shear     drop in shear flow at Re = 0.01, Ca = 0.05, R0 = 19 against Eq. 13
 """
 from __future__ import annotations
 
