@@ -444,14 +444,17 @@ class Spread3D:
     t_mu_count: float
 
 
-def spread3d_cap(tau: float, R0: float = 50.0, sigma: float = 1e-3, freq: int = 77,
-                 t_mu_count: float = 50.0) -> Spread3D:
-    """Sec. 3: 250 x 250 x 150 lattice, a drop resting as a hemisphere of
-    radius R0 (contact angle 90 deg) on its film spreads towards
-    theta_eq = 60 deg; xi / R0 = 0.05; about 120 000 triangles
-    (20 freq^2 = 118 580 at freq 77); run t_mu_count capillary times."""
+def spread3d_cap(tau: float, R0: float = 50.0 / 2.0 ** (1.0 / 3.0), sigma: float = 1e-3,
+                 freq: int = 77, t_mu_count: float = 50.0) -> Spread3D:
+    """Sec. 3: 250 x 250 x 150 lattice, a drop resting as a hemisphere
+    (contact angle 90 deg) on its film spreads towards theta_eq = 60 deg.
+    R0 is the radius of the sphere of the same volume (the paper's reference
+    radius), so the hemisphere has radius 2^(1/3) R0 (50 lu by default);
+    xi / R0 = 0.05; about 120 000 triangles (20 freq^2 = 118 580 at freq 77);
+    run t_mu_count capillary times t_mu = mu R0 / sigma."""
     xi = 0.05 * R0
-    nodes, faces = truncated_sphere(freq, R0, 90.0, WALL_PLANE + xi, (125.0 + 0.17, 125.0 - 0.11))
+    Rh = 2.0 ** (1.0 / 3.0) * R0
+    nodes, faces = truncated_sphere(freq, Rh, 90.0, WALL_PLANE + xi, (125.0 + 0.17, 125.0 - 0.11))
     mu = (tau - 0.5) / 3.0
     t_mu = mu * R0 / sigma
     steps = int(round(t_mu_count * t_mu))
@@ -460,11 +463,12 @@ def spread3d_cap(tau: float, R0: float = 50.0, sigma: float = 1e-3, freq: int = 
     return Spread3D(wl, R0, t_mu, sigma * R0 / mu ** 2, t_mu_count)
 
 
-def spread3d_sphere(R0: float = 50.0, sigma: float = 1e-3, tau: float = 0.56, freq: int = 77,
-                    t_mu_count: float = 50.0) -> Spread3D:
-    """Sec. 4: 300 x 300 x 250 lattice, a sphere of radius R0 whose lowest
-    node sits at the film distance xi from the wall, theta_eq = 45 deg,
-    tau = 0.56 (mu_in = 0.02), xi / R0 = 0.05, about 120 000 triangles."""
+def spread3d_sphere(R0: float = 50.0 / 2.0 ** (1.0 / 3.0), sigma: float = 1e-3, tau: float = 0.56,
+                    freq: int = 77, t_mu_count: float = 50.0) -> Spread3D:
+    """Sec. 4: 300 x 300 x 250 lattice, a sphere of radius R0 (the same
+    reference radius as the Sec. 3 runs) whose lowest node sits at the film
+    distance xi from the wall, theta_eq = 45 deg, tau = 0.56 (mu_in = 0.02),
+    xi / R0 = 0.05, about 120 000 triangles."""
     xi = 0.05 * R0
     nodes, faces = geodesic_sphere(freq, R0, (150.0 + 0.17, 150.0 - 0.11, WALL_PLANE + xi + R0))
     mu = (tau - 0.5) / 3.0

@@ -48,10 +48,13 @@ def test_paper_scale_mesh_size():
     assert len(s.work.faces) == 118580          # about the paper's 120 000 triangles
     vol = mesh_checks(s.work.nodes, s.work.faces)
     R0 = s.R0
-    assert abs(vol / (2.0 / 3.0 * math.pi * R0 ** 3) - 1.0) < 1e-3
+    # R0 is the radius of the sphere of the same volume as the hemisphere
+    assert abs(vol / (4.0 / 3.0 * math.pi * R0 ** 3) - 1.0) < 1e-3
+    assert s.work.xi == pytest.approx(0.05 * R0)
     z = s.work.nodes[:, 2]
+    Rh = 2.0 ** (1.0 / 3.0) * R0
     assert abs(z.min() - (W.WALL_PLANE + s.work.xi)) < 1e-12
-    assert abs(z.max() - z.min() - R0) < 1e-3 * R0   # no mesh vertex sits exactly on the pole
+    assert abs(z.max() - z.min() - Rh) < 1e-3 * Rh   # no mesh vertex sits exactly on the pole
     assert s.t_mu == pytest.approx((1.1 - 0.5) / 3.0 * R0 / s.work.sigma)
 
 
