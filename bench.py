@@ -42,7 +42,10 @@ sys.path.insert(0, ROOT)
 WORKLOAD_NAME = "d3q19_256x256x128_icosphere_R40_fp32dev"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "stream_collide_d3q19_256x256x128_fp32.txt")
+TRAFFIC_FILES = {
+    "fp32": os.path.join(ROOT, "profiles", "stream_collide_d3q19_256x256x128_fp32.txt"),
+    "fp16": os.path.join(ROOT, "profiles", "stream_collide_d3q19_256x256x128_fp16.txt"),
+}
 CSRC = os.path.join(ROOT, "paper_2604_17463_gb300", "csrc")
 SC_SOURCES = [os.path.join(CSRC, n) for n in ("lbm.cu", "lbm_pipe.cu", "lbm_core.cuh", "common.cuh")]
 
@@ -63,12 +66,13 @@ def source_digest(paths):
     return h.hexdigest()[:16]
 
 
-def ncu_traffic():
+def ncu_traffic(storage):
     """Per-launch DRAM bytes of the stream-collide kernel from the committed ncu
-    summary, valid only while the kernel source is unchanged since capture."""
+    summary of the same storage form, valid only while the kernel source is
+    unchanged since capture (None otherwise)."""
     try:
         vals = {}
-        with open(TRAFFIC_FILE) as fh:
+        with open(TRAFFIC_FILES[storage]) as fh:
             for line in fh:
                 if ":" in line:
                     k, v = line.split(":", 1)
@@ -331,7 +335,7 @@ def run_ours(args, wl):
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "kernel": "stream_collide", "achieved": achieved,
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": ncu_traffic(),
+                     "frac": achieved / peak, "traffic": ncu_traffic(args.storage),
                      "bytes_per_launch": bytes_per_launch, "launch_ms": sc_ms,
                      "kernel_share": kernel_share},
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
