@@ -66,10 +66,11 @@ def source_digest(paths):
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(storage):
+def ncu_traffic(storage, tuning=None):
     """Per-launch DRAM bytes of the stream-collide kernel from the committed ncu
-    summary of the same storage form, valid only while the kernel source is
-    unchanged since capture (None otherwise)."""
+    summary of the same storage form and launch shape ("variant,block_x,
+    rows,ctas,warps"), valid only while the kernel source is unchanged since
+    capture (None otherwise)."""
     try:
         vals = {}
         with open(TRAFFIC_FILES[storage]) as fh:
@@ -78,6 +79,8 @@ def ncu_traffic(storage):
                     k, v = line.split(":", 1)
                     vals[k.strip()] = v.strip()
         if vals.get("stream-collide sources sha256 prefix") != source_digest(SC_SOURCES):
+            return None
+        if tuning is not None and vals.get("launch shape") not in (None, tuning):
             return None
         return float(vals["dram bytes per launch"])
     except Exception:
@@ -335,7 +338,9 @@ def run_ours(args, wl):
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "kernel": "stream_collide", "achieved": achieved,
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": ncu_traffic(args.storage),
+                     "frac": achieved / peak, "traffic": ncu_traffic(args.storage, ",".join(
+                         str(tuned[k]) for k in ("variant", "block_x", "rows_per_tile",
+                                                 "ctas_per_sm", "consumer_warps"))),
                      "bytes_per_launch": bytes_per_launch, "launch_ms": sc_ms,
                      "kernel_share": kernel_share},
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
