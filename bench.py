@@ -68,9 +68,9 @@ def source_digest(paths):
 
 def ncu_traffic(storage, tuning=None):
     """Per-launch DRAM bytes of the stream-collide kernel from the committed ncu
-    summary of the same storage form and launch shape ("variant,block_x,
-    rows,ctas,warps"), valid only while the kernel source is unchanged since
-    capture (None otherwise)."""
+    summary of the same storage form and kernel variant (the first field of
+    the launch shape "variant,block_x,rows,ctas,warps"), valid only while the
+    kernel source is unchanged since capture (None otherwise)."""
     try:
         vals = {}
         with open(TRAFFIC_FILES[storage]) as fh:
@@ -80,7 +80,9 @@ def ncu_traffic(storage, tuning=None):
                     vals[k.strip()] = v.strip()
         if vals.get("stream-collide sources sha256 prefix") != source_digest(SC_SOURCES):
             return None
-        if tuning is not None and vals.get("launch shape") not in (None, tuning):
+        # the same kernel (variant); the block size does not change its traffic
+        shape = vals.get("launch shape")
+        if tuning is not None and shape is not None and shape.split(",")[0] != tuning.split(",")[0]:
             return None
         return float(vals["dram bytes per launch"])
     except Exception:
