@@ -57,7 +57,8 @@ typedef enum { IBLB_D2Q9 = 9, IBLB_D3Q19 = 19 } iblb_lattice;
 
 /* Population storage.  All forms hold deviations f_i - w_i from the rest
  * state; arithmetic is FP64 for IBLB_FP64 and FP32 otherwise.  IBLB_FP16_DEV
- * stores (f_i - w_i) * 2^fp16_scale_exp in binary16. */
+ * stores (f_i - w_i) * 2^fp16_scale_exp in binary16, rounded stochastically,
+ * and is limited to lattices of fewer than 2^32 cells (IBLB_EINVAL above). */
 typedef enum { IBLB_FP64 = 0, IBLB_FP32_DEV = 1, IBLB_FP16_DEV = 2 } iblb_storage;
 
 typedef struct {

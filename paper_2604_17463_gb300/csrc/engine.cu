@@ -256,6 +256,8 @@ iblb_status iblb_create(const iblb_config* cfg, void* cuda_stream, iblb_handle* 
     if (dim == 3 && (c.ny > 65535 || nz > 65535)) return IBLB_EINVAL;
     if (dim == 2 && c.ny > 65535) return IBLB_EINVAL;
     if (c.fp16_scale_exp < 0 || c.fp16_scale_exp > 24) return IBLB_EINVAL;
+    // binary16 stream-collide indexes cells with 32 bits
+    if (c.storage == IBLB_FP16_DEV && (double)c.nx * c.ny * nz >= 4294967296.0) return IBLB_EINVAL;
     if (c.tau_out != 0.0 && (!(c.tau_out > 0.5) || !std::isfinite(c.tau_out))) return IBLB_EINVAL;
     {
         const int wax = c.lattice == 9 ? 1 : 2;

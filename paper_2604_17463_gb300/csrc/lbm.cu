@@ -93,6 +93,27 @@ k_stream_collide(const typename StorageT<ST>::S* __restrict__ fin,
         const int cw = (D == 2) ? cy : cz;  // velocity along the wall axis
         const int sa = cw == 0 ? a : (cw > 0 ? am : ap);
         const bool solid = cw == 0 ? false : (cw > 0 ? solid_m : solid_p);
+        if constexpr (ST == ST_FP16) {
+            // binary16: 32-bit cell index on a per-plane base pointer (fewer
+            // integer instructions; the engine keeps binary16 lattices below
+            // 2^32 cells)
+            unsigned src32;
+            if (D == 2) {
+                src32 = (unsigned)sa * (unsigned)nx + (unsigned)sx;
+            } else {
+                const int sy = cy == 0 ? y : (cy > 0 ? ym : yp);
+                src32 = ((unsigned)sa * (unsigned)ny + (unsigned)sy) * (unsigned)nx + (unsigned)sx;
+            }
+            if (solid)
+                g[i] = T::load(fin + (long long)L::opp(i) * nc, (unsigned)cell, p.inv_scale);
+            else
+                g[i] = T::load(fin + (long long)i * nc, src32, p.inv_scale);
+            if (EXT && p.moving && solid) {
+                const double* uw = cw > 0 ? p.uw_lo : p.uw_hi;
+                g[i] += (R)(6.0 * L::w(i) * (cx * uw[0] + cy * uw[1] + cz * uw[2]));
+            }
+            continue;
+        }
         long long src;
         if (D == 2) {
             src = (long long)sa * nx + sx;
