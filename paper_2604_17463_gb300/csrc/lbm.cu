@@ -85,6 +85,10 @@ k_stream_collide(const typename StorageT<ST>::S* __restrict__ fin,
         yp = (y == ny - 1) ? 0 : y + 1;
     }
 
+    // binary16 populations stay in their stored scale (x 2^k) through the
+    // collision: the moments undo the scale, the new terms take it on, and
+    // no per-population rescaling is needed on load or store
+    const float lsc = (ST == ST_FP16) ? 1.0f : p.inv_scale;
     R g[Q];
 #pragma unroll
     for (int i = 0; i < Q; i++) {
@@ -105,12 +109,12 @@ k_stream_collide(const typename StorageT<ST>::S* __restrict__ fin,
                 src32 = ((unsigned)sa * (unsigned)ny + (unsigned)sy) * (unsigned)nx + (unsigned)sx;
             }
             if (solid)
-                g[i] = T::load(fin + (long long)L::opp(i) * nc, (unsigned)cell, p.inv_scale);
+                g[i] = T::load(fin + (long long)L::opp(i) * nc, (unsigned)cell, lsc);
             else
-                g[i] = T::load(fin + (long long)i * nc, src32, p.inv_scale);
+                g[i] = T::load(fin + (long long)i * nc, src32, lsc);
             if (EXT && p.moving && solid) {
                 const double* uw = cw > 0 ? p.uw_lo : p.uw_hi;
-                g[i] += (R)(6.0 * L::w(i) * (cx * uw[0] + cy * uw[1] + cz * uw[2]));
+                g[i] += (R)(6.0 * L::w(i) * (cx * uw[0] + cy * uw[1] + cz * uw[2])) * p.scale;
             }
             continue;
         }
@@ -143,14 +147,23 @@ k_stream_collide(const typename StorageT<ST>::S* __restrict__ fin,
             F[2 * nc + cell] = 0;
         }
     }
-    const CellMoments<Q, R> mo = cell_moments<Q, R>(g, Fx, Fy, Fz);
+    CellMoments<Q, R> mo;
+    if constexpr (ST == ST_FP16)
+        mo = cell_moments<Q, R>(g, Fx, Fy, Fz, (R)p.inv_scale);
+    else
+        mo = cell_moments<Q, R>(g, Fx, Fy, Fz);
     double om = p.omega;
     if (EXT && p.two_tau) {  // viscosity ratio: outside the interface relax with omega_out
         const int col = (D == 2) ? x : x + nx * y;
         if (!inside_cell(p.col_cnt, p.col_z, col, a)) om = p.omega_out;
     }
-    cell_collide<Q, R>(g, mo, (R)om, Fx, Fy, Fz);
-    store_cell<Q, ST, CS>(fout, nc, cell, g, p.scale, ST == ST_FP16 ? sr_seed(step, cell) : 0u);
+    if constexpr (ST == ST_FP16) {
+        cell_collide<Q, R>(g, mo, (R)om, Fx, Fy, Fz, (R)p.scale);
+        store_cell<Q, ST, CS>(fout, nc, cell, g, 1.0f, sr_seed(step, cell));
+    } else {
+        cell_collide<Q, R>(g, mo, (R)om, Fx, Fy, Fz);
+        store_cell<Q, ST, CS>(fout, nc, cell, g, p.scale, 0u);
+    }
 
     if (WRITE_ALL || band) {
         mom[cell] = mo.drho;

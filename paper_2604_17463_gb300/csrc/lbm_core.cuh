@@ -208,7 +208,8 @@ struct CellMoments {
 };
 
 template <int Q, typename R>
-__device__ __forceinline__ CellMoments<Q, R> cell_moments(const R* g, R Fx, R Fy, R Fz)
+__device__ __forceinline__ CellMoments<Q, R> cell_moments(const R* g, R Fx, R Fy, R Fz,
+                                                          R ginv = R(1))
 {
     using L = Stencil<Q>;
     constexpr int D = L::D;
@@ -225,6 +226,11 @@ __device__ __forceinline__ CellMoments<Q, R> cell_moments(const R* g, R Fx, R Fy
             if (L::cz(i) < 0) jz -= g[i];
         }
     }
+    // g may be held scaled by a power of two (binary16 storage): ginv undoes it
+    drho *= ginv;
+    jx *= ginv;
+    jy *= ginv;
+    jz *= ginv;
     CellMoments<Q, R> m;
     m.drho = drho;
     m.rho = R(1) + drho;
@@ -246,7 +252,7 @@ __device__ __forceinline__ CellMoments<Q, R> cell_moments(const R* g, R Fx, R Fy
 // coef_b and coef_a (exact mass and momentum identities in FP32).
 template <int Q, typename R>
 __device__ __forceinline__ void cell_collide(R* g, const CellMoments<Q, R>& m, R omega, R Fx, R Fy,
-                                             R Fz)
+                                             R Fz, R gscale = R(1))
 {
     using L = Stencil<Q>;
     constexpr int D = L::D;
@@ -258,13 +264,14 @@ __device__ __forceinline__ void cell_collide(R* g, const CellMoments<Q, R>& m, R
     const R k2 = omega * R(4.5) * m.rho;        // coefficient of (c.u)^2
     const R k1 = omega * m.rho;                 // coefficient of (c.u), over 3
     const R p9 = R(9) * pref;
-    g[0] = om1 * g[0] + coef_b<Q, R>(0) * sym0;
+    // g held scaled by gscale (a power of two): the new terms take the same scale
+    g[0] = om1 * g[0] + (coef_b<Q, R>(0) * gscale) * sym0;
 #pragma unroll
     for (int i = 1; i < Q; i++) {
         if (L::opp(i) < i) continue;  // each pair once
         const int o = L::opp(i);
-        const R w = coef_b<Q, R>(i);
-        const R w3 = coef_a<Q, R>(i);
+        const R w = coef_b<Q, R>(i) * gscale;
+        const R w3 = coef_a<Q, R>(i) * gscale;
         const R cu = (R)L::cx(i) * m.ux + (R)L::cy(i) * m.uy + (D == 3 ? (R)L::cz(i) * m.uz : R(0));
         const R cF = (R)L::cx(i) * Fx + (R)L::cy(i) * Fy + (D == 3 ? (R)L::cz(i) * Fz : R(0));
         const R sym = w * (sym0 + cu * (k2 * cu + p9 * cF));
