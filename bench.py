@@ -42,6 +42,7 @@ sys.path.insert(0, ROOT)
 WORKLOAD_NAME = "d3q19_256x256x128_icosphere_R40_fp32dev"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e data-sheet figure, quoted beside the measured peak
 TRAFFIC_FILES = {
     "fp32": os.path.join(ROOT, "profiles", "stream_collide_d3q19_256x256x128_fp32.txt"),
     "fp16": os.path.join(ROOT, "profiles", "stream_collide_d3q19_256x256x128_fp16.txt"),
@@ -322,9 +323,14 @@ def run_ours(args, wl):
     if world == 1 and not args.no_cpu_baseline:
         cpu_steps = 3
         cv, cdt = cpu_baseline_oracle(wl, cpu_steps)
+        from paper_2604_17463_gb300 import workloads as W
+        c1, _ = cpu_baseline_oracle(W.config1(), 200)
+        c2d, _ = cpu_baseline_oracle(W.config2(downscale=4), 50)
         cpu = {"value": cv, "unit": "MLUPS", "cores": 1, "kind": "oracle",
                "sample": f"{cpu_steps} full time steps of the same workload in the FP64 oracle "
-                         f"(single thread, {cdt:.1f} s)"}
+                         f"(single thread, {cdt:.1f} s)",
+               "other_workloads_mlups": {"c1_d2q9_128x64 (200 steps)": c1,
+                                         "c2_d2q9_512x128 downscaled (50 steps)": c2d}}
     clocks = clk.summary()
     line = {
         "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
@@ -344,6 +350,8 @@ def run_ours(args, wl):
                          str(tuned[k]) for k in ("variant", "block_x", "rows_per_tile",
                                                  "ctas_per_sm", "consumer_warps"))),
                      "bytes_per_launch": bytes_per_launch, "launch_ms": sc_ms,
+                     "stream_collide_mlups": cells / (sc_ms * 1e-3) / 1e6,
+                     "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                      "kernel_share": kernel_share},
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
