@@ -143,9 +143,12 @@ iblb_status iblb_observables(iblb_handle h, iblb_obs* out);
 
 /* ---- single-stage entry points (each runs one kernel of the step) ---- */
 
-/* Set every population to the equilibrium (Eq. 3) of the given fields:
- * rho [cells] (NULL: 1 everywhere), u [dim][cells], host buffers, layout
- * [component][z][y][x].  E.g. a fully developed shear flow.  Synchronises. */
+/* Set every population to the equilibrium (Sec. 2, Eq. 3) of the given
+ * fields: rho [cells] (NULL: 1 everywhere), u [dim][cells]; host buffers
+ * owned by the caller and only read, layout [component][z][y][x], FP64.
+ * E.g. a fully developed shear flow (Sec. 4).  Solid layers are set too (they
+ * are never read).  IBLB_EINVAL on a NULL handle or u; IBLB_ECUDA if a copy
+ * or the kernel fails.  Synchronises. */
 iblb_status iblb_set_equilibrium(iblb_handle h, const double* rho, const double* u);
 
 /* Deformation of the current interface in the shear plane (x and the wall
@@ -157,7 +160,11 @@ iblb_status iblb_set_equilibrium(iblb_handle h, const double* rho, const double*
 iblb_status iblb_deformation(iblb_handle h, double* out);
 
 /* Inside / outside classification of every cell by the current interface
- * (1 = inside), mask [cells].  Synchronises. */
+ * (Sec. 2: the ray tracing behind tau(x, t)): mask [cells], caller-owned host
+ * buffer, layout [z][y][x], 1 = inside.  Rays run along the wall axis; a
+ * cell is inside when an odd number of crossings lies below its centre.
+ * Works whether or not tau_out is set.  IBLB_ECLASSIFY when a column is
+ * crossed more than 16 times; IBLB_EINVAL on NULL arguments.  Synchronises. */
 iblb_status iblb_inside_mask(iblb_handle h, unsigned char* mask);
 
 /* Nodal forces phi [N][dim], normals [N][dim] and 1-ring measures chi [N]
