@@ -1,0 +1,44 @@
+"""Parity with the FP64 oracle at the full sizes of the benchmark workloads,
+in the launch configuration the benchmark times (autotuned stream-collide):
+the 3D drop on 256 x 256 x 128 and the 2048 x 512 spreading drop.  The
+oracle runs whole lattices, so a few steps of each are compared field by
+field (every fluid cell) and node by node."""
+import numpy as np
+import pytest
+
+from paper_2604_17463_gb300 import iblb
+from paper_2604_17463_gb300 import workloads as W
+from helpers import fluid_mask, oracle_from_workload, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def compare(wl, storage, steps, tol_u, tol_drho, tol_q):
+    o = oracle_from_workload(wl)
+    g = iblb.Simulation.from_workload(wl, storage=storage)
+    tuned = g.autotune(trials=3)
+    assert o.step(steps) == 0
+    g.step(steps)
+    ro, uo, qo = o.fields()
+    rg, ug, qg = g.fields()
+    m = fluid_mask(o.shape, wl.dim)
+    e_u = rel_l2(ug[:, m], uo[: wl.dim, m])
+    e_drho = rel_l2(rg[m] - 1.0, ro[m] - 1.0)
+    e_q = float(np.max(np.abs(qg - qo)))
+    print(f"{wl.name} storage {storage} tuning {tuned}: rel-L2 u {e_u:.2e}, "
+          f"rho-1 {e_drho:.2e}, max |dq| {e_q:.2e}")
+    assert e_u < tol_u and e_drho < tol_drho and e_q < tol_q
+    g.close()
+    o.close()
+
+
+def test_3d_benchmark_workload_fp32():
+    compare(W.config3(), iblb.FP32_DEV, 3, 1e-5, 1e-5, 1e-9)
+
+
+# binary16 keeps about three significant digits of each population deviation
+# (measured: rel-L2 2.8e-4 on u, 3.7e-4 on rho - 1, nodes within 3.4e-7)
+@pytest.mark.parametrize("storage,tol,tol_q", [(iblb.FP32_DEV, 1e-5, 1e-8),
+                                               (iblb.FP16_DEV, 2e-3, 1e-5)])
+def test_2d_spreading_workload(storage, tol, tol_q):
+    compare(W.config2(theta_eq_deg=30.0, tau=0.6), storage, 20, tol, tol, tol_q)
