@@ -74,17 +74,19 @@ def run_sequential(workloads, storage: int, stream: Optional[int] = None) -> Dic
 
 
 def serve(requests, storage: int, budget_2d: int, budget_3d: int, chunk: int = 500,
-          max_slots: int = 2048) -> Dict:
+          max_slots: int = 2048, streams=None) -> Dict:
     """Continuous-batching serving loop over `requests` (workloads.Request,
     arrival times in seconds from the start).  Returns per-request results
-    and the throughput / latency summary."""
-    import torch
+    and the throughput / latency summary.  `streams` = (2D, 3D) CUDA stream
+    handles; by default two new torch streams."""
+    if streams is None:
+        import torch
 
-    s2 = torch.cuda.Stream()
-    s3 = torch.cuda.Stream()
+        keep = (torch.cuda.Stream(), torch.cuda.Stream())
+        streams = (keep[0].cuda_stream, keep[1].cuda_stream)
     batches = {
-        9: iblb.Batch(iblb.D2Q9, storage, budget_2d, max_slots=max_slots, stream=s2.cuda_stream),
-        19: iblb.Batch(iblb.D3Q19, storage, budget_3d, max_slots=max_slots, stream=s3.cuda_stream),
+        9: iblb.Batch(iblb.D2Q9, storage, budget_2d, max_slots=max_slots, stream=streams[0]),
+        19: iblb.Batch(iblb.D3Q19, storage, budget_3d, max_slots=max_slots, stream=streams[1]),
     }
     pending = collections.deque(sorted(range(len(requests)), key=lambda i: requests[i].arrival_s))
     queue: collections.deque = collections.deque()
