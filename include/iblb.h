@@ -155,8 +155,8 @@ iblb_status iblb_set_equilibrium(iblb_handle h, const double* rho, const double*
  * axis), Sec. 4, Eq. 12: out[5] = {D = (r1 - r3)/(r1 + r3), r1, r3,
  * inclination of the r1 axis to x (degrees), enclosed area / volume}.  r1, r3
  * are the semi-axes of the ellipse (ellipsoid) with the same central second
- * moments as the enclosed region.  Needs a CCW ring / outward mesh of >= 3
- * nodes (IBLB_EINVAL otherwise).  Synchronises. */
+ * moments as the enclosed region.  Needs a CCW ring of >= 3 nodes / an
+ * outward mesh of >= 4 faces (IBLB_EINVAL otherwise).  Synchronises. */
 iblb_status iblb_deformation(iblb_handle h, double* out);
 
 /* Inside / outside classification of every cell by the current interface

@@ -691,7 +691,8 @@ iblb_status iblb_set_equilibrium(iblb_handle h, const double* rho, const double*
 iblb_status iblb_deformation(iblb_handle h, double* out)
 {
     if (!h || !out) return IBLB_EINVAL;
-    if (h->N < 3) return fail(h, IBLB_EINVAL, "deformation needs an interface");
+    if (h->N < 3 || (h->dim == 3 && h->M < 4))
+        return fail(h, IBLB_EINVAL, "deformation needs a closed interface");
     launch_deformation(h->dim, h->q, h->N, h->tri, h->M, h->defo, h->stream);
     g_launches++;
     CK(h, cudaGetLastError());
