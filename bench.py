@@ -715,10 +715,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="step", choices=["step", "batch", "serve", "shear", "spread2d", "spread3d"],
                     help="step: the 3D workload (default); batch / serve: the batched "
-                         "and served engines")
+                         "and served engines; spread2d / spread3d: the 2D precision sweep "
+                         "and the paper-scale 3D spreading runs; shear: the drop in shear")
     ap.add_argument("--count", type=int, default=256, help="batch / serve: simulations")
     ap.add_argument("--step-div", type=int, default=10,
-                    help="batch / serve: divide the 5k-50k step counts by this")
+                    help="batch / serve / spread2d: divide the step counts by this")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: arrivals per second")
     ap.add_argument("--chunk", type=int, default=500, help="serve: steps per scheduling round")
     ap.add_argument("--oracle-sample", type=int, default=6, help="serve: oracle-checked requests")
