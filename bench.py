@@ -649,6 +649,50 @@ def run_spread3d_mode(args):
     return 0
 
 
+def run_kernel2d_mode(args):
+    """Stream-collide alone on a plain D2Q9 lattice (--nx x --ny, walls, no
+    interface), the launch shape from --tuning or the autotuner: the 2D
+    roofline point.  Device time of the kernel from CUDA events."""
+    import torch
+    from paper_2604_17463_gb300 import iblb
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    storage = {"fp32": iblb.FP32_DEV, "fp16": iblb.FP16_DEV, "fp64": iblb.FP64}[args.storage]
+    stream = torch.cuda.current_stream()
+    g = iblb.Simulation(9, args.nx, args.ny, tau=0.8, wetting=False, sigma=0.0,
+                        body_force=(1e-6, 0.0, 0.0), storage=storage, stream=stream.cuda_stream)
+    if args.tuning:
+        v, bx, rows, ctas, ncw = (int(x) for x in args.tuning.split(","))
+        g.set_tuning(v, bx, 0, rows, ctas, ncw)
+        tuned = g.tuning()
+    else:
+        tuned = g.autotune(trials=5)
+    g.step(args.warmup)
+    n0 = iblb.iblb_kernel_launch_count()
+    ms = g.step_profiled(args.steps)
+    launches = iblb.iblb_kernel_launch_count() - n0
+    sc_ms = float(ms[iblb.K_STREAM_COLLIDE]) / args.steps
+    cells = g.fluid_cells
+    bytes_per_launch = g.stream_bytes_per_step
+    g.close()
+    peak, peak_kind = hbm_peak()
+    achieved = bytes_per_launch / (sc_ms * 1e-3) / 1e9
+    line = {
+        "metric": "mlups", "value": cells / (sc_ms * 1e-3) / 1e6, "unit": "MLUPS", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+        "data": "synthetic", "dtype": {"fp32": "f32", "fp16": "f32 (binary16 storage)",
+                                       "fp64": "f64"}[args.storage],
+        "config": {"workload": f"D2Q9 {args.nx}x{args.ny} stream-collide alone (walls, body "
+                               f"force, no interface)", "mode": "kernel2d",
+                   "stream_collide_tuning": tuned},
+        "roofline": {"bound": "hbm", "kernel": "stream_collide", "achieved": achieved,
+                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "bytes_per_launch": bytes_per_launch, "launch_ms": sc_ms},
+        "gpu_launches": int(launches),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_shear_mode(args):
     """Drop in shear at the paper's parameters (Sec. 4: Re = 0.01, Ca = 0.05,
     R0 = 19, tau = 1, lambda from --shear-lam): moving-wall bounce-back, the
@@ -713,7 +757,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve", "shear", "spread2d", "spread3d"],
+    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve", "shear", "spread2d", "spread3d",
+                             "kernel2d"],
                     help="step: the 3D workload (default); batch / serve: the batched "
                          "and served engines; spread2d / spread3d: the 2D precision sweep "
                          "and the paper-scale 3D spreading runs; shear: the drop in shear")
@@ -725,6 +770,8 @@ def main():
     ap.add_argument("--oracle-sample", type=int, default=6, help="serve: oracle-checked requests")
     ap.add_argument("--serve-storage", default="fp16", choices=["fp32", "fp16", "fp64"])
     ap.add_argument("--shear-lam", type=float, default=1.0, help="shear: viscosity ratio")
+    ap.add_argument("--nx", type=int, default=4096, help="kernel2d: lattice width")
+    ap.add_argument("--ny", type=int, default=4096, help="kernel2d: lattice height")
     ap.add_argument("--spread3d-taus", default="0.56,0.59,0.732,1.1",
                     help="spread3d: relaxation times of the 250x250x150 runs")
     ap.add_argument("--spread3d-sphere", type=int, default=1,
@@ -748,6 +795,8 @@ def main():
         return run_spread2d_mode(args)
     if args.mode == "spread3d":
         return run_spread3d_mode(args)
+    if args.mode == "kernel2d":
+        return run_kernel2d_mode(args)
     from paper_2604_17463_gb300 import workloads as W
     wl = W.config3()
     if args.impl == "reference":
