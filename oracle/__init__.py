@@ -48,6 +48,8 @@ class Params(ctypes.Structure):
         ("tau_out", ctypes.c_double),
         ("wall_u_lo", ctypes.c_double * 3),
         ("wall_u_hi", ctypes.c_double * 3),
+        ("shear_modulus", ctypes.c_double),
+        ("skalak_c", ctypes.c_double),
     ]
 
 
@@ -132,6 +134,12 @@ def _load():
     lib.or_sim_inside_mask.argtypes = [vp, ctypes.POINTER(ctypes.c_ubyte)]
     lib.or_sim_set_equilibrium.argtypes = [vp, dp, dp]
     lib.or_deformation.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ip, dp]
+    lib.or_skalak_W.argtypes = [ctypes.c_double] * 4
+    lib.or_skalak_W.restype = ctypes.c_double
+    lib.or_elastic_reference.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ip, dp]
+    lib.or_elastic_forces.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ip, dp,
+                                      ctypes.c_double, ctypes.c_double, dp]
+    lib.or_elastic_forces.restype = ctypes.c_double
     lib.or_sim_A.argtypes = [vp]
     lib.or_sim_A.restype = ctypes.c_double
     _lib = lib
@@ -208,9 +216,39 @@ def nodal_forces(q, tri=None, *, sigma, wetting=False, A=0.0, xi=1.0, n=9, m=3,
     return out
 
 
+def skalak_W(Gs, C, I1, I2) -> float:
+    """Skalak strain energy per unit reference area from the invariants."""
+    return _load().or_skalak_W(float(Gs), float(C), float(I1), float(I2))
+
+
+def elastic_reference(q0, tri=None) -> np.ndarray:
+    """Elastic reference data of an interface at positions q0 (see the C
+    header): [M, 5] per face in 3D, [N] reference segment lengths in 2D."""
+    q0 = np.ascontiguousarray(q0, dtype=np.float64)
+    N, dim = q0.shape
+    t = None if tri is None else np.ascontiguousarray(tri, dtype=np.int32)
+    M = 0 if t is None else t.shape[0]
+    ref = np.zeros(5 * M if dim == 3 else N)
+    _load().or_elastic_reference(dim, N, _dptr(q0), M, _iptr(t), _dptr(ref))
+    return ref.reshape(M, 5) if dim == 3 else ref
+
+
+def elastic_forces(q, ref, tri=None, *, Gs, C):
+    """(total Skalak energy, nodal forces -dE/dq [N, dim]) at positions q."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    N, dim = q.shape
+    t = None if tri is None else np.ascontiguousarray(tri, dtype=np.int32)
+    M = 0 if t is None else t.shape[0]
+    r = np.ascontiguousarray(ref, dtype=np.float64).ravel()
+    f = np.zeros((N, dim))
+    E = _load().or_elastic_forces(dim, N, _dptr(q), M, _iptr(t), _dptr(r), float(Gs), float(C),
+                                  _dptr(f))
+    return E, f
+
+
 def deformation(q, tri=None) -> dict:
     """Deformation index D = (r1 - r3)/(r1 + r3) of a closed ring (q [N, 2])
-    or outward mesh (q [N, 3], tri [M, 3]) in the shear plane (Sec. 4, Eq. 12)."""
+    or outward mesh (q [N, 3], tri [M, 3]) in the shear plane (Sec. 4, Eq. 15)."""
     q = np.ascontiguousarray(q, dtype=np.float64)
     N, dim = q.shape
     t = None if tri is None else np.ascontiguousarray(tri, dtype=np.int32)
@@ -226,7 +264,7 @@ class Sim:
     def __init__(self, lattice: int, nx: int, ny: int, nz: int = 1, *, tau=1.0, walls=True,
                  wetting=True, sigma=1e-3, xi=1.0, theta_eq_deg=90.0, pi_n=9, pi_m=3,
                  body_force=(0.0, 0.0, 0.0), tau_out=0.0, wall_u_lo=(0.0, 0.0, 0.0),
-                 wall_u_hi=(0.0, 0.0, 0.0)):
+                 wall_u_hi=(0.0, 0.0, 0.0), shear_modulus=0.0, skalak_c=0.0):
         self._lib = _load()
         p = Params()
         p.lattice = lattice
@@ -244,6 +282,8 @@ class Sim:
         for k in range(3):
             p.wall_u_lo[k] = wall_u_lo[k] if k < len(wall_u_lo) else 0.0
             p.wall_u_hi[k] = wall_u_hi[k] if k < len(wall_u_hi) else 0.0
+        p.shear_modulus = shear_modulus
+        p.skalak_c = skalak_c
         self.params = p
         self.Q = lattice
         self.dim = 2 if lattice == D2Q9 else 3
@@ -332,7 +372,7 @@ class Sim:
         self._lib.or_sim_set_equilibrium(self._h, None if r is None else _dptr(r), _dptr(u))
 
     def deformation(self) -> dict:
-        """Deformation index of the current interface (Sec. 4, Eq. 12)."""
+        """Deformation index of the current interface (Sec. 4, Eq. 15)."""
         return deformation(self.fields()[2], getattr(self, "_tri", None))
 
     def inside_mask(self) -> np.ndarray:

@@ -263,6 +263,136 @@ int or_nodal_forces(int dim, int N, const double* q, int M, const int* tri,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Elastic interface: Skalak strain energy on linear triangles               */
+/* ------------------------------------------------------------------------ */
+/* The paper forms the interface force from a finite-element strain energy
+ * (Sec. 2) and names elastic interfaces as the extension to come (Sec. 5).
+ * The law here is Skalak's (Skalak, Tozeren, Zarda, Chien, Biophys. J. 13,
+ * 245, 1973): per unit reference area
+ *   W = G_s/4 [I1^2 + 2 I1 - 2 I2 + C I2^2],
+ * with the invariants I1 = tr(Cg) - 2 and I2 = det(Cg) - 1 of the in-plane
+ * right Cauchy-Green tensor Cg = F^T F of each triangle (constant strain on a
+ * linear triangle).  F maps the triangle's reference plane onto its current
+ * position: with e1 = b - a, e2 = c - a the current edges and E1, E2 the
+ * reference edges written in an orthonormal frame of the reference plane,
+ * F = [e1 e2] [E1 E2]^-1. */
+double or_skalak_W(double Gs, double C, double I1, double I2)
+{
+    return 0.25 * Gs * (I1 * I1 + 2.0 * I1 - 2.0 * I2 + C * I2 * I2);
+}
+
+void or_elastic_reference(int dim, int N, const double* q0, int M, const int* tri, double* ref)
+{
+    if (dim == 2) {
+        for (int j = 0; j < N; j++) {
+            const int jn = (j + 1) % N;
+            const double sx = q0[2 * jn] - q0[2 * j], sy = q0[2 * jn + 1] - q0[2 * j + 1];
+            ref[j] = sqrt(sx * sx + sy * sy);
+        }
+        return;
+    }
+    for (int f = 0; f < M; f++) {
+        const double* a = q0 + 3 * tri[3 * f];
+        const double* b = q0 + 3 * tri[3 * f + 1];
+        const double* c = q0 + 3 * tri[3 * f + 2];
+        double E1[3], E2[3], n[3], u[3], v[3];
+        for (int k = 0; k < 3; k++) {
+            E1[k] = b[k] - a[k];
+            E2[k] = c[k] - a[k];
+        }
+        cross3(E1, E2, n);
+        const double nlen = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        const double L1 = sqrt(E1[0] * E1[0] + E1[1] * E1[1] + E1[2] * E1[2]);
+        for (int k = 0; k < 3; k++) {
+            u[k] = E1[k] / L1;
+            n[k] /= nlen;
+        }
+        cross3(n, u, v);  /* in-plane unit vector perpendicular to u */
+        /* reference edges in the frame (u, v): E1 -> (L1, 0), E2 -> (p, h) */
+        const double p = E2[0] * u[0] + E2[1] * u[1] + E2[2] * u[2];
+        const double h = E2[0] * v[0] + E2[1] * v[1] + E2[2] * v[2];
+        const double det = L1 * h;
+        /* inverse of [[L1, p], [0, h]] */
+        ref[5 * f + 0] = h / det;
+        ref[5 * f + 1] = -p / det;
+        ref[5 * f + 2] = 0.0;
+        ref[5 * f + 3] = L1 / det;
+        ref[5 * f + 4] = 0.5 * nlen;
+    }
+}
+
+double or_elastic_forces(int dim, int N, const double* q, int M, const int* tri,
+                         const double* ref, double Gs, double C, double* force)
+{
+    double E = 0.0;
+    if (force)
+        for (long k = 0; k < (long)N * dim; k++) force[k] = 0.0;
+    if (dim == 2) {
+        /* segment j from node j to j+1, stretch lambda = l / l0, plane strain
+         * (lambda2 = 1): E_j = l0 W(lambda^2 - 1, lambda^2 - 1); its tension
+         * T = dE_j/dl = dW/dlambda = G_s (1 + C) lambda (lambda^2 - 1) pulls
+         * node j along +t and node j+1 along -t */
+        for (int j = 0; j < N; j++) {
+            const int jn = (j + 1) % N;
+            const double sx = q[2 * jn] - q[2 * j], sy = q[2 * jn + 1] - q[2 * j + 1];
+            const double l = sqrt(sx * sx + sy * sy);
+            const double lam = l / ref[j];
+            const double e = lam * lam - 1.0;
+            E += ref[j] * or_skalak_W(Gs, C, e, e);
+            if (force) {
+                const double T = Gs * (1.0 + C) * lam * e;
+                force[2 * j] += T * sx / l;
+                force[2 * j + 1] += T * sy / l;
+                force[2 * jn] -= T * sx / l;
+                force[2 * jn + 1] -= T * sy / l;
+            }
+        }
+        return E;
+    }
+    for (int f = 0; f < M; f++) {
+        const int ia = tri[3 * f], ib = tri[3 * f + 1], ic = tri[3 * f + 2];
+        const double* Mi = ref + 5 * f;   /* Mi[2 r + c] = M_rc */
+        const double A0 = ref[5 * f + 4];
+        double e1[3], e2[3], F0[3], F1[3];
+        for (int k = 0; k < 3; k++) {
+            e1[k] = q[3 * ib + k] - q[3 * ia + k];
+            e2[k] = q[3 * ic + k] - q[3 * ia + k];
+        }
+        /* F = [e1 e2] M: column j = e1 M_0j + e2 M_1j */
+        for (int k = 0; k < 3; k++) {
+            F0[k] = e1[k] * Mi[0] + e2[k] * Mi[2];
+            F1[k] = e1[k] * Mi[1] + e2[k] * Mi[3];
+        }
+        const double C00 = F0[0] * F0[0] + F0[1] * F0[1] + F0[2] * F0[2];
+        const double C01 = F0[0] * F1[0] + F0[1] * F1[1] + F0[2] * F1[2];
+        const double C11 = F1[0] * F1[0] + F1[1] * F1[1] + F1[2] * F1[2];
+        const double I1 = C00 + C11 - 2.0;
+        const double I2 = C00 * C11 - C01 * C01 - 1.0;
+        E += A0 * or_skalak_W(Gs, C, I1, I2);
+        if (!force) continue;
+        /* S = dW/dCg = W_1 Id + W_2 cof(Cg), W_1 = dW/dI1, W_2 = dW/dI2,
+         * cof(Cg) = [[C11, -C01], [-C01, C00]] = d(det Cg)/dCg */
+        const double W1 = 0.5 * Gs * (I1 + 1.0);
+        const double W2 = 0.5 * Gs * (C * I2 - 1.0);
+        const double S00 = W1 + W2 * C11, S01 = -W2 * C01, S11 = W1 + W2 * C00;
+        /* dW/dF = 2 F S;  dW/de_k = sum_j (dW/dF)_{:,j} M_kj */
+        double G0[3], G1[3], d1[3], d2[3];
+        for (int k = 0; k < 3; k++) {
+            G0[k] = 2.0 * (F0[k] * S00 + F1[k] * S01);
+            G1[k] = 2.0 * (F0[k] * S01 + F1[k] * S11);
+            d1[k] = G0[k] * Mi[0] + G1[k] * Mi[1];
+            d2[k] = G0[k] * Mi[2] + G1[k] * Mi[3];
+        }
+        for (int k = 0; k < 3; k++) {
+            force[3 * ib + k] -= A0 * d1[k];
+            force[3 * ic + k] -= A0 * d2[k];
+            force[3 * ia + k] += A0 * (d1[k] + d2[k]);
+        }
+    }
+    return E;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Simulation state                                                           */
 /* ------------------------------------------------------------------------ */
 struct or_sim {
@@ -286,6 +416,7 @@ struct or_sim {
     double* phi;     /* [N][dim] */
     double* qdot;    /* [N][dim] */
     unsigned char* inside;  /* [ncell] 1 inside the interface */
+    double* eref;    /* elastic reference of the interface as set (see above) */
 };
 
 static long cell_index(const or_sim* s, int x, int y, int z)
@@ -349,6 +480,7 @@ void or_sim_destroy(or_sim* s)
     free(s->phi);
     free(s->qdot);
     free(s->inside);
+    free(s->eref);
     free(s);
 }
 
@@ -360,6 +492,8 @@ int or_sim_set_interface(or_sim* s, int N, const double* q, int M, const int* tr
     free(s->tri);
     free(s->phi);
     free(s->qdot);
+    free(s->eref);
+    s->eref = NULL;
     s->N = N;
     s->M = (s->dim == 3) ? M : N;
     s->q = (double*)malloc(sizeof(double) * (N > 0 ? N : 1) * s->dim);
@@ -370,6 +504,11 @@ int or_sim_set_interface(or_sim* s, int N, const double* q, int M, const int* tr
     if (s->dim == 3 && M > 0) {
         s->tri = (int*)malloc(sizeof(int) * 3 * M);
         memcpy(s->tri, tri, sizeof(int) * 3 * M);
+    }
+    if (N > 0 && s->p.shear_modulus != 0.0) {
+        /* the interface as set is the elastic reference shape */
+        s->eref = (double*)malloc(sizeof(double) * (s->dim == 3 ? 5 * (size_t)M : (size_t)N));
+        or_elastic_reference(s->dim, N, s->q, s->M, s->tri, s->eref);
     }
     return 0;
 }
@@ -411,9 +550,18 @@ static double wall_plane(const or_sim* s)
 
 int or_sim_nodal_forces(const or_sim* s, double* phi, double* normal, double* chi)
 {
-    return or_nodal_forces(s->dim, s->N, s->q, s->M, s->tri, s->p.sigma,
-                           s->p.wetting && s->p.walls, s->A, s->p.xi, s->p.pi_n,
-                           s->p.pi_m, wall_plane(s), phi, NULL, NULL, normal, chi);
+    const int bad = or_nodal_forces(s->dim, s->N, s->q, s->M, s->tri, s->p.sigma,
+                                    s->p.wetting && s->p.walls, s->A, s->p.xi, s->p.pi_n,
+                                    s->p.pi_m, wall_plane(s), phi, NULL, NULL, normal, chi);
+    if (phi && s->eref) {
+        /* elastic interface: add -dE/dq of the Skalak energy */
+        double* fe = (double*)malloc(sizeof(double) * (size_t)s->N * s->dim);
+        or_elastic_forces(s->dim, s->N, s->q, s->M, s->tri, s->eref, s->p.shear_modulus,
+                          s->p.skalak_c, fe);
+        for (long k = 0; k < (long)s->N * s->dim; k++) phi[k] += fe[k];
+        free(fe);
+    }
+    return bad;
 }
 
 /* Visit the delta stencil of node position qj: calls back with the cell index
@@ -889,7 +1037,7 @@ void or_sim_observables(const or_sim* s, or_obs* o)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Deformation index D = (r1 - r3) / (r1 + r3) (drop in shear, Sec. 4, Eq. 12) */
+/* Deformation index D = (r1 - r3) / (r1 + r3) (drop in shear, Sec. 4, Eq. 15) */
 /* The enclosed region is split into simplices from a reference point p0     */
 /* (the node mean): triangles (p0, a, b) of the ring in 2D, tetrahedra        */
 /* (p0, a, b, c) of the mesh in 3D, each with a signed measure.  Over a       */

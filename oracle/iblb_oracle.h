@@ -44,6 +44,8 @@ typedef struct {
                              (viscosity ratio 1).  Inside cells use tau. */
     double wall_u_lo[3];  /* velocity of the lower / upper wall (tangential; */
     double wall_u_hi[3];  /* the wall-axis component must be 0)              */
+    double shear_modulus; /* elastic interface: Skalak shear modulus G_s   */
+    double skalak_c;      /* Skalak area-dilation parameter C (0 with G_s 0) */
 } or_params;
 
 /* Fixed-size observables block (every entry FP64). */
@@ -76,7 +78,27 @@ int or_nodal_forces(int dim, int N, const double* q, int M, const int* tri,
                     double* phi, double* phi_sigma, double* phi_pi,
                     double* normal, double* chi);
 
-/* Deformation of a closed interface (the drop-in-shear test of Sec. 4, Eq. 12):
+/* ---- elastic interface (the elasticity outlook of Sec. 5; Sec. 2 forms the
+ * interface force from a finite-element strain energy) ----
+ * Skalak's strain energy per unit reference area of a membrane element,
+ *   W = G_s/4 [I1^2 + 2 I1 - 2 I2 + C I2^2],
+ *   I1 = lambda1^2 + lambda2^2 - 2,  I2 = lambda1^2 lambda2^2 - 1,
+ * with lambda1, lambda2 the principal in-plane stretch ratios, on linear
+ * (constant-strain) triangles whose reference shape is the interface as it
+ * was set.  2D rings: the plane-strain reduction lambda2 = 1 per unit
+ * reference length of each segment.  The nodal elastic force is minus the
+ * gradient of the total energy. */
+double or_skalak_W(double Gs, double C, double I1, double I2);
+/* Reference data of an interface at positions q0: 3D, per face the inverse
+ * M of the 2x2 matrix whose columns are the reference edges b - a, c - a in
+ * the face's own orthonormal frame, then the reference area (5 doubles per
+ * face, [M00, M01, M10, M11, A0]); 2D, per segment its reference length. */
+void   or_elastic_reference(int dim, int N, const double* q0, int M, const int* tri, double* ref);
+/* Total elastic energy at q; force [N][dim] (may be NULL) receives -dE/dq. */
+double or_elastic_forces(int dim, int N, const double* q, int M, const int* tri,
+                         const double* ref, double Gs, double C, double* force);
+
+/* Deformation of a closed interface (the drop-in-shear test of Sec. 4, Eq. 15):
  * the second moment S of the enclosed region about its centroid, restricted
  * to the shear plane (x and the wall axis), gives the semi-axes r1 >= r3 of
  * the ellipse (2D) / ellipsoid section (3D) with the same moments, and
