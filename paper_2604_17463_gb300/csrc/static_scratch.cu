@@ -10,6 +10,7 @@
 // sums live in the file-scope device array below (IBLB_STATIC_PARTIALS
 // doubles, 512 KiB, held by every GPU that loads the library until the
 // process exits).  The caller passes the populations and the output.
+#include <atomic>
 #include <cmath>
 
 #include "../../include/iblb.h"
@@ -28,7 +29,11 @@ constexpr int MS_CELLS_PER_THREAD = 64;
 constexpr long long MS_CELLS_PER_BLOCK = (long long)MS_THREADS * MS_CELLS_PER_THREAD;
 constexpr int MS_MAX_DEVICES = 64;
 
-double* g_partials_addr[MS_MAX_DEVICES] = {nullptr};
+// Device address of g_mass_partials per device, resolved by the first call on
+// that device.  Atomic, so that host threads making their first calls at the
+// same time do not race (both resolve the same address).
+std::atomic<double*> g_partials_addr[MS_MAX_DEVICES];
+constexpr int MS_TOTAL_THREADS = 256;
 
 // Block b sums the fluid cells [b * MS_CELLS_PER_BLOCK, (b+1) * MS_CELLS_PER_BLOCK)
 // in a fixed order and overwrites partial[b]: no entry needs clearing.
@@ -63,13 +68,27 @@ k_mass_static_partials(int Q, const typename StorageT<ST>::S* __restrict__ f, Gr
     }
 }
 
-// One thread adds the partials in order.
-__global__ void k_mass_static_total(const double* __restrict__ partial, int n, double* out)
+// One block adds the n partials in a fixed order: thread k sums the
+// contiguous range [k * n / T, (k + 1) * n / T), then a fixed shuffle and
+// shared-memory tree combines the T sums.  The order depends on n only, so
+// the result is deterministic.
+__global__ void __launch_bounds__(MS_TOTAL_THREADS)
+k_mass_static_total(const double* __restrict__ partial, int n, double* out)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int k = threadIdx.x;
+    const int lo = (int)((long long)k * n / MS_TOTAL_THREADS);
+    const int hi = (int)((long long)(k + 1) * n / MS_TOTAL_THREADS);
     double t = 0.0;
-    for (int b = 0; b < n; b++) t += partial[b];
-    *out = t;
+    for (int b = lo; b < hi; b++) t += partial[b];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    __shared__ double red[MS_TOTAL_THREADS / 32];
+    if ((k & 31) == 0) red[k >> 5] = t;
+    __syncthreads();
+    if (k == 0) {
+        double s = 0.0;
+        for (int w = 0; w < MS_TOTAL_THREADS / 32; w++) s += red[w];
+        *out = s;
+    }
 }
 
 }  // namespace
@@ -95,14 +114,15 @@ extern "C" iblb_status iblb_mass_static(const void* f_dev, int lattice, int stor
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MS_MAX_DEVICES) return IBLB_ECUDA;
-    if (!g_partials_addr[dev]) {
+    double* partial = g_partials_addr[dev].load(std::memory_order_acquire);
+    if (!partial) {
         // first call on this device (with it current): resolve the device
         // address of the static array once
         void* ptr = nullptr;
         if (cudaGetSymbolAddress(&ptr, g_mass_partials) != cudaSuccess || !ptr) return IBLB_ECUDA;
-        g_partials_addr[dev] = static_cast<double*>(ptr);
+        partial = static_cast<double*>(ptr);
+        g_partials_addr[dev].store(partial, std::memory_order_release);
     }
-    double* partial = g_partials_addr[dev];
 
     GridParams g{};
     g.nx = nx;
@@ -122,6 +142,8 @@ extern "C" iblb_status iblb_mass_static(const void* f_dev, int lattice, int stor
         k_mass_static_partials<ST_FP32><<<nb, MS_THREADS, 0, s>>>(lattice, (const float*)f_dev, g, inv_scale, partial);
     else
         k_mass_static_partials<ST_FP16><<<nb, MS_THREADS, 0, s>>>(lattice, (const __half*)f_dev, g, inv_scale, partial);
-    k_mass_static_total<<<1, 32, 0, s>>>(partial, nb, mass_dev);
-    return cudaGetLastError() == cudaSuccess ? IBLB_OK : IBLB_ECUDA;
+    k_mass_static_total<<<1, MS_TOTAL_THREADS, 0, s>>>(partial, nb, mass_dev);
+    if (cudaGetLastError() != cudaSuccess) return IBLB_ECUDA;
+    add_launches(2);
+    return IBLB_OK;
 }
