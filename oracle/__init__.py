@@ -95,11 +95,43 @@ def build(force: bool = False) -> str:
         return _LIB_PATH
 
 
+_OMP_LIB_PATH = os.path.join(_OUT_DIR, "liboracle_omp.so")
+_omp_lib = None
+
+
+def build_openmp(force: bool = False) -> str:
+    """The same oracle source compiled with -fopenmp: its stream-collide rows
+    run on all host cores with unchanged arithmetic per cell.  Used only to
+    time the oracle across the host's cores."""
+    with _lock:
+        newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+        if not force and os.path.exists(_OMP_LIB_PATH) and os.path.getmtime(_OMP_LIB_PATH) >= newest:
+            return _OMP_LIB_PATH
+        os.makedirs(_OUT_DIR, exist_ok=True)
+        tmp = _OMP_LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off",
+               "-fno-fast-math", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _OMP_LIB_PATH)
+        return _OMP_LIB_PATH
+
+
+def _load_openmp():
+    global _omp_lib
+    if _omp_lib is None:
+        _omp_lib = _bind(ctypes.CDLL(build_openmp()))
+    return _omp_lib
+
+
 def _load():
     global _lib
     if _lib is not None:
         return _lib
-    lib = ctypes.CDLL(build())
+    _lib = _bind(ctypes.CDLL(build()))
+    return _lib
+
+
+def _bind(lib):
     dp = ctypes.POINTER(ctypes.c_double)
     ip = ctypes.POINTER(ctypes.c_int)
     vp = ctypes.c_void_p
@@ -142,7 +174,6 @@ def _load():
     lib.or_elastic_forces.restype = ctypes.c_double
     lib.or_sim_A.argtypes = [vp]
     lib.or_sim_A.restype = ctypes.c_double
-    _lib = lib
     return lib
 
 
@@ -264,8 +295,10 @@ class Sim:
     def __init__(self, lattice: int, nx: int, ny: int, nz: int = 1, *, tau=1.0, walls=True,
                  wetting=True, sigma=1e-3, xi=1.0, theta_eq_deg=90.0, pi_n=9, pi_m=3,
                  body_force=(0.0, 0.0, 0.0), tau_out=0.0, wall_u_lo=(0.0, 0.0, 0.0),
-                 wall_u_hi=(0.0, 0.0, 0.0), shear_modulus=0.0, skalak_c=0.0):
-        self._lib = _load()
+                 wall_u_hi=(0.0, 0.0, 0.0), shear_modulus=0.0, skalak_c=0.0,
+                 openmp=False):
+        # openmp: the -fopenmp build (threads from OMP_NUM_THREADS), for timing
+        self._lib = _load_openmp() if openmp else _load()
         p = Params()
         p.lattice = lattice
         p.nx, p.ny, p.nz = nx, ny, (1 if lattice == D2Q9 else nz)

@@ -804,6 +804,11 @@ int or_sim_step(or_sim* s, int nsteps)
         const int two_tau = s->p.tau_out > 0.0 && s->p.tau_out != s->p.tau;
         if (two_tau) or_sim_inside_mask(s, s->inside);
 
+        /* every cell is updated from the old populations alone, so the rows
+         * may run in any order; a build with -fopenmp (used only to time the
+         * oracle on all host cores) splits them over threads, with the same
+         * arithmetic per cell */
+#pragma omp parallel for collapse(2) schedule(static)
         for (int z = 0; z < s->L[2]; z++)
             for (int y = 0; y < s->L[1]; y++) {
                 int layer = (s->wall_axis == 1) ? y : z;
