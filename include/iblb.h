@@ -86,6 +86,23 @@ typedef struct {
                                Tangential components only (the wall-axis
                                component, and z in 2D, must be 0), |u| <= 0.3;
                                needs walls = 1.  All zero = resting walls. */
+    int deterministic_spread; /* 1: spread the nodal forces (Eq. 8) as an
+                               ordered gather (each cell sums the nodes whose
+                               stencils cover it in a fixed order) instead of
+                               a scatter with atomic additions, so that runs
+                               are bitwise reproducible; 0: atomics (faster;
+                               FP64 sums then vary in their last bits). */
+    double shear_modulus;   /* elastic interface (the elasticity outlook of
+                               Sec. 5; Sec. 2 forms the interface force from a
+                               finite-element strain energy): shear modulus G_s
+                               of Skalak's law W = G_s/4 [I1^2 + 2 I1 - 2 I2 +
+                               C I2^2] per unit reference area on linear
+                               triangles (2D rings: plane strain), whose
+                               reference shape is the interface as set by
+                               iblb_set_interface; added to the surface
+                               tension.  0 = no elasticity (a clean drop). */
+    double skalak_c;        /* Skalak's area-dilation parameter C (> -1/2; the
+                               area modulus is G_s (1 + 2C)) */
 } iblb_config;
 
 typedef struct {
@@ -102,43 +119,81 @@ typedef struct {
 
 typedef struct iblb_sim* iblb_handle;
 
-/* Create a simulation at rest (rho = 1, u = 0) on `cuda_stream`
- * (a cudaStream_t; NULL = the legacy default stream).  Allocates the device
- * state: two population buffers, the moments, the force density and the
- * band flags.  Returns IBLB_EINVAL for a bad config, IBLB_ENOMEM if the
- * device cannot hold it. */
+/* Create a simulation at rest (rho = 1, u = 0, f_i = w_i) on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  The configuration is
+ * the paper's statement of the problem, Sec. 2: the lattice and velocity
+ * stencil with the populations f_i of Eq. 1, the relaxation time tau of
+ * Eq. 2 (and tau_out, tau(x, t) for the viscosity ratio lambda), the
+ * surface tension sigma of Eq. 9, and n, m, xi and theta_eq of Eq. 10-11,
+ * from which A is computed by Eq. 11.  Allocates the device state: two
+ * population buffers, the moments, the force density and the band flags;
+ * the library owns it.  cfg is read only.  *out receives the handle (NULL
+ * on failure).  Returns IBLB_EINVAL for a bad config (reason in
+ * iblb_last_error(NULL)), IBLB_ENOMEM if the device cannot hold it,
+ * IBLB_ECUDA if a CUDA call fails. */
 iblb_status iblb_create(const iblb_config* cfg, void* cuda_stream, iblb_handle* out);
+
+/* Free the device state of a handle (synchronises its stream first).  A NULL
+ * handle is ignored.  A library service; the paper has no counterpart. */
 void        iblb_destroy(iblb_handle h);
+
+/* Text of the last failure on a handle (NULL: of the last failed
+ * iblb_create on this thread); owned by the library, valid until the next
+ * call on the handle.  A library service; the paper has no counterpart. */
 const char* iblb_last_error(iblb_handle h);
 const char* iblb_status_string(iblb_status s);
 
-/* Set the interface (Sec. 2: N Lagrangian nodes, fixed connectivity).
+/* Set the interface (Sec. 2: N Lagrangian nodes q_j on a triangular mesh
+ * whose number of triangles stays fixed; the 2D analogue is a closed ring).
  * xyz [n_nodes][dim] host FP64.  2D: the nodes form a closed ring in
  * counter-clockwise order and `tri` must be NULL.  3D: tri [n_faces][3]
- * host int32, outward-oriented.  n_nodes = 0 removes the interface. */
+ * host int32, outward-oriented.  n_nodes = 0 removes the interface.  Both
+ * arrays are copied (the caller keeps them).  IBLB_EINVAL on a bad array or
+ * index, IBLB_ENODE_IN_WALL if a node lies at or below the wall plane with
+ * wetting on; synchronises. */
 iblb_status iblb_set_interface(iblb_handle h, const double* xyz, int n_nodes,
                                const int* tri, int n_faces);
 
-/* Advance n_steps time steps (asynchronous on the stream).  Each step:
- * nodal forces at q(t) -> spread F(t) -> fused stream-collide with Guo
- * forcing -> interpolate u(t) at q(t) -> Euler.  The last step of a call
- * also stores rho and u of every cell for iblb_read_fields. */
+/* Advance n_steps time steps (asynchronous on the stream).  Each step is
+ * one update of Sec. 2 with every term at time t: nodal forces at q(t)
+ * (surface tension and the wetting force phi_Pi,j of Eq. 9-11) -> spread
+ * F(t) (Eq. 8) -> the lattice Boltzmann equation (Eq. 1) with BGK
+ * relaxation (Eq. 2-3), the Guo source (Eq. 4) and the moments with the
+ * half-force correction (Eq. 5-6), fused as one pull-streaming kernel ->
+ * interpolate u(t) at q(t) (Eq. 7) -> the forward Euler update of the nodes.
+ * The last step of a call also stores rho and u of every cell for
+ * iblb_read_fields.  IBLB_EINVAL for n_steps < 0; device faults are reported
+ * by the next synchronising call. */
 iblb_status iblb_step(iblb_handle h, int n_steps);
 
-/* Synchronise the stream and report any latched device fault. */
+/* Synchronise the stream and report any latched device fault (a library
+ * service; the paper has no counterpart). */
+iblb_status iblb_clear_faults(iblb_handle h);  /* clear the latched device
+                                                  faults (synchronises); the
+                                                  state that produced them is
+                                                  left as it is */
 iblb_status iblb_sync(iblb_handle h);
 
-/* rho [cells], u [dim][cells] of the last moment evaluation (zero on solid
- * cells) and node positions xyz [N][dim]; any pointer may be NULL.
- * Synchronises. */
+/* Read back the state after the last step: rho [cells] and u [dim][cells]
+ * of the last moment evaluation (Eq. 5-6, with the force of that step; zero
+ * on solid cells) and the node positions q_j after the last Euler update,
+ * xyz [N][dim].  Caller-owned host buffers, FP64; any pointer may be NULL.
+ * Synchronises; returns a latched device fault as its status. */
 iblb_status iblb_read_fields(iblb_handle h, double* rho, double* u, double* xyz);
 
-/* Replace / read the populations f_i, host FP64 [Q][cells]. */
+/* Replace / read the populations f_i of Eq. 1, host FP64 [Q][cells]
+ * (caller-owned; converted from / to the storage form).  Synchronise. */
 iblb_status iblb_set_populations(iblb_handle h, const double* f);
 iblb_status iblb_get_populations(iblb_handle h, double* f);
 
-/* FP64 observables (A7): mass, volume, height, fitted contact angle,
- * contact-line position, film thickness.  Synchronises. */
+/* FP64 observables of the current state: mass (the sum of rho, Eq. 5, over
+ * the fluid cells), enclosed area / volume of the interface, the height h
+ * as the distance between the highest and lowest nodes along the wall axis
+ * (as the paper extracts h(t), Sec. 3), and the apparent contact angle,
+ * contact-line position and film thickness epsilon (Sec. 2) from a
+ * least-squares circle / sphere fit through the nodes above 3 xi, cut at the
+ * lowest node (the paper measures only h; the estimator is this library's).
+ * out is caller-owned.  Synchronises. */
 iblb_status iblb_observables(iblb_handle h, iblb_obs* out);
 
 /* ---- single-stage entry points (each runs one kernel of the step) ---- */
@@ -152,7 +207,7 @@ iblb_status iblb_observables(iblb_handle h, iblb_obs* out);
 iblb_status iblb_set_equilibrium(iblb_handle h, const double* rho, const double* u);
 
 /* Deformation of the current interface in the shear plane (x and the wall
- * axis), Sec. 4, Eq. 12: out[5] = {D = (r1 - r3)/(r1 + r3), r1, r3,
+ * axis), Sec. 4, Eq. 15: out[5] = {D = (r1 - r3)/(r1 + r3), r1, r3,
  * inclination of the r1 axis to x (degrees), enclosed area / volume}.  r1, r3
  * are the semi-axes of the ellipse (ellipsoid) with the same central second
  * moments as the enclosed region.  Needs a CCW ring of >= 3 nodes / an
@@ -202,6 +257,9 @@ iblb_status iblb_step_profiled(iblb_handle h, int n_steps, double* kernel_ms);
  *   variant 2: two x-adjacent cells per thread with 8 / 4-byte population
  *              loads and stores and packed FP32x2 arithmetic (FP32 and
  *              binary16 storage, even nx), block_x threads per block;
+ *   variant 3: two y-adjacent cells per thread (rows y, y + 1 of a layer)
+ *              with scalar loads and stores and packed FP32x2 arithmetic
+ *              (D3Q19, FP32 and binary16 storage), block_x threads per block;
  *   variant 1: the pipelined kernel: persistent CTAs in which a producer warp
  *              stages the source rows in shared memory with bulk asynchronous
  *              copies and consumer_warps warps collide from there;
@@ -216,6 +274,13 @@ typedef struct {
     int rows_per_tile;
     int ctas_per_sm;
     int consumer_warps;
+    long long wait_limit_cycles;  /* pipelined kernel: clock cycles a wait on
+                                     its pipeline may take before the kernel
+                                     gives up, latches IBLB_ETIMEOUT and stops
+                                     (the populations of that step are then
+                                     incomplete); 0 = about 2 s.  Copies in
+                                     flight are always waited for (bounded by
+                                     about 2 s) before the kernel exits. */
 } iblb_tuning;
 
 /* Set / read the launch shape.  iblb_set_tuning synchronises. */
@@ -230,7 +295,8 @@ iblb_status iblb_get_tuning(iblb_handle h, iblb_tuning* t);
  * unchanged.  `chosen` (may be NULL) receives the kept shape.  Synchronises. */
 iblb_status iblb_autotune(iblb_handle h, int trials, iblb_tuning* chosen);
 
-/* The stream-collide variant in use (0 plain, 1 pipelined, 2 pairs). */
+/* The stream-collide variant in use (0 plain, 1 pipelined, 2 x pairs,
+ * 3 row pairs). */
 int iblb_stream_collide_variant(iblb_handle h);
 
 /* Algorithmic HBM bytes of one stream-collide launch: populations read once
@@ -240,14 +306,16 @@ long long iblb_fluid_cells(iblb_handle h);
 
 /* ---- batched engine and serving admission ----
  *
- * A batch advances many independent droplet simulations ("slots") of one
+ * These calls are services of this library: the paper runs one simulation
+ * at a time, and each slot computes exactly the step of iblb_step (Sec. 2,
+ * Eq. 1-11 and forward Euler).  A batch advances many independent droplet simulations ("slots") of one
  * lattice type and one storage form with shared launches: every phase of a
  * time step is one launch over all active slots (the stream-collide phase a
  * persistent kernel walking a (slot, tile) work list).  Slot state lives in
  * one device arena of hbm_budget_bytes allocated at creation; a request is
  * admitted when its footprint fits (first fit), else IBLB_EAGAIN.  Slots
  * must have walls, no body force, and the batch's lattice and storage.
- * Each slot's tile shape (cells per thread of the stream-collide tiles) is
+ * Each slot's tile shape (32-cell row segments per stream-collide work item) is
  * chosen at admission by timing the candidates on that slot (cached per
  * lattice width).  Calls on one batch are not thread-safe. */
 typedef struct iblb_batch_s* iblb_batch;
@@ -261,25 +329,46 @@ typedef struct {
 /* Device bytes one slot of this configuration and interface takes. */
 size_t iblb_batch_footprint(const iblb_config* cfg, int n_nodes, int n_faces);
 
+/* Create a batch for slots of one lattice (IBLB_D2Q9 / IBLB_D3Q19) and one
+ * storage form, with a device arena of hbm_budget_bytes (rounded down to
+ * 256 B) and up to max_slots slots, working on cuda_stream.  The library
+ * owns the arena.  IBLB_EINVAL for bad arguments, IBLB_ENOMEM if the arena
+ * cannot be allocated. */
 iblb_status iblb_batch_create(int lattice, int storage, size_t hbm_budget_bytes, int max_slots,
                               void* cuda_stream, iblb_batch* out);
 void        iblb_batch_destroy(iblb_batch b);
 const char* iblb_batch_last_error(iblb_batch b);
 
-/* Admit a simulation at rest with the given interface (as iblb_set_interface)
- * for n_steps steps; *slot_out receives its slot.  IBLB_EAGAIN: no free slot
- * or no room in the arena now (retry after releases).  Synchronises. */
+/* Admit a simulation at rest with the given configuration (as iblb_create:
+ * the problem statement of Sec. 2) and interface (as iblb_set_interface)
+ * for n_steps steps; *slot_out receives its slot.  cfg, xyz and tri are
+ * copied.  IBLB_EAGAIN: no free slot or no room in the arena now (retry
+ * after releases); IBLB_EINVAL: a configuration the batch cannot take (see
+ * above) or a bad interface.  Synchronises. */
 iblb_status iblb_batch_admit(iblb_batch b, const iblb_config* cfg, const double* xyz, int n_nodes,
                              const int* tri, int n_faces, long long n_steps, int* slot_out);
 
-/* Advance every active slot by up to max_steps steps (asynchronous).  A slot
- * stops at its own last step and becomes done; *n_completed (may be NULL)
- * counts the slots that completed during this call. */
+/* Advance every active slot by up to max_steps steps of Sec. 2 (as
+ * iblb_step; asynchronous).  A slot stops at its own last step and becomes
+ * done; *n_completed (may be NULL) counts the slots that completed during
+ * this call. */
 iblb_status iblb_batch_run(iblb_batch b, int max_steps, int* n_completed);
+
+/* As iblb_batch_run, for measurement: the steps run one launch at a time
+ * (no CUDA graph) with a CUDA event pair around each phase.
+ * kernel_ms[IBLB_K_COUNT] receives the summed device time of each phase (ms;
+ * indices as for iblb_step_profiled); *stream_collide_bytes (may be NULL)
+ * the summed algorithmic bytes of the stream-collide launches (populations
+ * read once and written once per fluid cell of every active slot).  Results
+ * are those of iblb_batch_run.  IBLB_EINVAL on a NULL batch or kernel_ms.
+ * Synchronises after every step. */
+iblb_status iblb_batch_run_profiled(iblb_batch b, int max_steps, int* n_completed,
+                                    double* kernel_ms, double* stream_collide_bytes);
 iblb_status iblb_batch_sync(iblb_batch b);
 
-/* Slots that are done and not yet released (up to cap of them in
- * done_slots; *n_done is their total number). */
+/* Slots that are done and not yet released (up to cap of them in the
+ * caller's done_slots; *n_done is their total number).  Host bookkeeping
+ * only: it does not wait for the device (iblb_batch_sync does). */
 iblb_status iblb_batch_poll(iblb_batch b, int* done_slots, int cap, int* n_done);
 
 /* Steps done by a slot, and its latched device faults as a status. */
@@ -294,7 +383,13 @@ iblb_status iblb_batch_read_fields(iblb_batch b, int slot, double* rho, double* 
 iblb_status iblb_batch_release(iblb_batch b, int slot);
 iblb_status iblb_batch_stats(iblb_batch b, iblb_batch_info* info);
 
-/* The cells per thread chosen by the tile autotuner for a slot. */
+/* Steps until the next active slot completes (-1 if none is active); host
+ * bookkeeping, no synchronisation.  Lets a serving loop advance a batch
+ * exactly to its next completion. */
+long long iblb_batch_steps_to_next_completion(iblb_batch b);
+
+/* The 32-cell row segments per stream-collide work item chosen by the tile
+ * autotuner for a slot. */
 int iblb_batch_slot_tile(iblb_batch b, int slot);
 
 /* ---- mass reduction without device allocation ----
@@ -326,10 +421,17 @@ int iblb_batch_slot_tile(iblb_batch b, int slot);
  * partials it uses (the array keeps the last call's values; nothing needs
  * to start at zero), and all calls share the array: calls that overlap on
  * the GPU (on different streams, or from different threads) race and give
- * wrong results.  The first call on a device resolves the array's device
- * address with that device current; make that first call before any stream
- * capture.  The call makes no cudaMalloc, cudaFree or other allocating call.
- * Returns IBLB_EINVAL for bad arguments, IBLB_ECUDA if a CUDA call fails. */
+ * wrong results.  The first call on a device does the set-up: with that
+ * device current it resolves the array's device address (which also makes
+ * the CUDA runtime load this library's device code on that device, if it
+ * has not yet done so) and keeps the address for later calls.  So make that
+ * first call during start-up: before any stream capture, and before the
+ * caller reserves the device memory it will run from.  The kept address
+ * belongs to the device's primary context of this process: after a
+ * cudaDeviceReset the array and its address are gone, and this entry point
+ * must not be called again in that process.  Later calls make no cudaMalloc,
+ * cudaFree or other allocating call.  Returns IBLB_EINVAL for bad
+ * arguments, IBLB_ECUDA if a CUDA call fails. */
 #define IBLB_STATIC_PARTIALS 65536
 iblb_status iblb_mass_static(const void* f_dev, int lattice, int storage, int nx, int ny, int nz,
                              int walls, int fp16_scale_exp, double* mass_dev, void* cuda_stream);

@@ -5,10 +5,9 @@
 // storage form.  Each time step runs the same phases as a single simulation
 // (nodal forces, spread, stream-collide, interpolate + advect; Sec. 2 of the
 // paper), but every phase is ONE launch over all active slots:
-//   - stream-collide: a persistent kernel whose blocks fetch (slot, tile) work
-//     items from a list with an atomic counter; a tile is 128 x cpt consecutive
-//     fluid cells of one slot, cpt (cells per thread) chosen per slot by the
-//     tile autotuner;
+//   - stream-collide: a persistent kernel whose warps walk contiguous ranges
+//     of a (slot, row, x0) work list; an item is cpt 32-cell segments of one
+//     lattice row of one slot, cpt chosen per slot by the tile autotuner;
 //   - IB phases: one thread (forces) or one warp (spread, interpolation) per
 //     (slot, node) item of a concatenated node list.
 // Slot state lives in one device arena (the batch's HBM budget) carved by a
@@ -26,8 +25,38 @@
 #include "../../include/iblb.h"
 #include "ib_core.cuh"
 #include "lbm_core.cuh"
+#include "spread_det.cuh"
 
 namespace iblb {
+
+// Division of a 32-bit unsigned integer by an invariant divisor d >= 1 with
+// one multiply-high (Granlund & Montgomery, "Division by invariant integers
+// using multiplication", PLDI 1994, Fig. 4.1): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1,
+//   n / d = (t + ((n - t) >> s1)) >> s2,  t = umulhi(m, n),
+//   s1 = min(l, 1), s2 = max(l - 1, 0),
+// exact for every 32-bit n.
+struct FastDiv {
+    unsigned m;
+    int s1, s2;
+};
+
+inline FastDiv make_fastdiv(unsigned d)
+{
+    int l = 0;
+    while ((1ull << l) < (unsigned long long)d) l++;
+    FastDiv f;
+    f.m = (unsigned)((((1ull << 32) * ((1ull << l) - d)) / d) + 1ull);
+    f.s1 = l < 1 ? l : 1;
+    f.s2 = l - 1 > 0 ? l - 1 : 0;
+    return f;
+}
+
+__device__ __forceinline__ unsigned fast_div(unsigned n, unsigned m, int s1, int s2)
+{
+    const unsigned t = __umulhi(m, n);
+    return (t + ((n - t) >> s1)) >> s2;
+}
 
 struct SlotDev {
     void* f[2];
@@ -42,7 +71,8 @@ struct SlotDev {
     float omega_f, scale, inv_scale;
     int cur_base;          // current buffer = cur_base ^ batch parity
     unsigned* rng;         // two-entry step counter for binary16 stochastic rounding
-    int cpt;               // cells per thread of this slot's tiles
+    int cpt;               // 32-cell row segments per stream-collide work item
+    FastDiv div_nx, div_ny;  // fluid-cell index -> row -> (y, z)
     double* q;
     double* phi;
     int N, M;
@@ -57,81 +87,212 @@ namespace {
 
 constexpr int BT = 128;  // threads per stream-collide block
 
+// Rows of 32-cell segments a warp of the batched stream-collide works on at
+// once (their loads are all issued before any of them is collided, so that
+// enough bytes are in flight per SM for the HBM bound): two for the lighter
+// forms (D2Q9, and binary16 storage, whose cells carry fewer bytes), one for
+// D3Q19 FP32 and for FP64 (bound by the FP64 arithmetic).  A slot's work
+// items hold cpt segments, a multiple of this.
+template <int Q, int ST> struct BIlp {
+    static constexpr int value = ST == ST_FP64 ? 1 : ((Q == 9 || ST == ST_FP16) ? 2 : 1);
+};
+int b_ilp(int Q, int storage)
+{
+    return storage == ST_FP64 ? 1 : ((Q == 9 || storage == ST_FP16) ? 2 : 1);
+}
+
+// Resident blocks per SM asked of the register allocator.
+template <int Q, int ST> struct BMinBlocks {
+    static constexpr int value = ST == ST_FP64 ? (Q == 9 ? 5 : 4) : (Q == 9 ? 6 : (ST == ST_FP32 ? 5 : 4));
+};
+
+// One stream-collide work item: cpt consecutive 32-cell segments x0 ..
+// x0 + 32 segs - 1 of one lattice row of one slot, with the slot's
+// parameters the kernel needs on every item (96 bytes, read as six 16-byte
+// loads, so that an item costs one memory round trip).
+struct __align__(16) BItem {
+    const void* f[2];      // the slot's population buffers
+    uint8_t* flags;        // the slot's band flags (per 32-cell row segment)
+    void* F;               // the slot's force density [dim][ncell]
+    void* mom;             // the slot's moments [1 + dim][ncell]
+    int slot, row;         // slot index; full row index (y, or y + ny z)
+    int x0, nx, ny, Lw;    // first cell of the item; extent; wall-axis length
+    unsigned nc;           // cells of the slot's lattice
+    int segs;              // segments in this item
+    float omega_f;         // 1 / tau
+    int cur_base;          // current buffer = cur_base ^ batch parity
+    float scale, inv_scale;  // binary16 storage scale
+    unsigned* rng;         // binary16 rounding step counter
+};
+static_assert(sizeof(BItem) == 96, "work item layout");
+
+// An item as six 16-byte words held in registers; fields by their place
+// in BItem (little-endian).
+struct BItemRegs {
+    int4 a, b, c, d, e, f;
+};
+
+__device__ __forceinline__ BItemRegs load_item(const BItem* __restrict__ items, int i)
+{
+    const int4* p = reinterpret_cast<const int4*>(items + i);
+    return BItemRegs{__ldg(p), __ldg(p + 1), __ldg(p + 2), __ldg(p + 3), __ldg(p + 4),
+                     __ldg(p + 5)};
+}
+
+__device__ __forceinline__ void* ptr_of(int lo, int hi)
+{
+    return reinterpret_cast<void*>(((unsigned long long)(unsigned)hi << 32) | (unsigned)lo);
+}
+
+// Batched stream-collide.  Warp w of the persistent grid (W warps) takes the
+// items w, w + W, w + 2W, ... of the work list, which is ordered by slot,
+// row and x0: at any time the warps of the GPU work on one window of
+// consecutive items, so each population plane is read and written in a
+// compact region (DRAM pages are reused across warps) whatever the slot
+// sizes.  Lane k of a warp takes x = x0 + 32 j + k of segment j, so a warp
+// reads and writes 32 consecutive cells of a row per plane and every
+// segment is one band flag (laid out per row as in the single-simulation
+// engine).  Everything but the x wrap depends on the row only.  In band
+// segments the force density is loaded right after the populations, so that
+// its latency overlaps theirs.  Populations are addressed by one 32-bit index
+// i * ncell + cell from the slot's buffer (Q * ncell < 2^32).  Arithmetic is
+// FP32 for the FP32 and binary16 forms, FP64 for FP64.
 template <int Q, int ST, bool WRITE_ALL>
-__global__ void __launch_bounds__(BT)
-k_b_stream_collide(const SlotDev* __restrict__ slots, const int2* __restrict__ tiles, int ntiles,
-                   int par, unsigned* counter)
+__global__ void __launch_bounds__(BT, (BMinBlocks<Q, ST>::value))
+k_b_stream_collide(const SlotDev* __restrict__ slots, const BItem* __restrict__ items,
+                   int nitems, int par)
 {
     using T = StorageT<ST>;
     using S = typename T::S;
     using R = typename T::R;
     using L = Stencil<Q>;
     constexpr int D = L::D;
-    __shared__ int s_tile;
+    constexpr int ILP = BIlp<Q, ST>::value;
     const int lane = threadIdx.x & 31;
-    for (;;) {
-        if (threadIdx.x == 0) s_tile = (int)atomicAdd(counter, 1u);
-        __syncthreads();
-        const int t = s_tile;
-        __syncthreads();
-        if (t >= ntiles) break;
-        const int2 td = tiles[t];
-        const SlotDev& sd = slots[td.x];
-        const int cur = sd.cur_base ^ par;
+    const int nwarps = gridDim.x * (BT / 32);
+    const int wid = blockIdx.x * (BT / 32) + (threadIdx.x >> 5);
+    if (wid >= nitems) return;
+
+    for (int it = wid; it < nitems; it += nwarps) {
+        const BItemRegs item = load_item(items, it);
+        const int cur = item.e.w ^ par;  // cur_base ^ parity
+        const S* __restrict__ fin =
+            (const S*)(cur ? ptr_of(item.a.z, item.a.w) : ptr_of(item.a.x, item.a.y));
+        S* __restrict__ fout =
+            (S*)(cur ? ptr_of(item.a.x, item.a.y) : ptr_of(item.a.z, item.a.w));
+        uint8_t* __restrict__ flags = (uint8_t*)ptr_of(item.b.x, item.b.y);
+        R* __restrict__ F = (R*)ptr_of(item.b.z, item.b.w);
+        R* __restrict__ mom = (R*)ptr_of(item.c.x, item.c.y);
+        const int slot = item.c.z, row = item.c.w;
+        const int x0 = item.d.x, nx = item.d.y, ny = item.d.z, Lw = item.d.w;
+        const unsigned nc = (unsigned)item.e.x;
+        const int segs = item.e.y;
+        const int nseg = (nx + 31) >> 5;
+        R omega, gsc = R(1), ginv = R(1);
+        if constexpr (sizeof(R) == 4)
+            omega = __int_as_float(item.e.z);
+        else
+            omega = slots[slot].omega;
         unsigned step = 0;
-        if constexpr (ST == ST_FP16)  // the slot's first tile advances its counter
-            step = sr_step(sd.rng + cur, sd.rng + (cur ^ 1), td.y == 0 && threadIdx.x == 0);
-        const S* fin = (const S*)sd.f[cur];
-        S* fout = (S*)sd.f[cur ^ 1];
-        R* mom = (R*)sd.mom;
-        R* F = (R*)sd.F;
-        const GridParams g = sd.g;
-        const long long nc = g.ncell;
-        for (int c = 0; c < sd.cpt; c++) {
-            const long long f = (long long)td.y + (long long)c * BT + threadIdx.x;
-            const bool valid = f < sd.nfluid;
-            const long long seg = f >> 5;
-            int band = 0;
-            if (lane == 0 && valid) band = sd.flags[seg];
-            band = __shfl_sync(0xffffffffu, band, 0);
-            if (!valid) continue;
-            const long long cell = sd.fluid_off + f;
-            const long long row = cell / g.nx;
-            const int x = (int)(cell - row * g.nx);
-            int y, z;
-            if (D == 2) {
-                y = (int)row;
-                z = 0;
-            } else {
-                y = (int)(row % g.ny);
-                z = (int)(row / g.ny);
-            }
-            R gv[Q];
-            pull_cell<Q, ST>(fin, g, x, y, z, cell, sd.inv_scale, gv);
-            R Fx = 0, Fy = 0, Fz = 0;
-            if (band) {
-                Fx = F[cell];
-                Fy = F[nc + cell];
-                F[cell] = 0;
-                F[nc + cell] = 0;
-                if (D == 3) {
-                    Fz = F[2 * nc + cell];
-                    F[2 * nc + cell] = 0;
+        if constexpr (ST == ST_FP16) {  // populations stay in their stored scale
+            unsigned* rng = (unsigned*)ptr_of(item.f.z, item.f.w);
+            gsc = __int_as_float(item.f.x);
+            ginv = __int_as_float(item.f.y);
+            step = sr_step(rng + cur, nullptr, false);
+            // the slot's first item advances its rounding step counter
+            if (row == (D == 2 ? 1 : ny) && x0 == 0 && lane == 0) rng[cur ^ 1] = step + 1u;
+        }
+        int y, a;  // a: coordinate along the wall axis
+        if (D == 2) {
+            y = row;
+            a = row;
+        } else {
+            a = row / ny;
+            y = row - a * ny;
+        }
+        const unsigned rowbase = (unsigned)row * (unsigned)nx;
+        unsigned dym = 0u, dyp = 0u;
+        if (D == 3) {
+            dym = (y == 0) ? (unsigned)(ny - 1) * (unsigned)nx : 0u - (unsigned)nx;
+            dyp = (y == ny - 1) ? 0u - (unsigned)(ny - 1) * (unsigned)nx : (unsigned)nx;
+        }
+        const unsigned dwm = (D == 2) ? 0u - (unsigned)nx : 0u - (unsigned)nx * (unsigned)ny;
+        const bool solid_m = (a == 1), solid_p = (a == Lw - 2);
+        for (int j0 = 0; j0 < segs; j0 += ILP) {
+            R g[ILP][Q];
+            R fxk[ILP], fyk[ILP], fzk[ILP];
+            unsigned cellk[ILP];
+            int bandk[ILP];
+            bool validk[ILP];
+            // pass 1: the band flags and every population load, then the
+            // force density of the band segments
+#pragma unroll
+            for (int k = 0; k < ILP; k++) {
+                const int x = x0 + 32 * (j0 + k) + lane;
+                const bool valid = (j0 + k < segs) && x < nx;
+                validk[k] = valid;
+                const int xv = valid ? x : 0;  // idle lanes read cell 0's sources
+                bandk[k] = (j0 + k < segs) ? flags[(unsigned)row * (unsigned)nseg + (xv >> 5)] : 0;
+                const unsigned cell = rowbase + (unsigned)xv;
+                cellk[k] = cell;
+                const unsigned dxm = (xv == 0) ? (unsigned)(nx - 1) : 0u - 1u;       // c_x = +1
+                const unsigned dxp = (xv == nx - 1) ? 0u - (unsigned)(nx - 1) : 1u;  // c_x = -1
+#pragma unroll
+                for (int i = 0; i < Q; i++) {
+                    const int cx = L::cx(i), cy = L::cy(i);
+                    const int cw = (D == 2) ? cy : L::cz(i);
+                    const bool solid = cw == 0 ? false : (cw > 0 ? solid_m : solid_p);
+                    unsigned off = (cx > 0 ? dxm : (cx < 0 ? dxp : 0u)) +
+                                   (cw > 0 ? dwm : (cw < 0 ? 0u - dwm : 0u));
+                    if (D == 3) off += (cy > 0 ? dym : (cy < 0 ? dyp : 0u));
+                    if (solid)
+                        g[k][i] = T::load(fin, (unsigned)L::opp(i) * nc + cell, R(1));
+                    else
+                        g[k][i] = T::load(fin, (unsigned)i * nc + cell + off, R(1));
                 }
             }
-            const R omega = (R)sd.omega;
-            const CellMoments<Q, R> mo = cell_moments<Q, R>(gv, Fx, Fy, Fz);
-            cell_collide<Q, R>(gv, mo, omega, Fx, Fy, Fz);
-            store_cell<Q, ST, false>(fout, nc, cell, gv, sd.scale,
-                                     ST == ST_FP16 ? sr_seed(step, cell) : 0u);
-            if (WRITE_ALL || band) {
-                mom[cell] = mo.drho;
-                mom[nc + cell] = mo.ux;
-                mom[2 * nc + cell] = mo.uy;
-                if (D == 3) mom[3 * nc + cell] = mo.uz;
+#pragma unroll
+            for (int k = 0; k < ILP; k++) {
+                fxk[k] = R(0);
+                fyk[k] = R(0);
+                fzk[k] = R(0);
+                if (bandk[k] && validk[k]) {
+                    fxk[k] = F[cellk[k]];
+                    fyk[k] = F[nc + cellk[k]];
+                    if (D == 3) fzk[k] = F[2 * nc + cellk[k]];
+                }
             }
-            if (!isfinite(mo.drho)) atomicOr(sd.err, ERR_NONFINITE);
-            if (lane == 0 && band) sd.flags[seg] = 0;
+            // pass 2: collide and store each cell
+#pragma unroll
+            for (int k = 0; k < ILP; k++) {
+                if (!validk[k]) continue;
+                const unsigned cell = cellk[k];
+                const int band = bandk[k];
+                const R Fx = fxk[k], Fy = fyk[k], Fz = fzk[k];
+                if (band) {  // the band buffer is left zero for the next spread
+                    F[cell] = 0;
+                    F[nc + cell] = 0;
+                    if (D == 3) F[2 * nc + cell] = 0;
+                }
+                const CellMoments<Q, R> mo = cell_moments<Q, R>(g[k], Fx, Fy, Fz, ginv);
+                cell_collide<Q, R>(g[k], mo, omega, Fx, Fy, Fz, gsc);
+                store_cell_flat<Q, ST>(fout, nc, cell, g[k],
+                                       ST == ST_FP16 ? sr_seed(step, (long long)cell) : 0u);
+                if (WRITE_ALL || band) {
+                    mom[cell] = mo.drho;
+                    mom[nc + cell] = mo.ux;
+                    mom[2 * nc + cell] = mo.uy;
+                    if (D == 3) mom[3 * nc + cell] = mo.uz;
+                }
+                if (!isfinite(mo.drho)) atomicOr(slots[slot].err, ERR_NONFINITE);
+            }
+            // clear the flags of the segments just read (after every lane of
+            // the warp has read its flag)
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < ILP; k++)
+                if (lane == 0 && j0 + k < segs && bandk[k])
+                    flags[(unsigned)row * (unsigned)nseg + (unsigned)((x0 >> 5) + j0 + k)] = 0;
         }
     }
 }
@@ -153,7 +314,7 @@ __global__ void k_b_face_geometry(const SlotDev* __restrict__ slots,
     if (t >= nfaces) return;
     const int2 fd = faces[t];
     const SlotDev& sd = slots[fd.x];
-    face_records(sd.q, sd.tri, fd.y, sd.entry_pos, sd.entry_rec);
+    face_records(sd.q, sd.tri, fd.y, sd.entry_pos, sd.fp, sd.entry_rec);
 }
 
 __global__ void k_b_node_forces(const SlotDev* __restrict__ slots, const int2* __restrict__ nodes,
@@ -198,7 +359,7 @@ __global__ void k_b_spread(const SlotDev* __restrict__ slots, const int2* __rest
         if (s < S && ok && w != R(0)) {
             const long long cell = row * g.nx + ix;
             for (int k = 0; k < D; k++) atomicAdd(&F[k * g.ncell + cell], ph[k] * w);
-            sd.flags[(cell - sd.fluid_off) >> 5] = 1;
+            sd.flags[row * g.nseg_x + (ix >> 5)] = 1;
         }
     }
 }
@@ -244,15 +405,14 @@ __global__ void k_b_interp(const SlotDev* __restrict__ slots, const int2* __rest
 
 // ------------------------------------------------------------------ launchers
 static void launch_b_sc(int Q, int storage, bool write_all, const SlotDev* slots,
-                        const int2* tiles, int ntiles, int par, unsigned* counter, int grid,
-                        cudaStream_t s)
+                        const BItem* tiles, int ntiles, int par, int grid, cudaStream_t s)
 {
 #define IBLB_BSC(QQ, SS)                                                                       \
     do {                                                                                       \
         if (write_all)                                                                         \
-            k_b_stream_collide<QQ, SS, true><<<grid, BT, 0, s>>>(slots, tiles, ntiles, par, counter); \
+            k_b_stream_collide<QQ, SS, true><<<grid, BT, 0, s>>>(slots, tiles, ntiles, par);   \
         else                                                                                   \
-            k_b_stream_collide<QQ, SS, false><<<grid, BT, 0, s>>>(slots, tiles, ntiles, par, counter); \
+            k_b_stream_collide<QQ, SS, false><<<grid, BT, 0, s>>>(slots, tiles, ntiles, par);  \
     } while (0)
     if (Q == 9) {
         if (storage == ST_FP64) IBLB_BSC(9, ST_FP64);
@@ -264,6 +424,30 @@ static void launch_b_sc(int Q, int storage, bool write_all, const SlotDev* slots
         else IBLB_BSC(19, ST_FP16);
     }
 #undef IBLB_BSC
+}
+
+// Resident blocks per SM of the batched stream-collide instantiation used by
+// (Q, storage): the persistent grid is this times the SM count.
+static int b_sc_blocks_per_sm(int Q, int storage)
+{
+    int n = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+#define IBLB_OCC(QQ, SS) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_b_stream_collide<QQ, SS, false>, BT, 0)
+    if (Q == 9) {
+        if (storage == ST_FP64) IBLB_OCC(9, ST_FP64);
+        else if (storage == ST_FP32) IBLB_OCC(9, ST_FP32);
+        else IBLB_OCC(9, ST_FP16);
+    } else {
+        if (storage == ST_FP64) IBLB_OCC(19, ST_FP64);
+        else if (storage == ST_FP32) IBLB_OCC(19, ST_FP32);
+        else IBLB_OCC(19, ST_FP16);
+    }
+#undef IBLB_OCC
+    if (e != cudaSuccess || n < 1) {
+        (void)cudaGetLastError();
+        n = 4;
+    }
+    return n;
 }
 
 static void launch_b_ib(int dim, int storage, int phase, const SlotDev* slots, const int2* nodes,
@@ -357,11 +541,11 @@ struct Arena {
 };
 
 struct Layout {
-    size_t pop[2], mom, F, flags, err, rng, q, phi, tri, csr, epos, erec, total;
+    size_t pop[2], mom, F, flags, err, rng, q, phi, tri, csr, epos, erec, eref, total;
 };
 
 Layout slot_layout(int Q, int dim, size_t elt, size_t relt, long long ncell, long long nfluid,
-                   int N, int M)
+                   int rowlen, int N, int M, bool elastic)
 {
     Layout L{};
     size_t o = 0;
@@ -374,7 +558,8 @@ Layout slot_layout(int Q, int dim, size_t elt, size_t relt, long long ncell, lon
     L.pop[1] = take((size_t)Q * ncell * elt);
     L.mom = take((size_t)(1 + dim) * ncell * relt);
     L.F = take((size_t)dim * ncell * relt);
-    L.flags = take((size_t)((nfluid + 31) / 32));
+    (void)nfluid;
+    L.flags = take((size_t)(ncell / rowlen) * (size_t)((rowlen + 31) / 32));
     L.err = take(sizeof(int));
     L.rng = take(2 * sizeof(unsigned));
     L.q = take(sizeof(double) * (size_t)N * dim);
@@ -385,6 +570,7 @@ Layout slot_layout(int Q, int dim, size_t elt, size_t relt, long long ncell, lon
         L.epos = take(sizeof(int) * 3 * (size_t)M);
         L.erec = take(sizeof(double) * ENTRY_REC * 3 * (size_t)M);
     }
+    if (elastic) L.eref = take(sizeof(double) * (dim == 3 ? 5 * (size_t)M : (size_t)N));
     L.total = o;
     return L;
 }
@@ -417,19 +603,27 @@ struct iblb_batch_s {
     Arena arena;
     std::vector<Slot> slots;
     SlotDev* d_slots = nullptr;
-    int2* d_tiles = nullptr;
+    BItem* d_tiles = nullptr;  // stream-collide work items
     int2* d_nodes = nullptr;
     int2* d_faces = nullptr;
     size_t cap_tiles = 0, cap_nodes = 0, cap_faces = 0;
     int ntiles = 0, nnodes = 0, nfaces = 0, nactive = 0;
-    unsigned* d_counter = nullptr;
     double* d_partial = nullptr;
     double* d_obs = nullptr;
     int par = 0;
     bool dirty = true;
     int sm_count = 0;
+    int sc_blocks_per_sm = 4;  // resident blocks per SM of the stream-collide kernel
     std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;
     std::map<int, int> tile_cache;  // width bucket -> cells per thread
+    // order-deterministic spreading (when any active slot asks for it)
+    bool det = false;
+    DetSlot* d_detslots = nullptr;
+    size_t cap_detslots = 0;
+    DetBuffers detb{};
+    size_t cap_cnt = 0, cap_start = 0, cap_cur = 0, cap_active = 0, cap_actlist = 0;
+    size_t cap_binof = 0, cap_org = 0, cap_list = 0, cap_wts = 0;
+    int det_nbins = 0, det_ncelltiles = 0;
     std::string msg;
     long long launches = 0;
 };
@@ -468,10 +662,45 @@ cudaError_t ensure(T** p, size_t* cap, size_t n)
     return e;
 }
 
+// Stream-collide work items of one slot (descriptor d, index `slot`): every
+// fluid row (2D: y = 1 .. ny-2; 3D: rows z * ny + y with z = 1 .. nz-2) in
+// pieces of cpt 32-cell segments from x0 = 0.
+void slot_items(const SlotDev& d, int slot, int cpt, std::vector<BItem>& out)
+{
+    const GridParams& g = d.g;
+    const int step = 32 * cpt;
+    const int r0 = g.dim == 2 ? 1 : g.ny;
+    const int r1 = g.dim == 2 ? g.ny - 1 : g.ny * (g.nz - 1);
+    BItem it{};
+    it.f[0] = d.f[0];
+    it.f[1] = d.f[1];
+    it.flags = d.flags;
+    it.F = d.F;
+    it.mom = d.mom;
+    it.slot = slot;
+    it.nx = g.nx;
+    it.ny = g.ny;
+    it.Lw = g.dim == 2 ? g.ny : g.nz;
+    it.nc = (unsigned)g.ncell;
+    it.omega_f = d.omega_f;
+    it.cur_base = d.cur_base;
+    it.scale = d.scale;
+    it.inv_scale = d.inv_scale;
+    it.rng = d.rng;
+    for (int r = r0; r < r1; r++)
+        for (int x0 = 0; x0 < g.nx; x0 += step) {
+            it.row = r;
+            it.x0 = x0;
+            it.segs = std::min(cpt, (g.nx - x0 + 31) / 32);
+            out.push_back(it);
+        }
+}
+
 // Rebuild the slot descriptors and the work lists of the active slots.
 iblb_status rebuild(iblb_batch_s* b)
 {
-    std::vector<int2> tiles, nodes, faces;
+    std::vector<BItem> tiles;
+    std::vector<int2> nodes, faces;
     std::vector<SlotDev> devs(b->slots.size());
     for (size_t s = 0; s < b->slots.size(); s++) {
         Slot& sl = b->slots[s];
@@ -480,8 +709,7 @@ iblb_status rebuild(iblb_batch_s* b)
         sl.dev.cpt = sl.cpt;
         devs[s] = sl.dev;
         if (!sl.active) continue;
-        const long long tile = (long long)BT * sl.cpt;
-        for (long long f0 = 0; f0 < sl.dev.nfluid; f0 += tile) tiles.push_back(make_int2((int)s, (int)f0));
+        slot_items(sl.dev, (int)s, sl.cpt, tiles);
         for (int j = 0; j < sl.dev.N; j++) nodes.push_back(make_int2((int)s, j));
         for (int f = 0; f < (b->dim == 3 ? sl.dev.M : 0); f++) faces.push_back(make_int2((int)s, f));
     }
@@ -493,7 +721,7 @@ iblb_status rebuild(iblb_batch_s* b)
         BCK(b, cudaMemcpy(b->d_slots, devs.data(), sizeof(SlotDev) * devs.size(),
                           cudaMemcpyHostToDevice));
     if (!tiles.empty())
-        BCK(b, cudaMemcpy(b->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice));
+        BCK(b, cudaMemcpy(b->d_tiles, tiles.data(), sizeof(BItem) * tiles.size(), cudaMemcpyHostToDevice));
     if (!nodes.empty())
         BCK(b, cudaMemcpy(b->d_nodes, nodes.data(), sizeof(int2) * nodes.size(), cudaMemcpyHostToDevice));
     if (!faces.empty())
@@ -501,6 +729,49 @@ iblb_status rebuild(iblb_batch_s* b)
     b->ntiles = (int)tiles.size();
     b->nnodes = (int)nodes.size();
     b->nfaces = (int)faces.size();
+    // deterministic spread: bins and cell tiles of the active slots, numbered
+    // globally in slot order
+    b->det = false;
+    for (auto& sl : b->slots)
+        if (sl.active && sl.cfg.deterministic_spread) b->det = true;
+    if (b->det && !nodes.empty()) {
+        std::vector<DetSlot> ds(b->slots.size());
+        int nbins = 0, ncell = 0;
+        for (size_t k = 0; k < b->slots.size(); k++) {
+            const Slot& sl = b->slots[k];
+            if (!sl.active) continue;
+            DetSlot& d = ds[k];
+            d.g = sl.dev.g;
+            det_tiles(d.g, d.nb, d.ct);
+            d.bin_base = nbins;
+            d.cell_base = ncell;
+            nbins += d.nb[0] * d.nb[1] * d.nb[2];
+            ncell += d.ct[0] * d.ct[1] * d.ct[2];
+            d.q = sl.dev.q;
+            d.phi = sl.dev.phi;
+            d.F = sl.dev.F;
+            d.flags = sl.dev.flags;
+            d.flags_by_fluid = 0;
+            d.fluid_off = sl.dev.fluid_off;
+        }
+        const size_t ni = nodes.size();
+        BCK(b, ensure(&b->d_detslots, &b->cap_detslots, ds.size()));
+        BCK(b, ensure(&b->detb.cnt, &b->cap_cnt, (size_t)nbins));
+        BCK(b, ensure(&b->detb.start, &b->cap_start, (size_t)nbins));
+        BCK(b, ensure(&b->detb.cur, &b->cap_cur, (size_t)nbins));
+        BCK(b, ensure(&b->detb.active, &b->cap_active, (size_t)ncell));
+        BCK(b, ensure(&b->detb.act_list, &b->cap_actlist, (size_t)ncell));
+        BCK(b, ensure(&b->detb.bin_of, &b->cap_binof, ni));
+        BCK(b, ensure(&b->detb.org, &b->cap_org, 3 * ni));
+        BCK(b, ensure(&b->detb.list, &b->cap_list, ni));
+        double* w = (double*)b->detb.wts;  // FP64 room serves both precisions
+        BCK(b, ensure(&w, &b->cap_wts, 12 * ni));
+        b->detb.wts = w;
+        if (!b->detb.nact) BCK(b, cudaMalloc(&b->detb.nact, sizeof(int)));
+        BCK(b, cudaMemcpy(b->d_detslots, ds.data(), sizeof(DetSlot) * ds.size(), cudaMemcpyHostToDevice));
+        b->det_nbins = nbins;
+        b->det_ncelltiles = ncell;
+    }
     int na = 0;
     for (auto& sl : b->slots) na += sl.active ? 1 : 0;
     b->nactive = na;
@@ -512,7 +783,18 @@ iblb_status rebuild(iblb_batch_s* b)
 int kernels_per_step(const iblb_batch_s* b)
 {
     if (b->nnodes == 0) return 1;
-    return (b->dim == 3 ? 2 : 1) + 3;
+    return (b->dim == 3 ? 2 : 1) + 2 + (b->det ? DET_KERNELS : 1);
+}
+
+// A2/A3 over all active slots: atomics, or the ordered gather.
+void enqueue_spread(iblb_batch_s* b, cudaStream_t s)
+{
+    if (b->det)
+        launch_spread_det(b->storage, b->dim, b->d_detslots, b->d_nodes, b->nnodes, b->detb,
+                          b->det_nbins, b->det_ncelltiles, b->sm_count, s);
+    else
+        launch_b_ib(b->dim, b->storage, 1, b->d_slots, b->d_nodes, b->nnodes, b->d_faces,
+                    b->nfaces, s);
 }
 
 // One batched step at parity `par` (all phases over all active slots).
@@ -521,13 +803,10 @@ void enqueue_step(iblb_batch_s* b, cudaStream_t s, int par, bool write_all)
     if (b->nnodes > 0) {
         launch_b_ib(b->dim, b->storage, 0, b->d_slots, b->d_nodes, b->nnodes, b->d_faces,
                     b->nfaces, s);
-        launch_b_ib(b->dim, b->storage, 1, b->d_slots, b->d_nodes, b->nnodes, b->d_faces,
-                    b->nfaces, s);
+        enqueue_spread(b, s);
     }
-    cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned), s);
-    const int grid = std::max(1, std::min(b->ntiles, b->sm_count * 16));
-    launch_b_sc(b->Q, b->storage, write_all, b->d_slots, b->d_tiles, b->ntiles, par, b->d_counter,
-                grid, s);
+    const int grid = std::max(1, std::min(b->ntiles, b->sm_count * b->sc_blocks_per_sm));
+    launch_b_sc(b->Q, b->storage, write_all, b->d_slots, b->d_tiles, b->ntiles, par, grid, s);
     if (b->nnodes > 0)
         launch_b_ib(b->dim, b->storage, 2, b->d_slots, b->d_nodes, b->nnodes, b->d_faces,
                     b->nfaces, s);
@@ -583,35 +862,36 @@ iblb_status tune_slot(iblb_batch_s* b, int s)
         return IBLB_OK;
     }
     SlotDev* d_one = nullptr;
-    int2* d_t = nullptr;
-    unsigned* d_c = nullptr;
-    const long long maxt = (sl.dev.nfluid + BT - 1) / BT;
+    BItem* d_t = nullptr;
+    std::vector<BItem> probe;
+    {
+        SlotDev d = sl.dev;
+        d.cur_base = sl.buf;
+        slot_items(d, 0, b_ilp(b->Q, b->storage), probe);
+    }
+    const long long maxt = (long long)probe.size();
     BCK(b, cudaMalloc(&d_one, sizeof(SlotDev)));
-    BCK(b, cudaMalloc(&d_t, sizeof(int2) * (size_t)maxt));
-    BCK(b, cudaMalloc(&d_c, sizeof(unsigned)));
+    BCK(b, cudaMalloc(&d_t, sizeof(BItem) * (size_t)maxt));
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    int pick = 1;
+    int pick = 4 * b_ilp(b->Q, b->storage);
     const int trials = 5;
-    for (int cpt : {1, 2, 4}) {
+    const int ilp = b_ilp(b->Q, b->storage);
+    for (int cpt : {2 * ilp, 4 * ilp, 8 * ilp}) {
         SlotDev d = sl.dev;
         d.cpt = cpt;
         d.cur_base = sl.buf;
-        std::vector<int2> tl;
-        for (long long f0 = 0; f0 < d.nfluid; f0 += (long long)BT * cpt) tl.push_back(make_int2(0, (int)f0));
+        std::vector<BItem> tl;
+        slot_items(d, 0, cpt, tl);
         cudaMemcpy(d_one, &d, sizeof(SlotDev), cudaMemcpyHostToDevice);
-        cudaMemcpy(d_t, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice);
-        const int grid = std::max(1, std::min((int)tl.size(), b->sm_count * 16));
-        cudaMemsetAsync(d_c, 0, sizeof(unsigned), b->stream);
-        launch_b_sc(b->Q, b->storage, false, d_one, d_t, (int)tl.size(), 0, d_c, grid, b->stream);
+        cudaMemcpy(d_t, tl.data(), sizeof(BItem) * tl.size(), cudaMemcpyHostToDevice);
+        const int grid = std::max(1, std::min((int)tl.size(), b->sm_count * b->sc_blocks_per_sm));
+        launch_b_sc(b->Q, b->storage, false, d_one, d_t, (int)tl.size(), 0, grid, b->stream);
         cudaEventRecord(e0, b->stream);
-        for (int t = 0; t < trials; t++) {
-            cudaMemsetAsync(d_c, 0, sizeof(unsigned), b->stream);
-            launch_b_sc(b->Q, b->storage, false, d_one, d_t, (int)tl.size(), 0, d_c, grid,
-                        b->stream);
-        }
+        for (int t = 0; t < trials; t++)
+            launch_b_sc(b->Q, b->storage, false, d_one, d_t, (int)tl.size(), 0, grid, b->stream);
         cudaEventRecord(e1, b->stream);
         b->launches += trials + 1;
         add_launches(trials + 1);
@@ -627,7 +907,6 @@ iblb_status tune_slot(iblb_batch_s* b, int s)
     cudaEventDestroy(e1);
     cudaFree(d_one);
     cudaFree(d_t);
-    cudaFree(d_c);
     BCK(b, cudaGetLastError());
     sl.cpt = pick;
     b->tile_cache[key] = pick;
@@ -644,10 +923,15 @@ iblb_status check_cfg(const iblb_batch_s* b, const iblb_config& c)
     if ((dim == 2 ? c.ny : nz) < 3) return IBLB_EINVAL;
     if (!(c.tau > 0.5)) return IBLB_EINVAL;
     if (c.wetting && (!(c.xi > 0.0) || !(c.pi_n > c.pi_m) || c.pi_m < 2)) return IBLB_EINVAL;
+    // the stream-collide kernel indexes a slot's populations with 32 bits
+    if ((double)c.lattice * c.nx * c.ny * nz >= 4294967296.0) return IBLB_EINVAL;
     if (c.body_force[0] != 0.0 || c.body_force[1] != 0.0 || c.body_force[2] != 0.0)
         return IBLB_EINVAL;  // the batched kernel has no body force
     if (c.tau_out != 0.0 && c.tau_out != c.tau)
         return IBLB_EINVAL;  // nor a viscosity ratio
+    if (!(c.shear_modulus >= 0.0) || !std::isfinite(c.shear_modulus) || !(c.skalak_c > -0.5) ||
+        !std::isfinite(c.skalak_c))
+        return IBLB_EINVAL;
     for (int k = 0; k < 3; k++)
         if (c.wall_u_lo[k] != 0.0 || c.wall_u_hi[k] != 0.0)
             return IBLB_EINVAL;  // nor moving walls
@@ -668,7 +952,8 @@ size_t iblb_batch_footprint(const iblb_config* c, int n_nodes, int n_faces)
     const long long ncell = (long long)c->nx * c->ny * nz;
     const long long nfluid = dim == 2 ? (long long)c->nx * (c->ny - 2)
                                       : (long long)c->nx * c->ny * (nz - 2);
-    return slot_layout(c->lattice, dim, elt, relt, ncell, nfluid, n_nodes, n_faces).total;
+    return slot_layout(c->lattice, dim, elt, relt, ncell, nfluid, c->nx, n_nodes, n_faces,
+                       c->shear_modulus != 0.0).total;
 }
 
 iblb_status iblb_batch_create(int lattice, int storage, size_t hbm_budget_bytes, int max_slots,
@@ -691,10 +976,10 @@ iblb_status iblb_batch_create(int lattice, int storage, size_t hbm_budget_bytes,
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) b->sc_blocks_per_sm = b_sc_blocks_per_sm(lattice, storage);
     const size_t budget = hbm_budget_bytes / ALIGN * ALIGN;
     if (e == cudaSuccess) e = cudaMalloc(&b->arena_ptr, budget);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_slots, sizeof(SlotDev) * max_slots);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_partial, sizeof(double) * 1024);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_obs, sizeof(double) * 12);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
@@ -717,7 +1002,17 @@ void iblb_batch_destroy(iblb_batch b)
     cudaFree(b->d_tiles);
     cudaFree(b->d_nodes);
     cudaFree(b->d_faces);
-    cudaFree(b->d_counter);
+    cudaFree(b->d_detslots);
+    cudaFree(b->detb.cnt);
+    cudaFree(b->detb.start);
+    cudaFree(b->detb.cur);
+    cudaFree(b->detb.active);
+    cudaFree(b->detb.act_list);
+    cudaFree(b->detb.nact);
+    cudaFree(b->detb.bin_of);
+    cudaFree(b->detb.org);
+    cudaFree(b->detb.list);
+    cudaFree(b->detb.wts);
     cudaFree(b->d_partial);
     cudaFree(b->d_obs);
     if (b->cap) cudaStreamDestroy(b->cap);
@@ -774,8 +1069,9 @@ iblb_status iblb_batch_admit(iblb_batch b, const iblb_config* cfg, const double*
     g.ncell = (long long)cfg->nx * cfg->ny * nz;
     const long long nfluid = dim == 2 ? (long long)cfg->nx * (cfg->ny - 2)
                                       : (long long)cfg->nx * cfg->ny * (nz - 2);
-    const Layout L = slot_layout(b->Q, dim, b->elt, b->relt, g.ncell, nfluid, n_nodes,
-                                 dim == 3 ? n_faces : 0);
+    const bool elastic = cfg->shear_modulus != 0.0;
+    const Layout L = slot_layout(b->Q, dim, b->elt, b->relt, g.ncell, nfluid, cfg->nx, n_nodes,
+                                 dim == 3 ? n_faces : 0, elastic);
     size_t off = 0;
     if (!b->arena.alloc(L.total, &off)) return bfail(b, IBLB_EAGAIN, "no room in the HBM budget");
     Slot& sl = b->slots[s];
@@ -798,6 +1094,8 @@ iblb_status iblb_batch_admit(iblb_batch b, const iblb_config* cfg, const double*
     d.g = g;
     d.nfluid = nfluid;
     d.fluid_off = dim == 2 ? (long long)cfg->nx : (long long)cfg->nx * cfg->ny;
+    d.div_nx = make_fastdiv((unsigned)cfg->nx);
+    d.div_ny = make_fastdiv((unsigned)cfg->ny);
     d.omega = 1.0 / cfg->tau;
     d.omega_f = (float)d.omega;
     const int sexp = cfg->fp16_scale_exp ? cfg->fp16_scale_exp : 16;
@@ -814,6 +1112,9 @@ iblb_status iblb_batch_admit(iblb_batch b, const iblb_config* cfg, const double*
     d.fp.wetting = cfg->wetting ? 1 : 0;
     d.fp.A = cfg->wetting ? wetting_A(*cfg) : 0.0;
     d.fp.wall_plane = 0.5;
+    d.fp.Gs = cfg->shear_modulus;
+    d.fp.Cs = cfg->skalak_c;
+    d.fp.eref = elastic ? (const double*)(base + L.eref) : nullptr;
     if (dim == 3) {
         d.tri = (int*)(base + L.tri);
         d.csr_ptr = (int*)(base + L.csr);
@@ -836,6 +1137,12 @@ iblb_status iblb_batch_admit(iblb_batch b, const iblb_config* cfg, const double*
         launch_init_moments(b->storage, g, d.mom, b->stream);
         b->launches++;
         add_launches(1);
+        if (elastic) {  // the interface as admitted is the elastic reference shape
+            launch_elastic_reference(dim, d.q, n_nodes, dim == 3 ? n_faces : 0, d.tri,
+                                     (double*)(base + L.eref), b->stream);
+            b->launches++;
+            add_launches(1);
+        }
         e = cudaStreamSynchronize(b->stream);
     }
     if (e != cudaSuccess) {
@@ -851,15 +1158,41 @@ iblb_status iblb_batch_admit(iblb_batch b, const iblb_config* cfg, const double*
     return IBLB_OK;
 }
 
-iblb_status iblb_batch_run(iblb_batch b, int max_steps, int* n_completed)
+}  // extern "C"
+
+namespace {
+
+// Algorithmic HBM bytes of one batched stream-collide launch over the active
+// slots: populations read once and written once per fluid cell.
+double active_stream_bytes(const iblb_batch_s* b)
 {
-    if (!b || max_steps < 0) return IBLB_EINVAL;
+    double t = 0.0;
+    for (const auto& sl : b->slots)
+        if (sl.active) t += 2.0 * b->Q * (double)b->elt * (double)sl.dev.nfluid;
+    return t;
+}
+
+// Advance every active slot by up to max_steps steps.  Without `kernel_ms`
+// the steps run as CUDA-graph chunks; with it, one launch at a time with a
+// CUDA event pair around each phase (forces, spread, stream-collide,
+// interpolate + advect), summed into kernel_ms, and the algorithmic bytes of
+// the stream-collide launches summed into *sc_bytes.
+iblb_status batch_run(iblb_batch_s* b, int max_steps, int* n_completed, double* kernel_ms,
+                      double* sc_bytes)
+{
     int completed = 0;
     int left = max_steps;
-    while (left > 0) {
+    cudaEvent_t ev[IBLB_K_COUNT + 1] = {};
+    if (kernel_ms) {
+        for (int k = 0; k < IBLB_K_COUNT; k++) kernel_ms[k] = 0.0;
+        if (sc_bytes) *sc_bytes = 0.0;
+        for (auto& e : ev) BCK(b, cudaEventCreate(&e));
+    }
+    iblb_status st = IBLB_OK;
+    while (left > 0 && st == IBLB_OK) {
         if (b->dirty) {
-            iblb_status st = rebuild(b);
-            if (st != IBLB_OK) return st;
+            st = rebuild(b);
+            if (st != IBLB_OK) break;
         }
         if (b->nactive == 0) break;
         long long r = left;
@@ -867,18 +1200,60 @@ iblb_status iblb_batch_run(iblb_batch b, int max_steps, int* n_completed)
             if (sl.active) r = std::min(r, sl.steps_total - sl.steps_done);
         int seg = (int)r;
         // segment of `seg` steps, the last one writing every cell's moments
-        int done_here = 0;
-        while (done_here < seg) {
-            const int k = std::min(32, seg - done_here);
-            const bool last = (done_here + k == seg);
-            cudaGraphExec_t ge;
-            iblb_status st = get_graph(b, k, last, &ge);
-            if (st != IBLB_OK) return st;
-            BCK(b, cudaGraphLaunch(ge, b->stream));
-            b->launches += (long long)k * kernels_per_step(b);
-            add_launches((long long)k * kernels_per_step(b));
-            b->par ^= (k & 1);
-            done_here += k;
+        if (!kernel_ms) {
+            int done_here = 0;
+            while (done_here < seg) {
+                const int k = std::min(32, seg - done_here);
+                const bool last = (done_here + k == seg);
+                cudaGraphExec_t ge;
+                st = get_graph(b, k, last, &ge);
+                if (st != IBLB_OK) break;
+                cudaError_t e = cudaGraphLaunch(ge, b->stream);
+                if (e != cudaSuccess) {
+                    st = bfail(b, IBLB_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+                    break;
+                }
+                b->launches += (long long)k * kernels_per_step(b);
+                add_launches((long long)k * kernels_per_step(b));
+                b->par ^= (k & 1);
+                done_here += k;
+            }
+            if (st != IBLB_OK) break;
+        } else {
+            const double bytes = active_stream_bytes(b);
+            const int grid = std::max(1, std::min(b->ntiles, b->sm_count * b->sc_blocks_per_sm));
+            for (int k = 0; k < seg; k++) {
+                const bool last = (k == seg - 1);
+                cudaEventRecord(ev[0], b->stream);
+                if (b->nnodes > 0)
+                    launch_b_ib(b->dim, b->storage, 0, b->d_slots, b->d_nodes, b->nnodes,
+                                b->d_faces, b->nfaces, b->stream);
+                cudaEventRecord(ev[1], b->stream);
+                if (b->nnodes > 0) enqueue_spread(b, b->stream);
+                cudaEventRecord(ev[2], b->stream);
+                launch_b_sc(b->Q, b->storage, last, b->d_slots, b->d_tiles, b->ntiles, b->par,
+                            grid, b->stream);
+                cudaEventRecord(ev[3], b->stream);
+                if (b->nnodes > 0)
+                    launch_b_ib(b->dim, b->storage, 2, b->d_slots, b->d_nodes, b->nnodes,
+                                b->d_faces, b->nfaces, b->stream);
+                cudaEventRecord(ev[4], b->stream);
+                b->par ^= 1;
+                b->launches += kernels_per_step(b);
+                add_launches(kernels_per_step(b));
+                cudaError_t e = cudaEventSynchronize(ev[4]);
+                if (e != cudaSuccess) {
+                    st = bfail(b, IBLB_ECUDA, std::string("profiled step: ") + cudaGetErrorString(e));
+                    break;
+                }
+                for (int q = 0; q < IBLB_K_COUNT; q++) {
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, ev[q], ev[q + 1]);
+                    kernel_ms[q] += ms;
+                }
+                if (sc_bytes) *sc_bytes += bytes;
+            }
+            if (st != IBLB_OK) break;
         }
         for (auto& sl : b->slots) {
             if (!sl.active) continue;
@@ -893,9 +1268,30 @@ iblb_status iblb_batch_run(iblb_batch b, int max_steps, int* n_completed)
         }
         left -= seg;
     }
+    if (kernel_ms)
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
     if (n_completed) *n_completed = completed;
+    if (st != IBLB_OK) return st;
     BCK(b, cudaGetLastError());
     return IBLB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+iblb_status iblb_batch_run(iblb_batch b, int max_steps, int* n_completed)
+{
+    if (!b || max_steps < 0) return IBLB_EINVAL;
+    return batch_run(b, max_steps, n_completed, nullptr, nullptr);
+}
+
+iblb_status iblb_batch_run_profiled(iblb_batch b, int max_steps, int* n_completed,
+                                    double* kernel_ms, double* stream_collide_bytes)
+{
+    if (!b || max_steps < 0 || !kernel_ms) return IBLB_EINVAL;
+    return batch_run(b, max_steps, n_completed, kernel_ms, stream_collide_bytes);
 }
 
 iblb_status iblb_batch_sync(iblb_batch b)
@@ -1017,6 +1413,18 @@ iblb_status iblb_batch_stats(iblb_batch b, iblb_batch_info* info)
     info->free_bytes = b->arena.free_bytes();
     info->kernel_launches = b->launches;
     return IBLB_OK;
+}
+
+long long iblb_batch_steps_to_next_completion(iblb_batch b)
+{
+    if (!b) return -1;
+    long long r = -1;
+    for (const auto& sl : b->slots)
+        if (sl.active) {
+            const long long left = sl.steps_total - sl.steps_done;
+            if (r < 0 || left < r) r = left;
+        }
+    return r;
 }
 
 int iblb_batch_slot_tile(iblb_batch b, int slot)

@@ -104,16 +104,24 @@ struct ForceParams {
     int n, m;              // exponents of Pi
     int wetting;
     double wall_plane;     // 0.5
+    // elastic interface (Skalak): shear modulus, area-dilation parameter and
+    // the reference data of the interface as set (null when Gs = 0):
+    // 3D [M][5] = inverse reference edge matrix (4) and reference area per
+    // face; 2D [N] = reference length per segment
+    double Gs, Cs;
+    const double* eref;
 };
 
 // Launch shape of the stream-collide kernel (chosen by the autotuner).
 struct Tuning {
-    int variant = 1;            // 0: plain kernel; 1: pipelined kernel; 2: cell pairs (where the shape allows)
+    int variant = 1;            // 0: plain kernel; 1: pipelined kernel; 2: cell pairs along x;
+                                // 3: row pairs (where the shape allows)
     int block_x = 128;          // plain kernel: threads per block along x (64, 128, 256)
     int streaming_stores = 0;   // plain kernel: evict-first stores of the new populations
     int rows_per_tile = 2;      // pipelined kernel, rows mode: rows per tile
     int ctas_per_sm = 2;        // pipelined kernel: resident CTAs per SM (1 or 2)
     int consumer_warps = 8;     // pipelined kernel: 8 (2 CTAs/SM), 16 or 24 (1 CTA/SM)
+    long long wait_limit = 0;   // pipelined kernel: clock cycles a wait may take (0: ~2 s)
 };
 
 // Shape of the pipelined stream-collide launch (see lbm_pipe.cu).
@@ -133,6 +141,7 @@ struct PipeShape {
     int consumer_warps;    // consumer warps per CTA (8, 16 or 24)
     int smem_bytes;        // dynamic shared memory per CTA
     int grid;              // persistent CTAs
+    long long wait_limit;  // clock cycles a pipeline wait may take before it gives up
 };
 // Shared-memory limits of the device (bytes), read at creation.
 struct SmemLimits {
@@ -158,6 +167,13 @@ bool pair_kernel_ok(int storage, const GridParams& g);
 void launch_stream_collide_pairs(int Q, int storage, bool write_all, const void* fin, void* fout,
                                  void* moments, void* F, uint8_t* flags, const StreamParams& p,
                                  const Tuning& tu, cudaStream_t s);
+
+// Row-pair variant (lbm.cu): two y-adjacent cells per thread, packed FP32x2
+// arithmetic; D3Q19 with FP32 / binary16 storage.
+bool rowpair_kernel_ok(int Q, int storage, const GridParams& g);
+void launch_stream_collide_rowpairs(int storage, bool write_all, const void* fin, void* fout,
+                                    void* moments, void* F, uint8_t* flags, const StreamParams& p,
+                                    const Tuning& tu, cudaStream_t s);
 
 // Pipelined variant (lbm_pipe.cu): usable when pipe_shape() returns true.
 bool pipe_shape(int Q, int storage, const GridParams& g, int sm_count, const SmemLimits& lim,
@@ -204,6 +220,11 @@ void launch_spread(int storage, int dim, const double* q, const double* phi, int
 // qdot [N][dim] = sum u Delta; if advect, q += qdot.
 void launch_interp(int storage, int dim, double* q, const void* moments, int N, double* qdot,
                    bool advect, const GridParams& g, cudaStream_t s);
+
+// Elastic reference of the interface at its current positions (see
+// ForceParams::eref).
+void launch_elastic_reference(int dim, const double* q, int N, int M, const int* tri, double* eref,
+                              cudaStream_t s);
 
 // Observables (single block, deterministic).  out: 12 doubles, layout of iblb_obs.
 void launch_observables(int dim, const double* q, int N, const int* tri, int M,

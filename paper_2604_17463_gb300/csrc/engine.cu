@@ -18,6 +18,7 @@
 
 #include "../../include/iblb.h"
 #include "common.cuh"
+#include "spread_det.cuh"
 
 using namespace iblb;
 
@@ -65,11 +66,18 @@ struct iblb_sim {
     int* entry_pos = nullptr;    // CSR position of each (face, corner) (3D)
     double* entry_rec = nullptr; // per-(face, corner) geometry records in CSR order (3D)
     double* defo = nullptr;      // deformation output [8]
+    double* eref = nullptr;      // elastic reference of the interface (shear_modulus != 0)
     unsigned* rng = nullptr;     // two-entry step counter (binary16 stochastic rounding)
     bool moving = false;         // walls with a tangential velocity
     int* col_cnt = nullptr;      // viscosity ratio: crossings per lattice column
     double* col_z = nullptr;     // [column][COL_MAX] crossing heights
     bool two_tau = false;
+    // order-deterministic spreading (cfg.deterministic_spread)
+    bool det = false;
+    DetBuffers detb{};
+    DetSlot* d_detslot = nullptr;
+    DetSlot det_host{};
+    int det_nbins = 0, det_ncelltiles = 0;
     std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;  // (parity, steps, last)
     std::string msg;
 };
@@ -107,9 +115,22 @@ void clear_graphs(iblb_sim* h)
 }
 
 int force_kernels(const iblb_sim* h) { return h->dim == 3 ? 2 : 1; }
+int spread_kernels(const iblb_sim* h) { return h->det ? DET_KERNELS : 1; }
 int kernels_per_step(const iblb_sim* h)
 {
-    return (h->N > 0 ? 3 + force_kernels(h) : 1) + ((h->two_tau && h->N > 0) ? 1 : 0);
+    return (h->N > 0 ? 2 + force_kernels(h) + spread_kernels(h) : 1) +
+           ((h->two_tau && h->N > 0) ? 1 : 0);
+}
+
+// A2/A3: spread the nodal forces, with atomics or (deterministic_spread)
+// as an ordered gather.
+void enqueue_spread(iblb_sim* h, cudaStream_t s)
+{
+    if (h->det)
+        launch_spread_det(h->storage, h->dim, h->d_detslot, nullptr, h->N, h->detb, h->det_nbins,
+                          h->det_ncelltiles, h->sm_count, s);
+    else
+        launch_spread(h->storage, h->dim, h->q, h->phi, h->N, h->F, h->flags, h->g, s);
 }
 
 void enqueue_classify(iblb_sim* h, cudaStream_t s)
@@ -134,6 +155,11 @@ cudaError_t launch_sc(iblb_sim* h, cudaStream_t s, bool write_all)
                                     h->mom, h->F, h->flags, sp, h->tune, s);
         return cudaPeekAtLastError();
     }
+    if (h->tune.variant == 3 && rowpair_kernel_ok(h->Q, h->storage, h->g)) {
+        launch_stream_collide_rowpairs(h->storage, write_all, h->f[h->cur], h->f[h->cur ^ 1],
+                                       h->mom, h->F, h->flags, sp, h->tune, s);
+        return cudaPeekAtLastError();
+    }
     if (h->tune.variant == 1 && h->pipe_ok)
         return launch_stream_collide_pipe(h->Q, h->storage, write_all, h->f[h->cur],
                                           h->f[h->cur ^ 1], h->mom, h->F, h->flags, sp,
@@ -149,7 +175,7 @@ void enqueue_step(iblb_sim* h, cudaStream_t s, bool write_all)
     if (h->N > 0) {
         launch_forces(h->dim, h->q, h->N, h->M, h->tri, h->csr_ptr, h->entry_pos, h->entry_rec, h->fp, h->phi, nullptr,
                       nullptr, h->err, s);
-        launch_spread(h->storage, h->dim, h->q, h->phi, h->N, h->F, h->flags, h->g, s);
+        enqueue_spread(h, s);
     }
     enqueue_classify(h, s);
     launch_sc(h, s, write_all);
@@ -209,6 +235,7 @@ bool apply_tuning(iblb_sim* h, const Tuning& t)
     h->tune = t;
     h->pipe_ok = pipe_shape(h->Q, h->storage, h->g, h->sm_count, h->smem, t.rows_per_tile,
                             t.ctas_per_sm, t.consumer_warps, h->pipe);
+    if (t.wait_limit > 0) h->pipe.wait_limit = t.wait_limit;
     return h->pipe_ok;
 }
 
@@ -256,9 +283,12 @@ iblb_status iblb_create(const iblb_config* cfg, void* cuda_stream, iblb_handle* 
     if (dim == 3 && (c.ny > 65535 || nz > 65535)) return IBLB_EINVAL;
     if (dim == 2 && c.ny > 65535) return IBLB_EINVAL;
     if (c.fp16_scale_exp < 0 || c.fp16_scale_exp > 24) return IBLB_EINVAL;
-    // binary16 stream-collide indexes cells with 32 bits
-    if (c.storage == IBLB_FP16_DEV && (double)c.nx * c.ny * nz >= 4294967296.0) return IBLB_EINVAL;
+    // the stream-collide kernels index cells with 32 bits
+    if ((double)c.nx * c.ny * nz >= 4294967296.0) return IBLB_EINVAL;
     if (c.tau_out != 0.0 && (!(c.tau_out > 0.5) || !std::isfinite(c.tau_out))) return IBLB_EINVAL;
+    if (!(c.shear_modulus >= 0.0) || !std::isfinite(c.shear_modulus) || !(c.skalak_c > -0.5) ||
+        !std::isfinite(c.skalak_c))
+        return IBLB_EINVAL;
     {
         const int wax = c.lattice == 9 ? 1 : 2;
         bool mv = false;
@@ -317,6 +347,9 @@ iblb_status iblb_create(const iblb_config* cfg, void* cuda_stream, iblb_handle* 
     fp.wetting = c.wetting ? 1 : 0;
     fp.A = c.wetting ? wetting_amplitude(c) : 0.0;
     fp.wall_plane = 0.5;
+    fp.Gs = c.shear_modulus;
+    fp.Cs = c.skalak_c;
+    fp.eref = nullptr;  // set with the interface
 
     auto bail = [&](cudaError_t e, const char* where) {
         iblb_destroy(h);
@@ -348,6 +381,29 @@ iblb_status iblb_create(const iblb_config* cfg, void* cuda_stream, iblb_handle* 
         cudaMemsetAsync(h->col_cnt, 0, sizeof(int) * ncol, h->stream);
         sp.col_cnt = h->col_cnt;
         sp.col_z = h->col_z;
+    }
+    if (c.deterministic_spread) {
+        h->det = true;
+        DetSlot ds{};
+        ds.g = g;
+        det_tiles(g, ds.nb, ds.ct);
+        h->det_nbins = ds.nb[0] * ds.nb[1] * ds.nb[2];
+        h->det_ncelltiles = ds.ct[0] * ds.ct[1] * ds.ct[2];
+        ds.F = h->F;
+        ds.flags = h->flags;
+        ds.flags_by_fluid = 0;
+        const size_t nbn = (size_t)h->det_nbins, nct = (size_t)h->det_ncelltiles;
+        if ((e = cudaMalloc(&h->detb.cnt, sizeof(int) * nbn)) != cudaSuccess ||
+            (e = cudaMalloc(&h->detb.start, sizeof(int) * nbn)) != cudaSuccess ||
+            (e = cudaMalloc(&h->detb.cur, sizeof(int) * nbn)) != cudaSuccess ||
+            (e = cudaMalloc(&h->detb.active, sizeof(int) * nct)) != cudaSuccess ||
+            (e = cudaMalloc(&h->detb.act_list, sizeof(int2) * nct)) != cudaSuccess ||
+            (e = cudaMalloc(&h->detb.nact, sizeof(int))) != cudaSuccess ||
+            (e = cudaMalloc(&h->d_detslot, sizeof(DetSlot))) != cudaSuccess)
+            return bail(e, "deterministic spread");
+        h->det_host = ds;
+        if ((e = cudaMemcpy(h->d_detslot, &ds, sizeof(DetSlot), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return bail(e, "deterministic spread");
     }
     if ((e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking)) != cudaSuccess)
         return bail(e, "stream");
@@ -400,6 +456,18 @@ void iblb_destroy(iblb_handle h)
     free_dev(h->col_z);
     free_dev(h->defo);
     free_dev(h->rng);
+    free_dev(h->detb.bin_of);
+    free_dev(h->detb.org);
+    free_dev(h->detb.wts);
+    free_dev(h->detb.cnt);
+    free_dev(h->detb.start);
+    free_dev(h->detb.cur);
+    free_dev(h->detb.list);
+    free_dev(h->detb.active);
+    free_dev(h->detb.act_list);
+    free_dev(h->detb.nact);
+    free_dev(h->d_detslot);
+    free_dev(h->eref);
     if (h->cap) cudaStreamDestroy(h->cap);
     delete h;
 }
@@ -445,6 +513,12 @@ iblb_status iblb_set_interface(iblb_handle h, const double* xyz, int n_nodes, co
     free_dev(h->csr_ptr);
     free_dev(h->entry_pos);
     free_dev(h->entry_rec);
+    free_dev(h->detb.bin_of);
+    free_dev(h->detb.org);
+    free_dev(h->detb.wts);
+    free_dev(h->detb.list);
+    free_dev(h->eref);
+    h->fp.eref = nullptr;
     h->N = n_nodes;
     h->M = dim == 2 ? n_nodes : n_faces;
     if (n_nodes == 0) return IBLB_OK;
@@ -452,6 +526,16 @@ iblb_status iblb_set_interface(iblb_handle h, const double* xyz, int n_nodes, co
     CK(h, cudaMalloc(&h->q, qb));
     CK(h, cudaMalloc(&h->phi, qb));
     CK(h, cudaMemcpyAsync(h->q, xyz, qb, cudaMemcpyHostToDevice, h->stream));
+    if (h->det) {
+        CK(h, cudaMalloc(&h->detb.bin_of, sizeof(int) * n_nodes));
+        CK(h, cudaMalloc(&h->detb.org, sizeof(int) * 3 * (size_t)n_nodes));
+        CK(h, cudaMalloc(&h->detb.wts, h->relt * 12 * (size_t)n_nodes));
+        CK(h, cudaMalloc(&h->detb.list, sizeof(int) * n_nodes));
+        h->det_host.q = h->q;
+        h->det_host.phi = h->phi;
+        CK(h, cudaMemcpyAsync(h->d_detslot, &h->det_host, sizeof(DetSlot), cudaMemcpyHostToDevice,
+                              h->stream));
+    }
     if (dim == 3) {
         CK(h, cudaMalloc(&h->tri, sizeof(int) * 3 * (size_t)n_faces));
         CK(h, cudaMalloc(&h->csr_ptr, sizeof(int) * (n_nodes + 1)));
@@ -463,6 +547,14 @@ iblb_status iblb_set_interface(iblb_handle h, const double* xyz, int n_nodes, co
                               cudaMemcpyHostToDevice, h->stream));
         CK(h, cudaMemcpyAsync(h->entry_pos, ent.data(), sizeof(int) * ent.size(),
                               cudaMemcpyHostToDevice, h->stream));
+    }
+    if (h->fp.Gs != 0.0) {
+        // the interface as set is the elastic reference shape
+        CK(h, cudaMalloc(&h->eref, sizeof(double) * (dim == 3 ? 5 * (size_t)n_faces : (size_t)n_nodes)));
+        launch_elastic_reference(dim, h->q, n_nodes, n_faces, h->tri, h->eref, h->stream);
+        g_launches++;
+        CK(h, cudaGetLastError());
+        h->fp.eref = h->eref;
     }
     CK(h, cudaStreamSynchronize(h->stream));
     return IBLB_OK;
@@ -484,6 +576,15 @@ iblb_status iblb_step(iblb_handle h, int n_steps)
         h->cur ^= (k & 1);
         left -= k;
     }
+    return IBLB_OK;
+}
+
+iblb_status iblb_clear_faults(iblb_handle h)
+{
+    if (!h) return IBLB_EINVAL;
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMemsetAsync(h->err, 0, sizeof(int), h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
     return IBLB_OK;
 }
 
@@ -617,8 +718,8 @@ iblb_status iblb_force_field(iblb_handle h, double* F)
     if (h->N > 0) {
         launch_forces(h->dim, h->q, h->N, h->M, h->tri, h->csr_ptr, h->entry_pos, h->entry_rec, h->fp, h->phi, nullptr,
                       nullptr, h->err, h->stream);
-        launch_spread(h->storage, h->dim, h->q, h->phi, h->N, h->F, h->flags, h->g, h->stream);
-        g_launches += force_kernels(h) + 1;
+        enqueue_spread(h, h->stream);
+        g_launches += force_kernels(h) + spread_kernels(h);
     }
     launch_unpack_force(h->storage, h->g, h->F, h->sp.body, tmp, h->stream);
     g_launches++;
@@ -747,7 +848,7 @@ iblb_status iblb_step_profiled(iblb_handle h, int n_steps, double* kernel_ms)
             launch_forces(h->dim, h->q, h->N, h->M, h->tri, h->csr_ptr, h->entry_pos, h->entry_rec, h->fp, h->phi,
                           nullptr, nullptr, h->err, h->stream);
         cudaEventRecord(ev[1], h->stream);
-        if (ib) launch_spread(h->storage, h->dim, h->q, h->phi, h->N, h->F, h->flags, h->g, h->stream);
+        if (ib) enqueue_spread(h, h->stream);
         enqueue_classify(h, h->stream);
         cudaEventRecord(ev[2], h->stream);
         launch_sc(h, h->stream, last);
@@ -771,7 +872,7 @@ iblb_status iblb_step_profiled(iblb_handle h, int n_steps, double* kernel_ms)
 iblb_status iblb_set_tuning(iblb_handle h, const iblb_tuning* t)
 {
     if (!h || !t) return IBLB_EINVAL;
-    if (t->variant < 0 || t->variant > 2) return fail(h, IBLB_EINVAL, "variant must be 0, 1 or 2");
+    if (t->variant < 0 || t->variant > 3) return fail(h, IBLB_EINVAL, "variant must be 0 .. 3");
     if (t->block_x != 64 && t->block_x != 128 && t->block_x != 256)
         return fail(h, IBLB_EINVAL, "block_x must be 64, 128 or 256");
     if (t->rows_per_tile < 1 || t->rows_per_tile > 64)
@@ -779,6 +880,7 @@ iblb_status iblb_set_tuning(iblb_handle h, const iblb_tuning* t)
     if (!((t->ctas_per_sm == 2 && t->consumer_warps == 8) ||
           (t->ctas_per_sm == 1 && (t->consumer_warps == 16 || t->consumer_warps == 24))))
         return fail(h, IBLB_EINVAL, "ctas_per_sm 2 with 8 consumer warps, or 1 with 16 or 24");
+    if (t->wait_limit_cycles < 0) return fail(h, IBLB_EINVAL, "wait_limit_cycles must be >= 0");
     CK(h, cudaStreamSynchronize(h->stream));
     clear_graphs(h);
     Tuning tu;
@@ -788,6 +890,7 @@ iblb_status iblb_set_tuning(iblb_handle h, const iblb_tuning* t)
     tu.rows_per_tile = t->rows_per_tile;
     tu.ctas_per_sm = t->ctas_per_sm;
     tu.consumer_warps = t->consumer_warps;
+    tu.wait_limit = t->wait_limit_cycles;
     apply_tuning(h, tu);
     return IBLB_OK;
 }
@@ -795,14 +898,13 @@ iblb_status iblb_set_tuning(iblb_handle h, const iblb_tuning* t)
 iblb_status iblb_get_tuning(iblb_handle h, iblb_tuning* t)
 {
     if (!h || !t) return IBLB_EINVAL;
-    t->variant = (h->tune.variant == 1 && h->pipe_ok)
-                     ? 1
-                     : ((h->tune.variant == 2 && pair_kernel_ok(h->storage, h->g)) ? 2 : 0);
+    t->variant = iblb_stream_collide_variant(h);
     t->block_x = h->tune.block_x;
     t->streaming_stores = h->tune.streaming_stores;
     t->rows_per_tile = h->tune.rows_per_tile;
     t->ctas_per_sm = h->tune.ctas_per_sm;
     t->consumer_warps = h->tune.consumer_warps;
+    t->wait_limit_cycles = h->tune.wait_limit;
     return IBLB_OK;
 }
 
@@ -810,8 +912,9 @@ iblb_status iblb_autotune(iblb_handle h, int trials, iblb_tuning* chosen)
 {
     if (!h || trials < 1) return h ? fail(h, IBLB_EINVAL, "trials must be >= 1") : IBLB_EINVAL;
     std::vector<Tuning> cands;
-    for (int v : {0, 2}) {
+    for (int v : {0, 2, 3}) {
         if (v == 2 && !pair_kernel_ok(h->storage, h->g)) continue;
+        if (v == 3 && !rowpair_kernel_ok(h->Q, h->storage, h->g)) continue;
         for (int bx : {64, 128, 256}) {
             Tuning t;
             t.variant = v;
@@ -878,6 +981,7 @@ int iblb_stream_collide_variant(iblb_handle h)
     if (!h) return -1;
     if (h->tune.variant == 1 && h->pipe_ok) return 1;
     if (h->tune.variant == 2 && pair_kernel_ok(h->storage, h->g)) return 2;
+    if (h->tune.variant == 3 && rowpair_kernel_ok(h->Q, h->storage, h->g)) return 3;
     return 0;
 }
 

@@ -11,7 +11,8 @@
 //   2D ring (each segment is shared by two nodes); n_j is the normalised mean
 //   of the unit normals of the faces sharing node j, chi_j their total area.
 //   The surface-tension force is -sigma times the gradient of the interface
-//   area (3D) / length (2D) with linear elements.
+//   area (3D) / length (2D) with linear elements; an elastic interface adds
+//   minus the gradient of Skalak's strain energy (ib_core.cuh).
 // Delta is the tensor product of Peskin's 4-point kernel; stencil points on a
 // solid layer (or outside the lattice along the wall axis) take no force and
 // give zero velocity.
@@ -32,11 +33,34 @@ __global__ void k_forces_ring(const double* __restrict__ q, int N, ForceParams f
 
 // 3D mesh, pass 1: one thread per face writes its three corner records.
 __global__ void k_face_geometry(const double* __restrict__ q, const int* __restrict__ tri, int M,
-                                const int* __restrict__ entry_pos, double* __restrict__ rec)
+                                const int* __restrict__ entry_pos, ForceParams fp,
+                                double* __restrict__ rec)
 {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= M) return;
-    face_records(q, tri, f, entry_pos, rec);
+    face_records(q, tri, f, entry_pos, fp, rec);
+}
+
+// Elastic reference of the interface as it is now: per face (3D) the inverse
+// reference edge matrix and area, per segment (2D) the length.
+__global__ void k_elastic_reference(int dim, const double* __restrict__ q, int N, int M,
+                                    const int* __restrict__ tri, double* __restrict__ eref)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (dim == 3) {
+        if (t < M) face_elastic_reference(q, tri, t, eref + 5 * (long long)t);
+    } else if (t < N) {
+        const int tn = (t + 1 == N) ? 0 : t + 1;
+        const double sx = q[2 * tn] - q[2 * t], sy = q[2 * tn + 1] - q[2 * t + 1];
+        eref[t] = sqrt(sx * sx + sy * sy);
+    }
+}
+
+void launch_elastic_reference(int dim, const double* q, int N, int M, const int* tri, double* eref,
+                              cudaStream_t s)
+{
+    const int n = dim == 3 ? M : N;
+    if (n > 0) k_elastic_reference<<<(n + 127) / 128, 128, 0, s>>>(dim, q, N, M, tri, eref);
 }
 
 // 3D mesh, pass 2: one thread per node sums its records (no atomics).
@@ -59,7 +83,7 @@ void launch_forces(int dim, const double* q, int N, int M, const int* tri, const
         k_forces_ring<<<g, b, 0, s>>>(q, N, fp, phi, normal, chi, err);
     } else {
         const int b = 64;
-        k_face_geometry<<<(M + b - 1) / b, b, 0, s>>>(q, tri, M, entry_pos, entry_rec);
+        k_face_geometry<<<(M + b - 1) / b, b, 0, s>>>(q, tri, M, entry_pos, fp, entry_rec);
         k_node_forces<<<(N + b - 1) / b, b, 0, s>>>(q, N, entry_rec, csr_ptr, fp, phi, normal,
                                                     chi, err);
     }
@@ -381,7 +405,7 @@ k_observables(int dim, const double* __restrict__ q, int N, const int* __restric
     }
 }
 
-// Deformation index (Sec. 4, Eq. 12): the enclosed region is split into
+// Deformation index (Sec. 4, Eq. 15): the enclosed region is split into
 // simplices from the node mean p0 (triangles of the ring in 2D, tetrahedra of
 // the mesh in 3D).  Over a simplex with vertices v_k relative to p0 and
 // signed measure |K|: int x = |K| sum(v_k) / (d + 1) and

@@ -103,10 +103,83 @@ __device__ __forceinline__ bool point_of(const GridParams& g, R wk, int ik, int 
 }
 
 // ------------------------------------------------------------------ A1 pieces
+// Elastic interface: Skalak's strain energy per unit reference area,
+//   W = Gs/4 [I1^2 + 2 I1 - 2 I2 + C I2^2],  I1 = tr(Cg) - 2,  I2 = det(Cg) - 1,
+// Cg = F^T F the in-plane right Cauchy-Green tensor of a linear triangle,
+// F = [e1 e2] Mr with e1, e2 the current edges b - a, c - a and Mr the
+// inverse of the reference edges written in an orthonormal frame of the
+// reference triangle.  dW/dCg = W1 Id + W2 cof(Cg) (W1 = dW/dI1, W2 =
+// dW/dI2), dW/dF = 2 F dW/dCg, and the corner forces are -A0 dW/de1 (b),
+// -A0 dW/de2 (c) and their negated sum (a).  2D rings take the plane-strain
+// reduction (second stretch 1): segment tension T = Gs (1 + C) lam (lam^2 - 1),
+// lam = length / reference length.
+
+// Reference data of face f: Mr (row major) and the reference area.
+__device__ __forceinline__ void face_elastic_reference(const double* __restrict__ q,
+                                                       const int* __restrict__ tri, int f,
+                                                       double* __restrict__ ref)
+{
+    double a[3], E1[3], E2[3];
+    for (int k = 0; k < 3; k++) {
+        a[k] = q[3 * tri[3 * f] + k];
+        E1[k] = q[3 * tri[3 * f + 1] + k] - a[k];
+        E2[k] = q[3 * tri[3 * f + 2] + k] - a[k];
+    }
+    const double nx = E1[1] * E2[2] - E1[2] * E2[1];
+    const double ny = E1[2] * E2[0] - E1[0] * E2[2];
+    const double nz = E1[0] * E2[1] - E1[1] * E2[0];
+    const double twice_area = sqrt(nx * nx + ny * ny + nz * nz);
+    const double L1 = sqrt(E1[0] * E1[0] + E1[1] * E1[1] + E1[2] * E1[2]);
+    // frame: u along E1; the height of E2 above E1 is twice the area / L1,
+    // its projection on u is E2 . E1 / L1
+    const double p = (E2[0] * E1[0] + E2[1] * E1[1] + E2[2] * E1[2]) / L1;
+    const double h = twice_area / L1;
+    const double inv_det = 1.0 / (L1 * h);
+    ref[0] = h * inv_det;
+    ref[1] = -p * inv_det;
+    ref[2] = 0.0;
+    ref[3] = L1 * inv_det;
+    ref[4] = 0.5 * twice_area;
+}
+
+// Elastic corner forces of face f (out[v][k], v = corner a, b, c).
+__device__ __forceinline__ void face_elastic_force(const double* __restrict__ P0,
+                                                   const double* __restrict__ P1,
+                                                   const double* __restrict__ P2,
+                                                   const double* __restrict__ ref, double Gs,
+                                                   double Cs, double out[3][3])
+{
+    const double m00 = ref[0], m01 = ref[1], m10 = ref[2], m11 = ref[3], A0 = ref[4];
+    double f0[3], f1[3];
+    for (int k = 0; k < 3; k++) {
+        const double e1 = P1[k] - P0[k], e2 = P2[k] - P0[k];
+        f0[k] = e1 * m00 + e2 * m10;
+        f1[k] = e1 * m01 + e2 * m11;
+    }
+    const double c00 = f0[0] * f0[0] + f0[1] * f0[1] + f0[2] * f0[2];
+    const double c01 = f0[0] * f1[0] + f0[1] * f1[1] + f0[2] * f1[2];
+    const double c11 = f1[0] * f1[0] + f1[1] * f1[1] + f1[2] * f1[2];
+    const double I1 = c00 + c11 - 2.0;
+    const double I2 = c00 * c11 - c01 * c01 - 1.0;
+    const double W1 = 0.5 * Gs * (I1 + 1.0);
+    const double W2 = 0.5 * Gs * (Cs * I2 - 1.0);
+    const double s00 = W1 + W2 * c11, s01 = -W2 * c01, s11 = W1 + W2 * c00;
+    for (int k = 0; k < 3; k++) {
+        const double g0 = 2.0 * (f0[k] * s00 + f1[k] * s01);
+        const double g1 = 2.0 * (f0[k] * s01 + f1[k] * s11);
+        const double d1 = g0 * m00 + g1 * m01;
+        const double d2 = g0 * m10 + g1 * m11;
+        out[1][k] = -A0 * d1;
+        out[2][k] = -A0 * d2;
+        out[0][k] = A0 * (d1 + d2);
+    }
+}
+
 // 2D ring, node j of a ring of N nodes (segment j joins node j and j+1):
 // phi_j = sigma (t_j - t_{j-1}) - chi_j Pi(d_j) n_j / 2 with t the unit
 // tangents, n_j the normalised sum of the outward segment normals (t_y, -t_x)
-// of a counter-clockwise ring, chi_j = l_{j-1} + l_j.
+// of a counter-clockwise ring, chi_j = l_{j-1} + l_j; with an elastic
+// interface also T_j t_j - T_{j-1} t_{j-1}.
 __device__ __forceinline__ void ring_node_force(const double* __restrict__ q, int N, int j,
                                                 const ForceParams& fp, double* __restrict__ phi,
                                                 double* nrm, double* chi, int* err)
@@ -120,8 +193,15 @@ __device__ __forceinline__ void ring_node_force(const double* __restrict__ q, in
     const double s1x = cx - bx, s1y = cy - by;   // segment j
     const double l0 = sqrt(s0x * s0x + s0y * s0y);
     const double l1 = sqrt(s1x * s1x + s1y * s1y);
-    const double fsx = fp.sigma * (s1x / l1) - fp.sigma * (s0x / l0);
-    const double fsy = fp.sigma * (s1y / l1) - fp.sigma * (s0y / l0);
+    double fsx = fp.sigma * (s1x / l1) - fp.sigma * (s0x / l0);
+    double fsy = fp.sigma * (s1y / l1) - fp.sigma * (s0y / l0);
+    if (fp.eref) {
+        const double la0 = l0 / fp.eref[jm], la1 = l1 / fp.eref[j];
+        const double T0 = fp.Gs * (1.0 + fp.Cs) * la0 * (la0 * la0 - 1.0);
+        const double T1 = fp.Gs * (1.0 + fp.Cs) * la1 * (la1 * la1 - 1.0);
+        fsx += T1 * (s1x / l1) - T0 * (s0x / l0);
+        fsy += T1 * (s1y / l1) - T0 * (s0y / l0);
+    }
     const double nsx = s0y / l0 + s1y / l1;
     const double nsy = -s0x / l0 - s1x / l1;
     const double nl = sqrt(nsx * nsx + nsy * nsy);
@@ -142,15 +222,16 @@ __device__ __forceinline__ void ring_node_force(const double* __restrict__ q, in
     if (chi) chi[j] = ch;
 }
 
-// 3D mesh, face f: unit normal nu_f, area A_f and for each corner v
-// g_v = nu_f x (prev - next) (so d(A_f)/d(corner v) = g_v / 2), written as one
-// 8-double record (g_v[3], nu[3], A, pad) per corner at its CSR position.
+// 3D mesh, face f: unit normal nu_f, area A_f and for each corner v the
+// surface-tension force -sigma/2 nu_f x (prev - next) = -sigma d(A_f)/d(v)
+// (plus the elastic corner force of an elastic interface), written as one
+// 8-double record (force[3], nu[3], A, pad) per corner at its CSR position.
 constexpr int ENTRY_REC = 8;
 
 __device__ __forceinline__ void face_records(const double* __restrict__ q,
                                              const int* __restrict__ tri, int f,
                                              const int* __restrict__ entry_pos,
-                                             double* __restrict__ rec)
+                                             const ForceParams& fp, double* __restrict__ rec)
 {
     double P[3][3];
     for (int c = 0; c < 3; c++) {
@@ -165,14 +246,17 @@ __device__ __forceinline__ void face_records(const double* __restrict__ q,
     const double inv = 1.0 / nlen;
     const double nu[3] = {nf[0] * inv, nf[1] * inv, nf[2] * inv};
     const double area = 0.5 * nlen;
+    double fel[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    if (fp.eref) face_elastic_force(P[0], P[1], P[2], fp.eref + 5 * (long long)f, fp.Gs, fp.Cs, fel);
     for (int v = 0; v < 3; v++) {
         const double* nxt = P[(v + 1) % 3];
         const double* prv = P[(v + 2) % 3];
         const double e3[3] = {prv[0] - nxt[0], prv[1] - nxt[1], prv[2] - nxt[2]};
+        const double hs = 0.5 * fp.sigma;
         double* r = rec + (long long)ENTRY_REC * entry_pos[3 * f + v];
-        r[0] = nu[1] * e3[2] - nu[2] * e3[1];
-        r[1] = nu[2] * e3[0] - nu[0] * e3[2];
-        r[2] = nu[0] * e3[1] - nu[1] * e3[0];
+        r[0] = fel[v][0] - hs * (nu[1] * e3[2] - nu[2] * e3[1]);
+        r[1] = fel[v][1] - hs * (nu[2] * e3[0] - nu[0] * e3[2]);
+        r[2] = fel[v][2] - hs * (nu[0] * e3[1] - nu[1] * e3[0]);
         r[3] = nu[0];
         r[4] = nu[1];
         r[5] = nu[2];
@@ -181,7 +265,7 @@ __device__ __forceinline__ void face_records(const double* __restrict__ q,
 }
 
 // 3D mesh, node j: sum of its contiguous records (faces in increasing order),
-// phi_j = tension - chi_j Pi(d_j) n_j / 3.
+// phi_j = tension (+ elastic) - chi_j Pi(d_j) n_j / 3.
 __device__ __forceinline__ void mesh_node_force(const double* __restrict__ q, int j,
                                                 const double* __restrict__ rec,
                                                 const int* __restrict__ csr_ptr,
@@ -193,7 +277,7 @@ __device__ __forceinline__ void mesh_node_force(const double* __restrict__ q, in
     for (int e = e0; e < e1; e++) {
         const double* r = rec + (long long)ENTRY_REC * e;
         for (int k = 0; k < 3; k++) {
-            fs[k] -= fp.sigma * 0.5 * r[k];
+            fs[k] += r[k];
             ns[k] += r[3 + k];
         }
         area += r[6];

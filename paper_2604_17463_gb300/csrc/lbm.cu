@@ -64,79 +64,109 @@ k_stream_collide(const typename StorageT<ST>::S* __restrict__ fin,
     if (x >= nx) return;
     const long long cell = row * nx + x;
 
-    // neighbours: periodic along x (and y in 3D); the wall axis (y in 2D,
-    // z in 3D) has solid first/last layers when walls != 0
-    const int xm = (x == 0) ? nx - 1 : x - 1;
-    const int xp = (x == nx - 1) ? 0 : x + 1;
     const int Lw = (D == 2) ? ny : p.g.nz;
-    const int a = (D == 2) ? y : z;
-    int am = a - 1, ap = a + 1;
-    bool solid_m = false, solid_p = false;
-    if (walls) {
-        solid_m = (am == 0);
-        solid_p = (ap == Lw - 1);
-    } else {
-        if (am < 0) am = Lw - 1;
-        if (ap >= Lw) ap = 0;
-    }
-    int ym = y, yp = y;
-    if (D == 3) {
-        ym = (y == 0) ? ny - 1 : y - 1;
-        yp = (y == ny - 1) ? 0 : y + 1;
-    }
-
+    const int a = (D == 2) ? y : z;  // coordinate along the wall axis
     // binary16 populations stay in their stored scale (x 2^k) through the
     // collision: the moments undo the scale, the new terms take it on, and
     // no per-population rescaling is needed on load or store
     const float lsc = (ST == ST_FP16) ? 1.0f : p.inv_scale;
+    const unsigned c32 = (unsigned)cell;
     R g[Q];
+    R Fx, Fy, Fz;
+    if constexpr (D == 2) {
+        // Sources of the pull as 32-bit offsets from the cell on per-plane
+        // base pointers: periodic along x, solid first/last rows when walls
+        // != 0 (else periodic along y); everything but the x wrap depends on
+        // the block's row only.  Offsets are unsigned and wrap modulo 2^32
+        // (cell indices stay below 2^32).
+        const unsigned wstride = (unsigned)nx;
+        bool solid_m = false, solid_p = false;
+        unsigned dwm = 0u - wstride, dwp = wstride;  // sources a - 1, a + 1
+        if (walls) {
+            solid_m = (a - 1 == 0);
+            solid_p = (a + 1 == Lw - 1);
+        } else {
+            if (a == 0) dwm = (unsigned)(Lw - 1) * wstride;
+            if (a == Lw - 1) dwp = 0u - (unsigned)(Lw - 1) * wstride;
+        }
+        const unsigned dxm = (x == 0) ? (unsigned)(nx - 1) : 0u - 1u;
+        const unsigned dxp = (x == nx - 1) ? 0u - (unsigned)(nx - 1) : 1u;
 #pragma unroll
-    for (int i = 0; i < Q; i++) {
-        const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-        const int sx = cx == 0 ? x : (cx > 0 ? xm : xp);
-        const int cw = (D == 2) ? cy : cz;  // velocity along the wall axis
-        const int sa = cw == 0 ? a : (cw > 0 ? am : ap);
-        const bool solid = cw == 0 ? false : (cw > 0 ? solid_m : solid_p);
-        if constexpr (ST == ST_FP16) {
-            // binary16: 32-bit cell index on a per-plane base pointer (fewer
-            // integer instructions; the engine keeps binary16 lattices below
-            // 2^32 cells)
-            unsigned src32;
-            if (D == 2) {
-                src32 = (unsigned)sa * (unsigned)nx + (unsigned)sx;
+        for (int i = 0; i < Q; i++) {
+            const int cx = L::cx(i), cy = L::cy(i);
+            const bool solid = cy == 0 ? false : (cy > 0 ? solid_m : solid_p);
+            const unsigned off = (cx > 0 ? dxm : (cx < 0 ? dxp : 0u)) + (cy > 0 ? dwm : (cy < 0 ? dwp : 0u));
+            if (solid) {
+                g[i] = T::load(fin + (size_t)L::opp(i) * nc, c32, lsc);
+                if (EXT && p.moving) {  // moving wall: + 2 w_i (c_i . u_w) / c_s^2 (rho_w = 1)
+                    const double* uw = cy > 0 ? p.uw_lo : p.uw_hi;
+                    g[i] += (R)(6.0 * L::w(i) * (cx * uw[0] + cy * uw[1])) *
+                            (ST == ST_FP16 ? (R)p.scale : R(1));
+                }
             } else {
-                const int sy = cy == 0 ? y : (cy > 0 ? ym : yp);
-                src32 = ((unsigned)sa * (unsigned)ny + (unsigned)sy) * (unsigned)nx + (unsigned)sx;
+                g[i] = T::load(fin + (size_t)i * nc, c32 + off, lsc);
             }
-            if (solid)
-                g[i] = T::load(fin + (long long)L::opp(i) * nc, (unsigned)cell, lsc);
-            else
-                g[i] = T::load(fin + (long long)i * nc, src32, lsc);
-            if (EXT && p.moving && solid) {
-                const double* uw = cw > 0 ? p.uw_lo : p.uw_hi;
-                g[i] += (R)(6.0 * L::w(i) * (cx * uw[0] + cy * uw[1] + cz * uw[2])) * p.scale;
-            }
-            continue;
         }
-        long long src;
-        if (D == 2) {
-            src = (long long)sa * nx + sx;
+        Fx = param_body<R>(p, 0);
+        Fy = param_body<R>(p, 1);
+        Fz = R(0);
+    } else {
+        // 3D: neighbour coordinates per axis (periodic along x and y; solid
+        // first/last layers along z when walls != 0), the source index formed
+        // per direction; this form measured faster than the offset form above
+        // on the 3D workload
+        const int xm = (x == 0) ? nx - 1 : x - 1;
+        const int xp = (x == nx - 1) ? 0 : x + 1;
+        int am = a - 1, ap = a + 1;
+        bool solid_m = false, solid_p = false;
+        if (walls) {
+            solid_m = (am == 0);
+            solid_p = (ap == Lw - 1);
         } else {
+            if (am < 0) am = Lw - 1;
+            if (ap >= Lw) ap = 0;
+        }
+        const int ym = (y == 0) ? ny - 1 : y - 1;
+        const int yp = (y == ny - 1) ? 0 : y + 1;
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+            const int sx = cx == 0 ? x : (cx > 0 ? xm : xp);
+            const int sa = cz == 0 ? a : (cz > 0 ? am : ap);
             const int sy = cy == 0 ? y : (cy > 0 ? ym : yp);
-            src = ((long long)sa * ny + sy) * nx + sx;
-        }
-        if (solid) {
-            g[i] = T::load(fin, (long long)L::opp(i) * nc + cell, p.inv_scale);
-            if (EXT && p.moving) {  // moving wall: + 2 w_i (c_i . u_w) / c_s^2 (rho_w = 1)
-                const double* uw = cw > 0 ? p.uw_lo : p.uw_hi;
-                g[i] += (R)(6.0 * L::w(i) * (cx * uw[0] + cy * uw[1] + cz * uw[2]));
+            const bool solid = cz == 0 ? false : (cz > 0 ? solid_m : solid_p);
+            if constexpr (ST == ST_FP16) {
+                // binary16: 32-bit cell index on a per-plane base pointer
+                const unsigned src32 =
+                    ((unsigned)sa * (unsigned)ny + (unsigned)sy) * (unsigned)nx + (unsigned)sx;
+                if (solid)
+                    g[i] = T::load(fin + (long long)L::opp(i) * nc, c32, lsc);
+                else
+                    g[i] = T::load(fin + (long long)i * nc, src32, lsc);
+                if (EXT && p.moving && solid) {
+                    const double* uw = cz > 0 ? p.uw_lo : p.uw_hi;
+                    g[i] += (R)(6.0 * L::w(i) * (cx * uw[0] + cy * uw[1] + cz * uw[2])) * p.scale;
+                }
+                continue;
             }
-        } else {
-            g[i] = T::load(fin, (long long)i * nc + src, p.inv_scale);
+            const long long src = ((long long)sa * ny + sy) * nx + sx;
+            if (solid) {
+                g[i] = T::load(fin, (long long)L::opp(i) * nc + cell, p.inv_scale);
+                if (EXT && p.moving) {  // moving wall: + 2 w_i (c_i . u_w) / c_s^2 (rho_w = 1)
+                    const double* uw = cz > 0 ? p.uw_lo : p.uw_hi;
+                    g[i] += (R)(6.0 * L::w(i) * (cx * uw[0] + cy * uw[1] + cz * uw[2]));
+                }
+            } else {
+                g[i] = T::load(fin, (long long)i * nc + src, p.inv_scale);
+            }
         }
+        // the FP64 parameters converted per thread measured faster here than
+        // their FP32 copies
+        Fx = (R)p.body[0];
+        Fy = (R)p.body[1];
+        Fz = (R)p.body[2];
     }
 
-    R Fx = (R)p.body[0], Fy = (R)p.body[1], Fz = (R)p.body[2];
     if (band) {
         Fx += F[cell];
         Fy += F[nc + cell];
@@ -152,17 +182,23 @@ k_stream_collide(const typename StorageT<ST>::S* __restrict__ fin,
         mo = cell_moments<Q, R>(g, Fx, Fy, Fz, (R)p.inv_scale);
     else
         mo = cell_moments<Q, R>(g, Fx, Fy, Fz);
-    double om = p.omega;
+    R om = (D == 2) ? param_omega<R>(p) : (R)p.omega;
     if (EXT && p.two_tau) {  // viscosity ratio: outside the interface relax with omega_out
         const int col = (D == 2) ? x : x + nx * y;
-        if (!inside_cell(p.col_cnt, p.col_z, col, a)) om = p.omega_out;
+        if (!inside_cell(p.col_cnt, p.col_z, col, a)) om = (R)p.omega_out;
     }
     if constexpr (ST == ST_FP16) {
-        cell_collide<Q, R>(g, mo, (R)om, Fx, Fy, Fz, (R)p.scale);
-        store_cell<Q, ST, CS>(fout, nc, cell, g, 1.0f, sr_seed(step, cell));
+        cell_collide<Q, R>(g, mo, om, Fx, Fy, Fz, (R)p.scale);
+        if constexpr (D == 2)
+            store_cell32<Q, ST, CS>(fout, nc, c32, g, 1.0f, sr_seed(step, cell));
+        else
+            store_cell<Q, ST, CS>(fout, nc, cell, g, 1.0f, sr_seed(step, cell));
     } else {
-        cell_collide<Q, R>(g, mo, (R)om, Fx, Fy, Fz);
-        store_cell<Q, ST, CS>(fout, nc, cell, g, p.scale, 0u);
+        cell_collide<Q, R>(g, mo, om, Fx, Fy, Fz);
+        if constexpr (D == 2)
+            store_cell32<Q, ST, CS>(fout, nc, c32, g, p.scale, 0u);
+        else
+            store_cell<Q, ST, CS>(fout, nc, cell, g, p.scale, 0u);
     }
 
     if (WRITE_ALL || band) {
@@ -481,6 +517,191 @@ void launch_stream_collide_pairs(int Q, int storage, bool write_all, const void*
         if (storage == ST_FP32) launch_sc2_t<19, ST_FP32>(write_all, fin, fout, moments, F, flags, p, tu, s);
         else launch_sc2_t<19, ST_FP16>(write_all, fin, fout, moments, F, flags, p, tu, s);
     }
+}
+
+// ------------------------------------------------------------------ row pairs
+// Variant 3 (D3Q19, FP32 / binary16 storage): two cells per thread, (x, y0, z)
+// and (x, y0 + 1, z), in adjacent rows of one layer.  Loads and stores stay
+// scalar and coalesced along x; the two cells share the neighbour indices
+// along x and z and the per-thread set-up, and their moments and collision
+// run in packed FP32x2 arithmetic (one instruction for both cells).  binary16
+// stores convert the two cells' values of a population with one stochastic
+// rounding instruction.  A last odd row is computed by its own lane pair
+// with the second cell masked off.
+template <int ST> struct RowPair;
+template <> struct RowPair<ST_FP32> {
+    __device__ __forceinline__ static float load(const float* p, unsigned i) { return p[i]; }
+};
+template <> struct RowPair<ST_FP16> {
+    __device__ __forceinline__ static float load(const __half* p, unsigned i) { return __half2float(p[i]); }
+};
+
+template <int ST, bool WRITE_ALL, int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+k_stream_collide_y2(const typename StorageT<ST>::S* __restrict__ fin,
+                    typename StorageT<ST>::S* __restrict__ fout, float* __restrict__ mom,
+                    float* __restrict__ F, uint8_t* __restrict__ flags, const StreamParams p)
+{
+    using L = Stencil<19>;
+    using P = RowPair<ST>;
+    constexpr int Q = 19;
+    const int nx = p.g.nx, ny = p.g.ny, nz = p.g.nz;
+    const unsigned nc = (unsigned)p.g.ncell;
+    const int walls = p.g.walls;
+    const int woff = walls ? 1 : 0;
+    const int x = blockIdx.x * BLOCK + threadIdx.x;
+    const int y0 = 2 * blockIdx.y;
+    const int z = blockIdx.z + woff;
+    const bool hasB = y0 + 1 < ny;
+    const int lane = threadIdx.x & 31;
+    const unsigned rowA = (unsigned)z * (unsigned)ny + (unsigned)y0;
+    const unsigned rowB = hasB ? rowA + 1u : rowA;
+    int fa = 0, fb = 0;
+    if (lane == 0 && (x >> 5) < p.g.nseg_x) {
+        fa = flags[rowA * (unsigned)p.g.nseg_x + (x >> 5)];
+        fb = hasB ? flags[rowB * (unsigned)p.g.nseg_x + (x >> 5)] : 0;
+    }
+    const int bandA = __shfl_sync(0xffffffffu, fa, 0);
+    const int bandB = __shfl_sync(0xffffffffu, fb, 0);
+    unsigned step = 0;
+    if constexpr (ST == ST_FP16)
+        step = sr_step(p.rng_in, p.rng_out,
+                       blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0);
+    if (x >= nx) return;
+    const unsigned cellA = rowA * (unsigned)nx + (unsigned)x;
+    const unsigned cellB = rowB * (unsigned)nx + (unsigned)x;
+
+    const int xm = (x == 0) ? nx - 1 : x - 1;
+    const int xp = (x == nx - 1) ? 0 : x + 1;
+    int am = z - 1, ap = z + 1;
+    bool solid_m = false, solid_p = false;
+    if (walls) {
+        solid_m = (am == 0);
+        solid_p = (ap == nz - 1);
+    } else {
+        if (am < 0) am = nz - 1;
+        if (ap >= nz) ap = 0;
+    }
+    const int yB = hasB ? y0 + 1 : y0;
+    const int ymA = (y0 == 0) ? ny - 1 : y0 - 1;
+    const int ypA = (y0 + 1 == ny) ? 0 : y0 + 1;
+    const int ymB = (yB == 0) ? ny - 1 : yB - 1;
+    const int ypB = (yB + 1 == ny) ? 0 : yB + 1;
+
+    float2 g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+        const bool solid = cz == 0 ? false : (cz > 0 ? solid_m : solid_p);
+        if (solid) {
+            const typename StorageT<ST>::S* pl = fin + (size_t)L::opp(i) * nc;
+            g[i] = make_float2(P::load(pl, cellA), P::load(pl, cellB));
+            continue;
+        }
+        const int sx = cx == 0 ? x : (cx > 0 ? xm : xp);
+        const int sz = cz == 0 ? z : (cz > 0 ? am : ap);
+        const int syA = cy == 0 ? y0 : (cy > 0 ? ymA : ypA);
+        const int syB = cy == 0 ? yB : (cy > 0 ? ymB : ypB);
+        const unsigned zb = (unsigned)sz * (unsigned)ny;
+        const typename StorageT<ST>::S* pl = fin + (size_t)i * nc;
+        g[i] = make_float2(P::load(pl, (zb + (unsigned)syA) * (unsigned)nx + (unsigned)sx),
+                           P::load(pl, (zb + (unsigned)syB) * (unsigned)nx + (unsigned)sx));
+    }
+    float2 Fx = p2(p.body_f[0]), Fy = p2(p.body_f[1]), Fz = p2(p.body_f[2]);
+    if (bandA) {
+        Fx.x += F[cellA];
+        Fy.x += F[nc + cellA];
+        Fz.x += F[2 * nc + cellA];
+        F[cellA] = 0.f;
+        F[nc + cellA] = 0.f;
+        F[2 * nc + cellA] = 0.f;
+    }
+    if (bandB && hasB) {
+        Fx.y += F[cellB];
+        Fy.y += F[nc + cellB];
+        Fz.y += F[2 * nc + cellB];
+        F[cellB] = 0.f;
+        F[nc + cellB] = 0.f;
+        F[2 * nc + cellB] = 0.f;
+    }
+    const float ginv = (ST == ST_FP16) ? p.inv_scale : 1.0f;
+    const float gsc = (ST == ST_FP16) ? p.scale : 1.0f;
+    const CellMoments2 mo = cell_moments2<Q>(g, Fx, Fy, Fz, ginv);
+    cell_collide2<Q>(g, mo, p.omega_f, Fx, Fy, Fz, gsc);
+    if constexpr (ST == ST_FP16) {
+        unsigned short* o = reinterpret_cast<unsigned short*>(fout);
+        const unsigned seed = sr_seed(step, (long long)cellA);
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            // cell B in the high half, cell A in the low half
+            const unsigned h = cvt_rs_f16x2(g[i].y, g[i].x, sr_bits(seed, i));
+            unsigned short* pl = o + (size_t)i * nc;
+            pl[cellA] = (unsigned short)(h & 0xffffu);
+            if (hasB) pl[cellB] = (unsigned short)(h >> 16);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            float* pl = fout + (size_t)i * nc;
+            pl[cellA] = g[i].x;
+            if (hasB) pl[cellB] = g[i].y;
+        }
+    }
+    if (WRITE_ALL || bandA) {
+        mom[cellA] = mo.drho.x;
+        mom[nc + cellA] = mo.ux.x;
+        mom[2 * nc + cellA] = mo.uy.x;
+        mom[3 * nc + cellA] = mo.uz.x;
+    }
+    if (hasB && (WRITE_ALL || bandB)) {
+        mom[cellB] = mo.drho.y;
+        mom[nc + cellB] = mo.ux.y;
+        mom[2 * nc + cellB] = mo.uy.y;
+        mom[3 * nc + cellB] = mo.uz.y;
+    }
+    if (!isfinite(mo.drho.x) || (hasB && !isfinite(mo.drho.y))) atomicOr(p.err, ERR_NONFINITE);
+    if (lane == 0) {
+        if (bandA) flags[rowA * (unsigned)p.g.nseg_x + (x >> 5)] = 0;
+        if (bandB && hasB) flags[rowB * (unsigned)p.g.nseg_x + (x >> 5)] = 0;
+    }
+}
+
+template <int ST, int BLOCK>
+static void launch_y2_b(bool write_all, const void* fin, void* fout, void* mom, void* F,
+                        uint8_t* flags, const StreamParams& p, cudaStream_t s)
+{
+    using T = StorageT<ST>;
+    const int woff = p.g.walls ? 1 : 0;
+    dim3 grid((p.g.nx + BLOCK - 1) / BLOCK, (p.g.ny + 1) / 2, p.g.nz - 2 * woff);
+    auto* a = (const typename T::S*)fin;
+    auto* b = (typename T::S*)fout;
+    if (write_all)
+        k_stream_collide_y2<ST, true, BLOCK><<<grid, BLOCK, 0, s>>>(a, b, (float*)mom, (float*)F, flags, p);
+    else
+        k_stream_collide_y2<ST, false, BLOCK><<<grid, BLOCK, 0, s>>>(a, b, (float*)mom, (float*)F, flags, p);
+}
+
+bool rowpair_kernel_ok(int Q, int storage, const GridParams& g)
+{
+    return Q == 19 && storage != ST_FP64 && g.ny >= 2;
+}
+
+void launch_stream_collide_rowpairs(int storage, bool write_all, const void* fin, void* fout,
+                                    void* moments, void* F, uint8_t* flags, const StreamParams& p,
+                                    const Tuning& tu, cudaStream_t s)
+{
+#define IBLB_Y2(SS)                                                                           \
+    switch (tu.block_x) {                                                                    \
+        case 64: launch_y2_b<SS, 64>(write_all, fin, fout, moments, F, flags, p, s); break;  \
+        case 256: launch_y2_b<SS, 256>(write_all, fin, fout, moments, F, flags, p, s); break; \
+        default: launch_y2_b<SS, 128>(write_all, fin, fout, moments, F, flags, p, s); break; \
+    }
+    if (storage == ST_FP32) {
+        IBLB_Y2(ST_FP32)
+    } else {
+        IBLB_Y2(ST_FP16)
+    }
+#undef IBLB_Y2
 }
 
 // ------------------------------------------------------------------ conversions

@@ -123,6 +123,65 @@ __device__ __forceinline__ void store_cell(typename StorageT<ST>::S* __restrict_
     }
 }
 
+// As store_cell, with the cell index in 32 bits on per-plane base pointers
+// (the lattice holds fewer than 2^32 cells).
+template <int Q, int ST, bool CS>
+__device__ __forceinline__ void store_cell32(typename StorageT<ST>::S* __restrict__ fout,
+                                             long long nc, unsigned cell,
+                                             const typename StorageT<ST>::R* g, float scale,
+                                             unsigned seed)
+{
+    using T = StorageT<ST>;
+    if constexpr (ST == ST_FP16) {
+        unsigned short* o = reinterpret_cast<unsigned short*>(fout);
+#pragma unroll
+        for (int i = 0; i < Q; i += 2) {
+            const float lo = (i + 1 < Q) ? g[i + 1] * scale : 0.0f;
+            const unsigned h = cvt_rs_f16x2(g[i] * scale, lo, sr_bits(seed, i >> 1));
+            unsigned short* p0 = o + (size_t)i * nc;
+            if (CS) {
+                __stcs(p0 + cell, (unsigned short)(h >> 16));
+                if (i + 1 < Q) __stcs(p0 + nc + cell, (unsigned short)(h & 0xffffu));
+            } else {
+                p0[cell] = (unsigned short)(h >> 16);
+                if (i + 1 < Q) p0[nc + cell] = (unsigned short)(h & 0xffffu);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            typename T::S* pl = fout + (size_t)i * nc;
+            if (CS)
+                T::store_cs(pl, cell, g[i], scale);
+            else
+                T::store(pl, cell, g[i], scale);
+        }
+    }
+}
+
+// As store_cell, with one 32-bit index i * nc + cell into the buffer (the
+// buffer holds fewer than 2^32 elements).
+template <int Q, int ST>
+__device__ __forceinline__ void store_cell_flat(typename StorageT<ST>::S* __restrict__ fout,
+                                                unsigned nc, unsigned cell,
+                                                const typename StorageT<ST>::R* g, unsigned seed)
+{
+    using T = StorageT<ST>;
+    if constexpr (ST == ST_FP16) {
+        unsigned short* o = reinterpret_cast<unsigned short*>(fout);
+#pragma unroll
+        for (int i = 0; i < Q; i += 2) {
+            const float lo = (i + 1 < Q) ? g[i + 1] : 0.0f;
+            const unsigned h = cvt_rs_f16x2(g[i], lo, sr_bits(seed, i >> 1));
+            o[(unsigned)i * nc + cell] = (unsigned short)(h >> 16);
+            if (i + 1 < Q) o[(unsigned)(i + 1) * nc + cell] = (unsigned short)(h & 0xffffu);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; i++) T::store(fout, (unsigned)i * nc + cell, g[i], 1.0f);
+    }
+}
+
 // Time-step number for the rounding hash: read from the current slot of a
 // two-entry device counter; one thread of the launch writes the next value
 // into the other slot (read and written entries never coincide in a launch).
@@ -298,7 +357,7 @@ struct CellMoments2 {
 
 template <int Q>
 __device__ __forceinline__ CellMoments2 cell_moments2(const float2* g, float2 Fx, float2 Fy,
-                                                      float2 Fz)
+                                                      float2 Fz, float ginv = 1.0f)
 {
     using L = Stencil<Q>;
     constexpr int D = L::D;
@@ -315,6 +374,12 @@ __device__ __forceinline__ CellMoments2 cell_moments2(const float2* g, float2 Fx
             if (L::cz(i) < 0) jz = sub2(jz, g[i]);
         }
     }
+    if (ginv != 1.0f) {  // g held scaled by a power of two (binary16 storage)
+        drho = mul2(drho, p2(ginv));
+        jx = mul2(jx, p2(ginv));
+        jy = mul2(jy, p2(ginv));
+        jz = mul2(jz, p2(ginv));
+    }
     CellMoments2 m;
     m.drho = drho;
     m.rho = add2(p2(1.f), drho);
@@ -327,7 +392,8 @@ __device__ __forceinline__ CellMoments2 cell_moments2(const float2* g, float2 Fx
 
 template <int Q>
 __device__ __forceinline__ void cell_collide2(float2* g, const CellMoments2& m, float omega,
-                                              float2 Fx, float2 Fy, float2 Fz)
+                                              float2 Fx, float2 Fy, float2 Fz,
+                                              float gscale = 1.0f)
 {
     using L = Stencil<Q>;
     constexpr int D = L::D;
@@ -340,13 +406,14 @@ __device__ __forceinline__ void cell_collide2(float2* g, const CellMoments2& m, 
     const float2 k2 = mul2(p2(omega * 4.5f), m.rho);
     const float2 k1 = mul2(p2(omega), m.rho);
     const float2 p1 = p2(pref), p9 = p2(9.0f * pref);
-    g[0] = fma2(om1, g[0], mul2(p2(coef_b<Q, float>(0)), sym0));
+    // g held scaled by gscale (a power of two): the new terms take the same scale
+    g[0] = fma2(om1, g[0], mul2(p2(coef_b<Q, float>(0) * gscale), sym0));
 #pragma unroll
     for (int i = 1; i < Q; i++) {
         if (L::opp(i) < i) continue;
         const int o = L::opp(i);
-        const float2 w = p2(coef_b<Q, float>(i));
-        const float2 w3 = p2(coef_a<Q, float>(i));
+        const float2 w = p2(coef_b<Q, float>(i) * gscale);
+        const float2 w3 = p2(coef_a<Q, float>(i) * gscale);
         float2 cu = p2(0.f), cF = p2(0.f);
         if (L::cx(i) > 0) { cu = add2(cu, m.ux); cF = add2(cF, Fx); }
         if (L::cx(i) < 0) { cu = sub2(cu, m.ux); cF = sub2(cF, Fx); }

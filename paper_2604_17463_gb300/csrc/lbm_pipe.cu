@@ -19,9 +19,10 @@
 // For a direction whose source row is a solid layer (bounce-back) the
 // producer stages the opposite direction of the current row instead, and the
 // consumer reads it unshifted.
-// Every wait is bounded: after ~2 s a waiting thread latches ERR_TIMEOUT and
-// the CTA stops; the producer always waits (bounded) for the copies it issued
-// before it exits.
+// Every wait is bounded: after a limit (by default ~2 s; a launch-shape
+// parameter) a waiting thread latches ERR_TIMEOUT and the CTA stops; the
+// producer always waits (bounded by ~2 s) for the copies it issued before it
+// exits.
 #include "lbm_core.cuh"
 
 namespace iblb {
@@ -91,6 +92,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
     return ok != 0;
 }
 
+// Non-blocking test of the phase (mbarrier.test_wait never suspends the
+// thread, unlike try_wait, which may wait inside the instruction).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
 {
     asm volatile(
@@ -102,16 +118,34 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 
 constexpr long long PIPE_TIMEOUT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
 
-// Bounded wait for the phase of `bar` with the given parity.  Returns false
-// (and stops the CTA) on timeout or when another thread of the CTA gave up.
+// Bounded wait for the phase of `bar` with the given parity, at most `limit`
+// clock cycles.  Returns false (and stops the CTA) on timeout or when another
+// thread of the CTA gave up.
+// Limits below WAIT_POLL_BELOW cycles are enforced by polling with the
+// non-blocking test (a suspended try_wait could outlast them); longer ones
+// wait in try_wait between clock checks.
+constexpr long long WAIT_POLL_BELOW = 1000000LL;
+
 __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, int* err,
-                                           volatile int* abort_flag)
+                                           volatile int* abort_flag, long long limit)
 {
+    if (limit < WAIT_POLL_BELOW) {
+        const long long t0 = clock64();
+        while (!mbar_test_wait(bar, parity)) {
+            if (*abort_flag) return false;
+            if (clock64() - t0 > limit) {
+                atomicOr(err, ERR_TIMEOUT);
+                *abort_flag = 1;
+                return false;
+            }
+        }
+        return true;
+    }
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
         if (*abort_flag) return false;
-        if (clock64() - t0 > PIPE_TIMEOUT_CYCLES) {
+        if (clock64() - t0 > limit) {
             atomicOr(err, ERR_TIMEOUT);
             *abort_flag = 1;
             return false;
@@ -227,7 +261,7 @@ k_sc_pipe(const typename StorageT<ST>::S* __restrict__ fin,
             const int s = (int)(k % ps.stages);
             if (k >= ps.stages) {
                 const uint32_t par = (uint32_t)(((k / ps.stages) - 1) & 1);
-                if (!wait_phase(&empty[s], par, p.err, &abort_flag)) break;
+                if (!wait_phase(&empty[s], par, p.err, &abort_flag, ps.wait_limit)) break;
             }
             int y0, z, x0, rows;
             decode_tile<D>(ps, p.g, t, y0, z, x0, rows);
@@ -272,6 +306,8 @@ k_sc_pipe(const typename StorageT<ST>::S* __restrict__ fin,
             __syncwarp();
         }
         // drain: the copies of the last issued tiles must land before exit
+        // (with the fixed ~2 s bound whatever the tuned wait limit: copies
+        // in flight complete in microseconds)
         const long long issued = k;
         const long long first = issued > ps.stages ? issued - ps.stages : 0;
         for (long long j = first; j < issued; j++) {
@@ -297,7 +333,9 @@ k_sc_pipe(const typename StorageT<ST>::S* __restrict__ fin,
     long long k = 0;
     for (long long t = blockIdx.x; t < ps.ntiles; t += gridDim.x, ++k) {
         const int s = (int)(k % ps.stages);
-        if (!wait_phase(&full[s], (uint32_t)((k / ps.stages) & 1), p.err, &abort_flag)) break;
+        if (!wait_phase(&full[s], (uint32_t)((k / ps.stages) & 1), p.err, &abort_flag,
+                        ps.wait_limit))
+            break;
         int y0, z, x0, rows;
         decode_tile<D>(ps, p.g, t, y0, z, x0, rows);
         const unsigned char* stage = smem + (size_t)s * ps.stage_bytes;
@@ -384,6 +422,7 @@ bool pipe_shape(int Q, int storage, const GridParams& g, int sm_count, const Sme
     if (ctas_per_sm == 2 && consumer_warps != 8) return false;
     if (ctas_per_sm == 1 && consumer_warps != 16 && consumer_warps != 24) return false;
     ps.consumer_warps = consumer_warps;
+    ps.wait_limit = PIPE_TIMEOUT_CYCLES;
     const int elt = elt_of(storage);
     const int halo = 16 / elt;
     const int woff = g.walls ? 1 : 0;

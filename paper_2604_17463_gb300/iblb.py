@@ -56,6 +56,9 @@ class Config(ctypes.Structure):
         ("tau_out", ctypes.c_double),
         ("wall_u_lo", ctypes.c_double * 3),
         ("wall_u_hi", ctypes.c_double * 3),
+        ("deterministic_spread", ctypes.c_int),
+        ("shear_modulus", ctypes.c_double),
+        ("skalak_c", ctypes.c_double),
     ]
 
 
@@ -67,6 +70,7 @@ class Tuning(ctypes.Structure):
         ("rows_per_tile", ctypes.c_int),
         ("ctas_per_sm", ctypes.c_int),
         ("consumer_warps", ctypes.c_int),
+        ("wait_limit_cycles", ctypes.c_longlong),
     ]
 
     def as_dict(self):
@@ -126,6 +130,7 @@ def load():
         "iblb_set_interface": (st, [vp, dp, ip, ctypes.POINTER(ctypes.c_int), ip]),
         "iblb_step": (st, [vp, ip]),
         "iblb_sync": (st, [vp]),
+        "iblb_clear_faults": (st, [vp]),
         "iblb_read_fields": (st, [vp, dp, dp, dp]),
         "iblb_set_populations": (st, [vp, dp]),
         "iblb_get_populations": (st, [vp, dp]),
@@ -149,6 +154,7 @@ def load():
         "iblb_batch_admit": (st, [vp, ctypes.POINTER(Config), dp, ip, ctypes.POINTER(ctypes.c_int),
                                   ip, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int)]),
         "iblb_batch_run": (st, [vp, ip, ctypes.POINTER(ctypes.c_int)]),
+        "iblb_batch_run_profiled": (st, [vp, ip, ctypes.POINTER(ctypes.c_int), dp, dp]),
         "iblb_batch_sync": (st, [vp]),
         "iblb_batch_poll": (st, [vp, ctypes.POINTER(ctypes.c_int), ip, ctypes.POINTER(ctypes.c_int)]),
         "iblb_batch_slot_status": (st, [vp, ip, ctypes.POINTER(ctypes.c_longlong)]),
@@ -157,6 +163,7 @@ def load():
         "iblb_batch_release": (st, [vp, ip]),
         "iblb_batch_stats": (st, [vp, ctypes.POINTER(BatchInfo)]),
         "iblb_batch_slot_tile": (ctypes.c_int, [vp, ip]),
+        "iblb_batch_steps_to_next_completion": (ctypes.c_longlong, [vp]),
         "iblb_stream_bytes_per_step": (ctypes.c_double, [vp]),
         "iblb_fluid_cells": (ctypes.c_longlong, [vp]),
         "iblb_kernel_launch_count": (ctypes.c_longlong, []),
@@ -197,7 +204,8 @@ def current_stream_handle() -> int:
 def make_config(lattice, nx, ny, nz=1, *, tau=1.0, walls=True, wetting=True, sigma=1e-3, xi=1.0,
                 theta_eq_deg=90.0, pi_n=9, pi_m=3, body_force=(0.0, 0.0, 0.0), storage=FP64,
                 fp16_scale_exp=0, tau_out=0.0, wall_u_lo=(0.0, 0.0, 0.0),
-                wall_u_hi=(0.0, 0.0, 0.0)) -> Config:
+                wall_u_hi=(0.0, 0.0, 0.0), deterministic_spread=False, shear_modulus=0.0,
+                skalak_c=0.0) -> Config:
     c = Config()
     c.lattice = lattice
     c.nx, c.ny, c.nz = nx, ny, (1 if lattice == D2Q9 else nz)
@@ -216,6 +224,9 @@ def make_config(lattice, nx, ny, nz=1, *, tau=1.0, walls=True, wetting=True, sig
     for k in range(3):
         c.wall_u_lo[k] = wall_u_lo[k] if k < len(wall_u_lo) else 0.0
         c.wall_u_hi[k] = wall_u_hi[k] if k < len(wall_u_hi) else 0.0
+    c.deterministic_spread = int(bool(deterministic_spread))
+    c.shear_modulus = shear_modulus
+    c.skalak_c = skalak_c
     return c
 
 
@@ -288,9 +299,10 @@ def iblb_step_profiled(h, n_steps: int) -> np.ndarray:
 
 
 def iblb_set_tuning(h, variant: int, block_x: int = 128, streaming_stores: int = 0,
-                    rows_per_tile: int = 2, ctas_per_sm: int = 2, consumer_warps: int = 8):
+                    rows_per_tile: int = 2, ctas_per_sm: int = 2, consumer_warps: int = 8,
+                    wait_limit_cycles: int = 0):
     t = Tuning(int(variant), int(block_x), int(streaming_stores), int(rows_per_tile),
-               int(ctas_per_sm), int(consumer_warps))
+               int(ctas_per_sm), int(consumer_warps), int(wait_limit_cycles))
     _check(h, load().iblb_set_tuning(h, ctypes.byref(t)))
 
 
@@ -416,9 +428,12 @@ class Simulation:
         return qd
 
     def set_tuning(self, variant, block_x=128, streaming_stores=0, rows_per_tile=2,
-                   ctas_per_sm=2, consumer_warps=8):
+                   ctas_per_sm=2, consumer_warps=8, wait_limit_cycles=0):
         iblb_set_tuning(self.h, variant, block_x, streaming_stores, rows_per_tile, ctas_per_sm,
-                        consumer_warps)
+                        consumer_warps, wait_limit_cycles)
+
+    def clear_faults(self):
+        _check(self.h, load().iblb_clear_faults(self.h))
 
     def tuning(self):
         return iblb_get_tuning(self.h)
@@ -438,7 +453,7 @@ class Simulation:
                                                     _dptr(u)))
 
     def deformation(self):
-        """Deformation index of the interface in the shear plane (Sec. 4, Eq. 12)."""
+        """Deformation index of the interface in the shear plane (Sec. 4, Eq. 15)."""
         out = np.zeros(5)
         _check(self.h, load().iblb_deformation(self.h, _dptr(out)))
         return dict(D=out[0], r1=out[1], r3=out[2], angle_deg=out[3], volume=out[4])
@@ -528,6 +543,15 @@ class Batch:
         self._check(load().iblb_batch_run(self.h, int(max_steps), ctypes.byref(done)))
         return done.value
 
+    def run_profiled(self, max_steps: int):
+        """(completed, per-phase device ms [K_COUNT], stream-collide bytes)."""
+        done = ctypes.c_int(0)
+        kms = np.zeros(K_COUNT)
+        nb = ctypes.c_double(0.0)
+        self._check(load().iblb_batch_run_profiled(self.h, int(max_steps), ctypes.byref(done),
+                                                   _dptr(kms), ctypes.byref(nb)))
+        return done.value, kms, nb.value
+
     def sync(self):
         self._check(load().iblb_batch_sync(self.h))
 
@@ -562,6 +586,10 @@ class Batch:
     def release(self, slot: int):
         self._check(load().iblb_batch_release(self.h, int(slot)))
         self.meta.pop(slot, None)
+
+    def steps_to_next_completion(self) -> int:
+        """Steps until the next active slot completes (-1: none active)."""
+        return int(load().iblb_batch_steps_to_next_completion(self.h))
 
     def tile(self, slot: int) -> int:
         return load().iblb_batch_slot_tile(self.h, int(slot))

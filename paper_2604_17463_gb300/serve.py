@@ -115,9 +115,13 @@ def serve(requests, storage: int, budget_2d: int, budget_3d: int, chunk: int = 5
             if pending:
                 time.sleep(max(0.0, requests[pending[0]].arrival_s - (time.perf_counter() - t0)))
             continue
-        # both batches advance concurrently on their own streams
+        # both batches advance concurrently on their own streams, each by at
+        # most `chunk` steps and never past its next completion, so that a
+        # finished request is read and its room freed in the same round
         for b in batches.values():
-            b.run(chunk)
+            left = b.steps_to_next_completion()
+            if left > 0:
+                b.run(min(chunk, left))
         for b in batches.values():
             b.sync()
         for lat, b in batches.items():

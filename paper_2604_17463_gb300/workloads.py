@@ -300,7 +300,7 @@ class ShearDrop:
 
     def d_inf(self) -> float:
         """Small-deformation steady deformation of an unbounded 3D drop
-        (Sec. 4, Eq. 13): (19 lambda + 16) / (16 lambda + 16) Ca."""
+        (Sec. 4, Eq. 16): (19 lambda + 16) / (16 lambda + 16) Ca."""
         lam = self.lam
         return (19.0 * lam + 16.0) / (16.0 * lam + 16.0) * self.Ca
 

@@ -1,0 +1,153 @@
+"""Order-deterministic spreading (iblb_config.deterministic_spread).
+
+With the flag on, Eq. 8 is evaluated as an ordered gather, so a run repeated
+on the same inputs gives bitwise the same fields and node positions; it still
+matches the FP64 oracle within the FP64 tolerances (relative L2 <= 1e-10 on
+rho - 1 and u, nodes to 1e-11), and the spread force field matches the
+oracle's and the atomic path's to round-off.  In the batched engine a slot
+with the flag gives bitwise the same result alone and in a mix.
+"""
+import numpy as np
+import pytest
+
+from paper_2604_17463_gb300 import iblb
+from paper_2604_17463_gb300 import workloads as W
+from helpers import fluid_mask, oracle_from_workload, rel_l2, small_2d, small_3d
+
+pytestmark = pytest.mark.gpu
+
+GB = 1 << 30
+
+
+def seam_2d():
+    # ragged width (37, not a multiple of the 4-cell bins) and a drop across
+    # the periodic seam at x = 0
+    wl = small_2d(nx=37, ny=26, R=6.0, cx=1.3)
+    return wl
+
+
+def seam_3d():
+    wl = small_3d(n=22, nz=17, R=5.0)
+    wl.nodes = wl.nodes.copy()
+    wl.nodes[:, 0] -= 10.6   # drop centre near x = 0.4: its stencils wrap
+    wl.nodes[:, 1] += 9.7    # and near y = 20.7
+    return wl
+
+
+CASES = {"2d": small_2d, "3d": small_3d, "2d_seam": seam_2d, "3d_seam": seam_3d}
+
+
+@pytest.mark.parametrize("which", list(CASES))
+@pytest.mark.parametrize("storage,tol", [(iblb.FP64, 1e-13), (iblb.FP32_DEV, 1e-6)])
+def test_force_field_matches_oracle_and_atomic_path(which, storage, tol):
+    wl = CASES[which]()
+    o = oracle_from_workload(wl)
+    Fo, bad = o.force_field()
+    assert not bad
+    g = iblb.Simulation.from_workload(wl, storage=storage, deterministic_spread=True)
+    a = iblb.Simulation.from_workload(wl, storage=storage)
+    Fg, Fa = g.force_field(), a.force_field()
+    dim = wl.dim
+    scale = np.max(np.abs(Fo[:dim]))
+    assert scale > 0
+    assert np.max(np.abs(Fg - Fo[:dim])) <= tol * scale
+    assert np.max(np.abs(Fg - Fa)) <= tol * scale
+    # the band buffer is left cleared: a second call gives the same field
+    assert np.array_equal(g.force_field(), Fg)
+    g.close()
+    a.close()
+
+
+@pytest.mark.parametrize("which,steps", [("2d", 200), ("3d", 20), ("2d_seam", 120), ("3d_seam", 15)])
+def test_bitwise_repeatable_and_matches_oracle(which, steps):
+    wl = CASES[which]()
+    runs = []
+    for _ in range(2):
+        g = iblb.Simulation.from_workload(wl, deterministic_spread=True)
+        g.step(steps)
+        runs.append(g.fields())
+        g.close()
+    (r0, u0, q0), (r1, u1, q1) = runs
+    assert np.array_equal(r0, r1) and np.array_equal(u0, u1) and np.array_equal(q0, q1)
+    o = oracle_from_workload(wl)
+    assert o.step(steps) == 0
+    ro, uo, qo = o.fields()
+    m = fluid_mask(o.shape, wl.dim)
+    assert rel_l2(r0[m] - 1.0, ro[m] - 1.0) < 1e-10
+    assert rel_l2(u0[:, m], uo[: wl.dim, m]) < 1e-10
+    assert np.max(np.abs(q0 - qo)) < 1e-11
+
+
+def test_config1_deterministic_2000_steps():
+    # the 128x64 drop of the first workload, 2000 steps, twice: bitwise equal,
+    # and within the FP64 tolerances of the oracle
+    wl = W.config1()
+    out = []
+    for _ in range(2):
+        g = iblb.Simulation.from_workload(wl, deterministic_spread=True)
+        g.step(wl.steps)
+        out.append(g.fields())
+        g.close()
+    assert all(np.array_equal(a, b) for a, b in zip(out[0], out[1]))
+    o = oracle_from_workload(wl)
+    assert o.step(wl.steps) == 0
+    ro, uo, qo = o.fields()
+    m = fluid_mask(o.shape, 2)
+    rg, ug, qg = out[0]
+    assert rel_l2(ug[:, m], uo[:2, m]) < 1e-10
+    assert rel_l2(rg[m], ro[m]) < 1e-10
+    # rho - 1 ~ 3e-5: the oracle's rounding of its raw f ~ 0.1-0.4 bounds the
+    # agreement on the deviation at ~1e-9 relative after 2000 steps
+    assert rel_l2(rg[m] - 1.0, ro[m] - 1.0) < 1e-8
+    assert np.max(np.abs(qg - qo)) < 1e-11
+
+
+def test_batch_alone_and_in_the_mix_bitwise():
+    steps = 300
+    target = W.droplet_2d(96, 70.0, 0.8, steps, name="target")
+    alone = iblb.Batch(iblb.D2Q9, iblb.FP64, 1 * GB, max_slots=4)
+    sa = alone.admit_workload(target, n_steps=steps, deterministic_spread=True)
+    alone.run(steps)
+    ra, ua, qa = alone.fields(sa)
+    mix = iblb.Batch(iblb.D2Q9, iblb.FP64, 1 * GB, max_slots=32)
+    rng = np.random.default_rng(9)
+    for k in range(10):
+        w = int(rng.integers(64, 300))
+        mix.admit_workload(W.droplet_2d(w, float(rng.uniform(30, 150)), float(rng.uniform(0.6, 1.4)), 0),
+                           n_steps=int(rng.integers(100, 500)), deterministic_spread=True)
+    sm = mix.admit_workload(target, n_steps=steps, deterministic_spread=True)
+    mix.run(120)
+    for k in range(3):   # arrivals while it runs
+        mix.admit_workload(W.droplet_2d(int(rng.integers(64, 200)), 90.0, 1.0, 0), n_steps=200,
+                           deterministic_spread=True)
+    mix.run(1000)
+    assert mix.steps_done(sm) == steps
+    rm, um, qm = mix.fields(sm)
+    assert np.array_equal(rm, ra) and np.array_equal(um, ua) and np.array_equal(qm, qa)
+    # and the slot matches the oracle
+    o = oracle_from_workload(target)
+    assert o.step(steps) == 0
+    ro, uo, qo = o.fields()
+    m = fluid_mask(o.shape, 2)
+    assert rel_l2(ua[:, m], uo[:2, m]) < 1e-10
+    assert np.max(np.abs(qa - qo)) < 1e-11
+    alone.close()
+    mix.close()
+
+
+def test_batch_3d_deterministic_slot_matches_single_engine():
+    wl = small_3d(n=24, nz=20, R=6.0)
+    steps = 12
+    b = iblb.Batch(iblb.D3Q19, iblb.FP64, 1 * GB, max_slots=4)
+    s = b.admit_workload(wl, n_steps=steps, deterministic_spread=True)
+    b.admit_workload(small_3d(n=20, nz=16, R=4.5), n_steps=steps + 5, deterministic_spread=True)
+    b.run(steps)
+    rb, ub, qb = b.fields(s)
+    g = iblb.Simulation.from_workload(wl, deterministic_spread=True)
+    g.step(steps)
+    rg, ug, qg = g.fields()
+    m = fluid_mask(rg.shape, 3)
+    assert np.array_equal(ub[:, m], ug[:, m]) or rel_l2(ub[:, m], ug[:, m]) < 1e-13
+    assert np.max(np.abs(qb - qg)) < 1e-13
+    g.close()
+    b.close()

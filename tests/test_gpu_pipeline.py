@@ -36,6 +36,8 @@ def applies(variant, Q, nx, storage):
     library falls back to the plain kernel)."""
     if variant == 2:
         return storage != iblb.FP64 and nx % 2 == 0
+    if variant == 3:
+        return storage != iblb.FP64 and Q == 19
     return variant == 0
 
 
@@ -47,12 +49,12 @@ def test_kernel_variants_match_plain_and_oracle(Q, dims, walls, storage):
     body = (2e-6, -1e-6, 5e-7 if Q == 19 else 0.0)
     f0 = near_eq(Q, shape, seed=nx + ny)
     out = {}
-    for variant in (0, 1, 2):
+    for variant in (0, 1, 2, 3):
         g = iblb.Simulation(Q, nx, ny, nz, tau=0.83, walls=walls, wetting=False, body_force=body,
                             storage=storage)
         g.set_tuning(variant, rows_per_tile=3)
-        if variant == 2:
-            assert g.variant == (2 if applies(2, Q, nx, storage) else 0)
+        if variant in (2, 3):
+            assert g.variant == (variant if applies(variant, Q, nx, storage) else 0)
         g.set_populations(f0)
         g.step(4)
         out[variant] = g.populations()
@@ -64,7 +66,7 @@ def test_kernel_variants_match_plain_and_oracle(Q, dims, walls, storage):
     # (populations here have |g| < 1/32, i.e. below 2048 once scaled by 2^16,
     # where the binary16 spacing is at most 1: one ulp <= 2^-16 unscaled)
     tol = {iblb.FP64: 1e-15, iblb.FP32_DEV: 2e-7, iblb.FP16_DEV: 2.0 ** -16 * 1.01}[storage]
-    for variant in (1, 2):
+    for variant in (1, 2, 3):
         assert np.max(np.abs(out[variant][:, m] - out[0][:, m])) < tol, variant
     if storage == iblb.FP64:
         o = oracle.Sim(Q, nx, ny, nz, tau=0.83, walls=walls, wetting=False, body_force=body)
@@ -112,7 +114,7 @@ def test_autotune_leaves_state_unchanged():
     a.step(5)
     b.step(5)
     pick = b.autotune(trials=3)
-    assert pick["variant"] in (0, 1, 2)
+    assert pick["variant"] in (0, 1, 2, 3)
     a.step(5)
     b.step(5)
     fa, fb = a.populations(), b.populations()
@@ -122,3 +124,38 @@ def test_autotune_leaves_state_unchanged():
     assert np.max(np.abs(qa - qb)) < 1e-9
     a.close()
     b.close()
+
+
+def test_wait_limit_latches_timeout_and_the_handle_recovers():
+    # The pipelined kernel's waits on its shared-memory pipeline are bounded.
+    # With a limit of 200 clock cycles (shorter than any bulk copy takes) the
+    # consumers give up at their first wait: the launch latches IBLB_ETIMEOUT,
+    # which the next synchronising call reports, and the producer still waits
+    # for its copies before it exits.  After iblb_clear_faults, with the
+    # default limit and the populations set again, the same handle gives
+    # exactly the results of a fresh one.
+    Q, nx, ny = 9, 256, 64
+    f0 = near_eq(Q, (1, ny, nx), seed=77)
+    kw = dict(tau=0.8, walls=True, wetting=False, storage=iblb.FP32_DEV)
+    g = iblb.Simulation(Q, nx, ny, **kw)
+    g.set_populations(f0)
+    g.set_tuning(1, rows_per_tile=2, ctas_per_sm=2, consumer_warps=8, wait_limit_cycles=200)
+    assert g.variant == 1
+    assert g.tuning()["wait_limit_cycles"] == 200
+    g.step(3)
+    with pytest.raises(iblb.IBLBError) as e:
+        g.sync()
+    assert e.value.status == 6   # IBLB_ETIMEOUT
+    g.clear_faults()
+    g.sync()
+    g.set_tuning(1, rows_per_tile=2, ctas_per_sm=2, consumer_warps=8)
+    g.set_populations(f0)
+    g.step(5)
+    ref = iblb.Simulation(Q, nx, ny, **kw)
+    ref.set_tuning(1, rows_per_tile=2, ctas_per_sm=2, consumer_warps=8)
+    ref.set_populations(f0)
+    ref.step(5)
+    m = fluid_mask((1, ny, nx), 2)   # solid rows are never written
+    assert np.array_equal(g.populations()[:, m], ref.populations()[:, m])
+    g.close()
+    ref.close()

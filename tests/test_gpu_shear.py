@@ -1,6 +1,6 @@
 """GPU parity and validation of the drop-in-shear pieces (Sec. 4): moving-wall
-bounce-back, equilibrium initialisation, the deformation index D (Eq. 12),
-and the steady deformation of the paper's case against Eq. 13.
+bounce-back, equilibrium initialisation, the deformation index D (Eq. 15),
+and the steady deformation of the paper's case against Eq. 16.
 """
 import math
 
@@ -138,7 +138,7 @@ def test_shear_drop_paper_case_fp32():
     hist, obs = run_shear(case, iblb.FP32_DEV)
     D_end = hist[-1][1]
     err = abs(D_end - case.d_inf()) / case.d_inf()
-    print(f"shear drop: D(12 t_mu) = {D_end:.5f}, Eq. 13 {case.d_inf():.5f}, "
+    print(f"shear drop: D(12 t_mu) = {D_end:.5f}, Eq. 16 {case.d_inf():.5f}, "
           f"rel. distance {err * 100:.2f} %, inclination {hist[-1][2]:.1f} deg")
     assert err < 0.05
     # steady: the last quarter changes by < 1 %

@@ -1,5 +1,5 @@
 """Pins of the oracle's drop-in-shear pieces (Sec. 4): moving-wall bounce-back,
-equilibrium initialisation from fields, and the deformation index D (Eq. 12).
+equilibrium initialisation from fields, and the deformation index D (Eq. 15).
 
 - Plane Couette flow between walls moving at u_lo and u_hi is an exact
   steady solution of BGK with halfway bounce-back: u(a) = u_lo + (u_hi -

@@ -9,7 +9,8 @@ from paper_2604_17463_gb300 import workloads as W
 
 
 class FakeBatch:
-    """Admission by a cell budget; each run advances every slot by `chunk`."""
+    """Admission by a cell budget; each run advances every slot by `chunk`
+    (never past its own step count)."""
     log = []
 
     def __init__(self, lattice, storage, budget, max_slots=64, stream=None):
@@ -32,9 +33,14 @@ class FakeBatch:
         for v in self.slots.values():
             v[1] -= min(chunk, v[1])
         self.launches += 1
+        FakeBatch.log.append(("run", chunk))
 
     def sync(self):
         pass
+
+    def steps_to_next_completion(self):
+        left = [v[1] for v in self.slots.values() if v[1] > 0]
+        return min(left) if left else -1
 
     def poll(self):
         return [s for s, v in self.slots.items() if v[1] == 0]
@@ -92,3 +98,16 @@ def test_large_request_does_not_block_smaller_ones(fake):
     assert order.index("c200") < order.index("b900")
     assert order.index("d200") < order.index("b900")
     assert out["max_queue"] >= 1
+
+
+def test_rounds_stop_at_the_next_completion(fake):
+    # with chunk = 500, a 120-step request completes after a round of 120
+    # steps (not 500), and the 1000-step one keeps running in later rounds
+    reqs = [req("short", 0.0, 20, 120), req("long", 0.0, 20, 1000)]
+    out = serve.serve(reqs, iblb.FP32_DEV, budget_2d=10_000, budget_3d=10_000, chunk=500,
+                      streams=(0, 0))
+    assert out["completed"] == 2
+    runs = [c for ev, c in fake.log if ev == "run"]
+    assert runs[0] == 120
+    assert runs[1:] == [500, 380]
+    assert all(r["steps"] == q.work.steps for r, q in zip(out["results"], reqs))
