@@ -538,8 +538,10 @@ def run_serve_mode(args):
     reqs = W.config5(count=args.count, rate_per_s=args.rate, steps_lo=5000 // args.step_div,
                      steps_hi=50000 // args.step_div)
     storage = {"fp32": iblb.FP32_DEV, "fp16": iblb.FP16_DEV, "fp64": iblb.FP64}[args.serve_storage]
-    # seeded sample of the 2D requests for the oracle check
-    two_d = [i for i, r in enumerate(reqs) if r.work.lattice == 9]
+    # seeded sample of the 2D requests for the oracle check (among those the
+    # single-threaded oracle runs in a bounded time)
+    two_d = [i for i, r in enumerate(reqs) if r.work.lattice == 9 and
+             r.work.fluid_cells * r.work.steps <= args.oracle_max_updates]
     k = max(1, int(round(args.oracle_frac * len(reqs))))
     rng = np.random.default_rng(20260417 + 55)
     sample = sorted(int(i) for i in rng.choice(two_d, size=min(k, len(two_d)), replace=False))
@@ -578,7 +580,8 @@ def run_serve_mode(args):
         "oracle_check": {"max_dtheta_deg": max(errs) if errs else None, "theta_compared": len(errs),
                          "max_rel_dheight": max(herrs) if herrs else None,
                          "requests": len(sample), "sample": f"seeded {len(sample)} of the "
-                         f"{len(two_d)} 2D requests ({args.oracle_frac:.0%} of all)",
+                         f"{len(two_d)} 2D requests with at most {args.oracle_max_updates:.0e} "
+                         f"cell updates ({args.oracle_frac:.0%} of all requests)",
                          "oracle_cores": pool._processes if hasattr(pool, "_processes") else None,
                          "oracle_wait_after_serving_s": oracle_extra_s},
         "gpu_launches": int(launches),
@@ -896,6 +899,9 @@ def main():
                     help="batch / serve / spread2d: divide the step counts by this")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: arrivals per second")
     ap.add_argument("--chunk", type=int, default=500, help="serve: steps per scheduling round")
+    ap.add_argument("--oracle-max-updates", type=float, default=3e9,
+                    help="serve: the oracle sample is drawn among the 2D requests with at most "
+                         "this many cell updates")
     ap.add_argument("--oracle-frac", type=float, default=0.02,
                     help="serve: fraction of the requests (drawn among the 2D ones) checked "
                          "against the FP64 oracle")

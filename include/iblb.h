@@ -281,6 +281,16 @@ typedef struct {
                                      incomplete); 0 = about 2 s.  Copies in
                                      flight are always waited for (bounded by
                                      about 2 s) before the kernel exits. */
+    int ib_per_node;              /* 3D interfaces: 0 (default) spreads and
+                                     interpolates by spatial groups of nodes
+                                     (the nodes of one 8 x 8 x 8 tile of the
+                                     lattice; each group sums its stencils in,
+                                     or reads them from, a box of the lattice
+                                     in shared memory); 1 uses one thread per
+                                     node with one global addition per
+                                     stencil point.  Results differ only by
+                                     the order of the additions.  Not changed
+                                     by iblb_autotune. */
 } iblb_tuning;
 
 /* Set / read the launch shape.  iblb_set_tuning synchronises. */
@@ -288,11 +298,13 @@ iblb_status iblb_set_tuning(iblb_handle h, const iblb_tuning* t);
 iblb_status iblb_get_tuning(iblb_handle h, iblb_tuning* t);
 
 /* Autotuner: time every applicable launch shape (plain kernel with 64, 128
- * and 256-thread blocks; pair kernel likewise; pipelined kernel with 1, 2 or 4 rows per tile and
- * 8, 16 or 24 consumer warps) over `trials` launches each and keep the
- * fastest.  The trial launches read the current populations and write only
- * the second (scratch) population buffer, so the simulation state is left
- * unchanged.  `chosen` (may be NULL) receives the kept shape.  Synchronises. */
+ * and 256-thread blocks; x-pair and row-pair kernels likewise; pipelined
+ * kernel with 1, 2 or 4 rows per tile and 8, 16 or 24 consumer warps) over
+ * `trials` launches each, after 4 * trials untimed warm-up launches, in two
+ * passes (the faster pass of each shape counts), and keep the fastest.  The
+ * trial launches read the current populations and write only the second
+ * (scratch) population buffer, so the simulation state is left unchanged.
+ * `chosen` (may be NULL) receives the kept shape.  Synchronises. */
 iblb_status iblb_autotune(iblb_handle h, int trials, iblb_tuning* chosen);
 
 /* The stream-collide variant in use (0 plain, 1 pipelined, 2 x pairs,

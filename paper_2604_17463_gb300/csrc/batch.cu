@@ -87,23 +87,24 @@ namespace {
 
 constexpr int BT = 128;  // threads per stream-collide block
 
-// Rows of 32-cell segments a warp of the batched stream-collide works on at
-// once (their loads are all issued before any of them is collided, so that
-// enough bytes are in flight per SM for the HBM bound): two for the lighter
-// forms (D2Q9, and binary16 storage, whose cells carry fewer bytes), one for
-// D3Q19 FP32 and for FP64 (bound by the FP64 arithmetic).  A slot's work
-// items hold cpt segments, a multiple of this.
-template <int Q, int ST> struct BIlp {
-    static constexpr int value = ST == ST_FP64 ? 1 : ((Q == 9 || ST == ST_FP16) ? 2 : 1);
-};
-int b_ilp(int Q, int storage)
+// 32-cell segments a warp of the batched stream-collide works on at once
+// (their loads are all issued before any of them is collided, so that
+// enough bytes are in flight per SM for the HBM bound), and the resident
+// blocks per SM asked of the register allocator; chosen by measurement on
+// the 256-drop set (D2Q9 FP32: 3 segments at 5 blocks beat 2 at 6 or 8 and
+// 4 at 4; D2Q9 binary16: 2 at 6).  FP64 is bound by its arithmetic.  A
+// slot's work items hold cpt segments, a multiple of this.
+constexpr int b_ilp_of(int Q, int ST)
 {
-    return storage == ST_FP64 ? 1 : ((Q == 9 || storage == ST_FP16) ? 2 : 1);
+    return ST == ST_FP64 ? 1 : (Q == 9 ? (ST == ST_FP32 ? 3 : 2) : (ST == ST_FP16 ? 2 : 1));
 }
+template <int Q, int ST> struct BIlp {
+    static constexpr int value = b_ilp_of(Q, ST);
+};
+int b_ilp(int Q, int storage) { return b_ilp_of(Q, storage); }
 
-// Resident blocks per SM asked of the register allocator.
 template <int Q, int ST> struct BMinBlocks {
-    static constexpr int value = ST == ST_FP64 ? (Q == 9 ? 5 : 4) : (Q == 9 ? 6 : (ST == ST_FP32 ? 5 : 4));
+    static constexpr int value = ST == ST_FP64 ? (Q == 9 ? 5 : 4) : (Q == 9 ? (ST == ST_FP32 ? 5 : 6) : (ST == ST_FP32 ? 5 : 4));
 };
 
 // One stream-collide work item: cpt consecutive 32-cell segments x0 ..
@@ -257,9 +258,16 @@ k_b_stream_collide(const SlotDev* __restrict__ slots, const BItem* __restrict__ 
                 fyk[k] = R(0);
                 fzk[k] = R(0);
                 if (bandk[k] && validk[k]) {
-                    fxk[k] = F[cellk[k]];
-                    fyk[k] = F[nc + cellk[k]];
-                    if (D == 3) fzk[k] = F[2 * nc + cellk[k]];
+                    if constexpr (sizeof(R) == 4) {  // float4 per cell
+                        const float4 f = reinterpret_cast<const float4*>(F)[cellk[k]];
+                        fxk[k] = f.x;
+                        fyk[k] = f.y;
+                        fzk[k] = f.z;
+                    } else {
+                        fxk[k] = F[cellk[k]];
+                        fyk[k] = F[nc + cellk[k]];
+                        if (D == 3) fzk[k] = F[2 * nc + cellk[k]];
+                    }
                 }
             }
             // pass 2: collide and store each cell
@@ -270,20 +278,19 @@ k_b_stream_collide(const SlotDev* __restrict__ slots, const BItem* __restrict__ 
                 const int band = bandk[k];
                 const R Fx = fxk[k], Fy = fyk[k], Fz = fzk[k];
                 if (band) {  // the band buffer is left zero for the next spread
-                    F[cell] = 0;
-                    F[nc + cell] = 0;
-                    if (D == 3) F[2 * nc + cell] = 0;
+                    if constexpr (sizeof(R) == 4) {
+                        reinterpret_cast<float4*>(F)[cell] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    } else {
+                        F[cell] = 0;
+                        F[nc + cell] = 0;
+                        if (D == 3) F[2 * nc + cell] = 0;
+                    }
                 }
                 const CellMoments<Q, R> mo = cell_moments<Q, R>(g[k], Fx, Fy, Fz, ginv);
                 cell_collide<Q, R>(g[k], mo, omega, Fx, Fy, Fz, gsc);
                 store_cell_flat<Q, ST>(fout, nc, cell, g[k],
                                        ST == ST_FP16 ? sr_seed(step, (long long)cell) : 0u);
-                if (WRITE_ALL || band) {
-                    mom[cell] = mo.drho;
-                    mom[nc + cell] = mo.ux;
-                    mom[2 * nc + cell] = mo.uy;
-                    if (D == 3) mom[3 * nc + cell] = mo.uz;
-                }
+                if (WRITE_ALL || band) put_moments<D, R>(mom, nc, cell, mo.drho, mo.ux, mo.uy, mo.uz);
                 if (!isfinite(mo.drho)) atomicOr(slots[slot].err, ERR_NONFINITE);
             }
             // clear the flags of the segments just read (after every lane of
@@ -327,78 +334,31 @@ __global__ void k_b_node_forces(const SlotDev* __restrict__ slots, const int2* _
     mesh_node_force(sd.q, nd.y, sd.entry_rec, sd.csr_ptr, sd.fp, sd.phi, nullptr, nullptr, sd.err);
 }
 
-// One warp per (slot, node): scatter-add into the slot's force density and
-// mark its fluid-cell segments.
+// One thread per (slot, node): spread into the slot's force density and mark
+// its band segments (as the single-simulation kernel, spread_node).
 template <int D, typename R>
-__global__ void k_b_spread(const SlotDev* __restrict__ slots, const int2* __restrict__ nodes,
-                           int nnodes)
+__global__ void __launch_bounds__(128)
+k_b_spread(const SlotDev* __restrict__ slots, const int2* __restrict__ nodes, int nnodes)
 {
-    constexpr int S = (D == 2) ? 16 : 64;
-    constexpr int PPL = (S + 31) / 32;
-    const int item = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (item >= nnodes) return;  // uniform per warp
-    const int2 nd = nodes[item];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nnodes) return;
+    const int2 nd = nodes[t];
     const SlotDev& sd = slots[nd.x];
-    const GridParams g = sd.g;
-    R wk;
-    int ik;
-    node_weights<D, R>(g, sd.q, nd.y, lane, wk, ik);
-    R phl = R(0);
-    if (lane < D) phl = (R)sd.phi[D * nd.y + lane];
-    R ph[3];
-    for (int k = 0; k < D; k++) ph[k] = __shfl_sync(0xffffffffu, phl, k);
-    R* F = (R*)sd.F;
-#pragma unroll
-    for (int p = 0; p < PPL; p++) {
-        const int s = lane + 32 * p;
-        R w;
-        long long row;
-        int ix;
-        const bool ok = point_of<D, R>(g, wk, ik, s < S ? s : 0, w, row, ix);
-        if (s < S && ok && w != R(0)) {
-            const long long cell = row * g.nx + ix;
-            for (int k = 0; k < D; k++) atomicAdd(&F[k * g.ncell + cell], ph[k] * w);
-            sd.flags[row * g.nseg_x + (ix >> 5)] = 1;
-        }
-    }
+    spread_node<D, R>(sd.g, sd.q, sd.phi, nd.y, (R*)sd.F, sd.flags);
 }
 
+// One thread per (slot, node): interpolate and advect (interp_node).
 template <int D, typename R>
-__global__ void k_b_interp(const SlotDev* __restrict__ slots, const int2* __restrict__ nodes,
-                           int nnodes)
+__global__ void __launch_bounds__(128)
+k_b_interp(const SlotDev* __restrict__ slots, const int2* __restrict__ nodes, int nnodes)
 {
-    constexpr int S = (D == 2) ? 16 : 64;
-    constexpr int PPL = (S + 31) / 32;
-    const int item = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (item >= nnodes) return;
-    const int2 nd = nodes[item];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nnodes) return;
+    const int2 nd = nodes[t];
     const SlotDev& sd = slots[nd.x];
-    const GridParams g = sd.g;
-    R wk;
-    int ik;
-    node_weights<D, R>(g, sd.q, nd.y, lane, wk, ik);
-    const R* mom = (const R*)sd.mom;
-    R acc[3] = {R(0), R(0), R(0)};
-#pragma unroll
-    for (int p = 0; p < PPL; p++) {
-        const int s = lane + 32 * p;
-        R w;
-        long long row;
-        int ix;
-        const bool ok = point_of<D, R>(g, wk, ik, s < S ? s : 0, w, row, ix);
-        if (s < S && ok) {
-            const long long cell = row * g.nx + ix;
-            for (int k = 0; k < D; k++) acc[k] += w * mom[(k + 1) * g.ncell + cell];
-        }
-    }
-    for (int k = 0; k < D; k++)
-        for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
-    if (lane < D) {
-        const R a = lane == 0 ? acc[0] : (lane == 1 ? acc[1] : acc[D == 3 ? 2 : 1]);
-        sd.q[D * nd.y + lane] += (double)a;
-    }
+    R acc[3];
+    interp_node<D, R>(sd.g, sd.q, (const R*)sd.mom, nd.y, acc);
+    for (int k = 0; k < D; k++) sd.q[D * nd.y + k] += (double)acc[k];
 }
 
 }  // namespace
@@ -454,7 +414,7 @@ static void launch_b_ib(int dim, int storage, int phase, const SlotDev* slots, c
                         int nnodes, const int2* faces, int nfaces, cudaStream_t s)
 {
     const int wb = 128;
-    const int warps_grid = (int)(((long long)nnodes * 32 + wb - 1) / wb);
+    const int node_grid = (nnodes + wb - 1) / wb;  // one thread per (slot, node)
     if (phase == 0) {  // nodal forces
         if (dim == 2) {
             k_b_forces_ring<<<(nnodes + 127) / 128, 128, 0, s>>>(slots, nodes, nnodes);
@@ -464,19 +424,19 @@ static void launch_b_ib(int dim, int storage, int phase, const SlotDev* slots, c
         }
     } else if (phase == 1) {  // spread
         if (storage == ST_FP64) {
-            if (dim == 2) k_b_spread<2, double><<<warps_grid, wb, 0, s>>>(slots, nodes, nnodes);
-            else k_b_spread<3, double><<<warps_grid, wb, 0, s>>>(slots, nodes, nnodes);
+            if (dim == 2) k_b_spread<2, double><<<node_grid, wb, 0, s>>>(slots, nodes, nnodes);
+            else k_b_spread<3, double><<<node_grid, wb, 0, s>>>(slots, nodes, nnodes);
         } else {
-            if (dim == 2) k_b_spread<2, float><<<warps_grid, wb, 0, s>>>(slots, nodes, nnodes);
-            else k_b_spread<3, float><<<warps_grid, wb, 0, s>>>(slots, nodes, nnodes);
+            if (dim == 2) k_b_spread<2, float><<<node_grid, wb, 0, s>>>(slots, nodes, nnodes);
+            else k_b_spread<3, float><<<node_grid, wb, 0, s>>>(slots, nodes, nnodes);
         }
     } else {  // interpolate + advect
         if (storage == ST_FP64) {
-            if (dim == 2) k_b_interp<2, double><<<warps_grid, wb, 0, s>>>(slots, nodes, nnodes);
-            else k_b_interp<3, double><<<warps_grid, wb, 0, s>>>(slots, nodes, nnodes);
+            if (dim == 2) k_b_interp<2, double><<<node_grid, wb, 0, s>>>(slots, nodes, nnodes);
+            else k_b_interp<3, double><<<node_grid, wb, 0, s>>>(slots, nodes, nnodes);
         } else {
-            if (dim == 2) k_b_interp<2, float><<<warps_grid, wb, 0, s>>>(slots, nodes, nnodes);
-            else k_b_interp<3, float><<<warps_grid, wb, 0, s>>>(slots, nodes, nnodes);
+            if (dim == 2) k_b_interp<2, float><<<node_grid, wb, 0, s>>>(slots, nodes, nnodes);
+            else k_b_interp<3, float><<<node_grid, wb, 0, s>>>(slots, nodes, nnodes);
         }
     }
 }
@@ -556,8 +516,9 @@ Layout slot_layout(int Q, int dim, size_t elt, size_t relt, long long ncell, lon
     };
     L.pop[0] = take((size_t)Q * ncell * elt);
     L.pop[1] = take((size_t)Q * ncell * elt);
-    L.mom = take((size_t)(1 + dim) * ncell * relt);
-    L.F = take((size_t)dim * ncell * relt);
+    const int storage = relt == 8 ? 0 : 1;
+    L.mom = take(moments_bytes(storage, dim, ncell));
+    L.F = take(force_bytes(storage, dim, ncell));
     (void)nfluid;
     L.flags = take((size_t)(ncell / rowlen) * (size_t)((rowlen + 31) / 32));
     L.err = take(sizeof(int));

@@ -112,6 +112,22 @@ struct ForceParams {
     const double* eref;
 };
 
+// Layout of the force density F and of the moments in device memory: in
+// FP32 compute precision one float4 per cell, F = (Fx, Fy, Fz, 0) and
+// moments = (drho, ux, uy, uz) (uz = 0 in 2D), so that spreading adds one
+// vector per stencil point and interpolation reads one; in FP64,
+// [component][cell] arrays (F: dim components, moments: 1 + dim).
+inline size_t force_bytes(int storage, int dim, long long ncell)
+{
+    return storage == 0 ? sizeof(double) * (size_t)dim * (size_t)ncell
+                        : sizeof(float) * 4 * (size_t)ncell;
+}
+inline size_t moments_bytes(int storage, int dim, long long ncell)
+{
+    return storage == 0 ? sizeof(double) * (size_t)(1 + dim) * (size_t)ncell
+                        : sizeof(float) * 4 * (size_t)ncell;
+}
+
 // Launch shape of the stream-collide kernel (chosen by the autotuner).
 struct Tuning {
     int variant = 1;            // 0: plain kernel; 1: pipelined kernel; 2: cell pairs along x;
@@ -122,6 +138,8 @@ struct Tuning {
     int ctas_per_sm = 2;        // pipelined kernel: resident CTAs per SM (1 or 2)
     int consumer_warps = 8;     // pipelined kernel: 8 (2 CTAs/SM), 16 or 24 (1 CTA/SM)
     long long wait_limit = 0;   // pipelined kernel: clock cycles a wait may take (0: ~2 s)
+    int ib_per_node = 0;        // 3D interfaces: 1 spreads / interpolates one thread per node
+                                // instead of by spatial groups of nodes
 };
 
 // Shape of the pipelined stream-collide launch (see lbm_pipe.cu).
@@ -220,6 +238,44 @@ void launch_spread(int storage, int dim, const double* q, const double* phi, int
 // qdot [N][dim] = sum u Delta; if advect, q += qdot.
 void launch_interp(int storage, int dim, double* q, const void* moments, int N, double* qdot,
                    bool advect, const GridParams& g, cudaStream_t s);
+
+// Spatial groups of 3D interface nodes (ib_groups.cu): nodes of one
+// GROUP_TILE^3 tile of the lattice, at most GROUP_NODES per group; the
+// grouped spread / interpolation hold a group's box of the lattice in shared
+// memory (box_cap cells).
+constexpr int GROUP_TILE = 8;
+constexpr int GROUP_NODES = 128;
+template <typename R>
+constexpr int box_cap() { return sizeof(R) == 4 ? 2048 : 1536; }
+struct NodeGroups {
+    int* tile_cnt = nullptr;   // [ntiles] nodes per tile (zero between regroups)
+    int* tile_off = nullptr;   // [ntiles] first list position of each tile
+    int* key = nullptr;        // [N] tile of each node
+    int* rank = nullptr;       // [N] position of each node within its tile
+    int* list = nullptr;       // [N] nodes ordered by tile
+    int2* desc = nullptr;      // [max_groups] (first list position, node count)
+    int* ngroups = nullptr;    // [1]
+    int ntiles = 0, max_groups = 0;
+};
+// Tiles of a lattice and the bound on the number of groups of N nodes.
+inline int group_tiles(const GridParams& g)
+{
+    return ((g.nx + GROUP_TILE - 1) / GROUP_TILE) * ((g.ny + GROUP_TILE - 1) / GROUP_TILE) *
+           ((g.nz + GROUP_TILE - 1) / GROUP_TILE);
+}
+inline int group_bound(int N, int ntiles)
+{
+    return (N + GROUP_NODES - 1) / GROUP_NODES + (N < ntiles ? N : ntiles);
+}
+void launch_regroup(const double* q, int N, const GridParams& g, const NodeGroups& ng,
+                    cudaStream_t s);
+constexpr int REGROUP_KERNELS = 3;
+void launch_spread_grouped(int storage, const double* q, const double* phi, const NodeGroups& ng,
+                           void* F, uint8_t* flags, const GridParams& g, int sm_count,
+                           cudaStream_t s);
+void launch_interp_grouped(int storage, double* q, const void* moments, const NodeGroups& ng,
+                           double* qdot, bool advect, const GridParams& g, int sm_count,
+                           cudaStream_t s);
 
 // Elastic reference of the interface at its current positions (see
 // ForceParams::eref).

@@ -90,104 +90,63 @@ void launch_forces(int dim, const double* q, int N, int M, const int* tri, const
 }
 
 // ------------------------------------------------------------------ A2 + A3 spread
-// One warp per node: weighted scatter-add of phi_j into the force density
-// (fire-and-forget atomics) and marking of the 32-cell row segments touched.
+// One thread per node (spread_node in ib_core.cuh): one vector atomic per
+// stencil point, the touched 32-cell row segments marked.  Measured against
+// one warp per node (lanes sharing the stencil points) on the 59 292-node
+// paper-scale mesh: 45 us against 44 us per step, so the simpler form stays.
 template <int D, typename R>
-__global__ void k_spread(const double* __restrict__ q, const double* __restrict__ phi, int N,
-                         R* __restrict__ F, uint8_t* __restrict__ flags, GridParams g)
+__global__ void __launch_bounds__(128)
+k_spread_t(const double* __restrict__ q, const double* __restrict__ phi, int N,
+           R* __restrict__ F, uint8_t* __restrict__ flags, GridParams g)
 {
-    constexpr int S = (D == 2) ? 16 : 64;
-    constexpr int PPL = (S + 31) / 32;
-    const int node = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (node >= N) return;  // uniform per warp
-    R wk;
-    int ik;
-    node_weights<D, R>(g, q, node, lane, wk, ik);
-    R phl = R(0);
-    if (lane < D) phl = (R)phi[D * node + lane];
-    R ph[3];
-    for (int k = 0; k < D; k++) ph[k] = __shfl_sync(0xffffffffu, phl, k);
-#pragma unroll
-    for (int p = 0; p < PPL; p++) {
-        const int s = lane + 32 * p;
-        R w;
-        long long row;
-        int ix;
-        const bool ok = point_of<D, R>(g, wk, ik, s < S ? s : 0, w, row, ix);
-        if (s < S && ok && w != R(0)) {
-            const long long cell = row * g.nx + ix;
-            for (int k = 0; k < D; k++) atomicAdd(&F[k * g.ncell + cell], ph[k] * w);
-            flags[row * g.nseg_x + (ix >> 5)] = 1;
-        }
-    }
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < N) spread_node<D, R>(g, q, phi, j, F, flags);
 }
 
 void launch_spread(int storage, int dim, const double* q, const double* phi, int N, void* F,
                    uint8_t* flags, const GridParams& g, cudaStream_t s)
 {
-    const int b = 128;
-    const long long threads = (long long)N * 32;
-    const int grid = (int)((threads + b - 1) / b);
-    if (grid == 0) return;
+    if (N <= 0) return;
+    const int b = 128, grid = (N + b - 1) / b;
     if (storage == ST_FP64) {
-        if (dim == 2) k_spread<2, double><<<grid, b, 0, s>>>(q, phi, N, (double*)F, flags, g);
-        else k_spread<3, double><<<grid, b, 0, s>>>(q, phi, N, (double*)F, flags, g);
+        if (dim == 2) k_spread_t<2, double><<<grid, b, 0, s>>>(q, phi, N, (double*)F, flags, g);
+        else k_spread_t<3, double><<<grid, b, 0, s>>>(q, phi, N, (double*)F, flags, g);
     } else {
-        if (dim == 2) k_spread<2, float><<<grid, b, 0, s>>>(q, phi, N, (float*)F, flags, g);
-        else k_spread<3, float><<<grid, b, 0, s>>>(q, phi, N, (float*)F, flags, g);
+        if (dim == 2) k_spread_t<2, float><<<grid, b, 0, s>>>(q, phi, N, (float*)F, flags, g);
+        else k_spread_t<3, float><<<grid, b, 0, s>>>(q, phi, N, (float*)F, flags, g);
     }
 }
 
 // ------------------------------------------------------------------ A5 + A6 interpolate, advect
-// One warp per node; lanes share the stencil points and reduce by shuffles.
+// One thread per node (interp_node in ib_core.cuh): 16 velocity reads in
+// flight per thread; on the 59 292-node mesh 16 us per step against 35 us
+// for one warp per node with two reads per lane and a shuffle reduction.
 template <int D, typename R>
-__global__ void k_interp(double* __restrict__ q, const R* __restrict__ mom, int N,
-                         double* __restrict__ qdot, int advect, GridParams g)
+__global__ void __launch_bounds__(128)
+k_interp_t(double* __restrict__ q, const R* __restrict__ mom, int N, double* __restrict__ qdot,
+           int advect, GridParams g)
 {
-    constexpr int S = (D == 2) ? 16 : 64;
-    constexpr int PPL = (S + 31) / 32;
-    const int node = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (node >= N) return;  // uniform per warp
-    R wk;
-    int ik;
-    node_weights<D, R>(g, q, node, lane, wk, ik);
-    R acc[3] = {R(0), R(0), R(0)};
-#pragma unroll
-    for (int p = 0; p < PPL; p++) {
-        const int s = lane + 32 * p;
-        R w;
-        long long row;
-        int ix;
-        const bool ok = point_of<D, R>(g, wk, ik, s < S ? s : 0, w, row, ix);
-        if (s < S && ok) {
-            const long long cell = row * g.nx + ix;
-            for (int k = 0; k < D; k++) acc[k] += w * mom[(k + 1) * g.ncell + cell];
-        }
-    }
-    for (int k = 0; k < D; k++)
-        for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
-    if (lane < D) {
-        const R a = lane == 0 ? acc[0] : (lane == 1 ? acc[1] : acc[D == 3 ? 2 : 1]);
-        if (qdot) qdot[D * node + lane] = (double)a;
-        if (advect) q[D * node + lane] += (double)a;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    R acc[3];
+    interp_node<D, R>(g, q, mom, j, acc);
+    for (int k = 0; k < D; k++) {
+        if (qdot) qdot[D * j + k] = (double)acc[k];
+        if (advect) q[D * j + k] += (double)acc[k];
     }
 }
 
 void launch_interp(int storage, int dim, double* q, const void* moments, int N, double* qdot,
                    bool advect, const GridParams& g, cudaStream_t s)
 {
-    const int b = 128;
-    const long long threads = (long long)N * 32;
-    const int grid = (int)((threads + b - 1) / b);
-    if (grid == 0) return;
+    if (N <= 0) return;
+    const int b = 128, grid = (N + b - 1) / b;
     if (storage == ST_FP64) {
-        if (dim == 2) k_interp<2, double><<<grid, b, 0, s>>>(q, (const double*)moments, N, qdot, advect, g);
-        else k_interp<3, double><<<grid, b, 0, s>>>(q, (const double*)moments, N, qdot, advect, g);
+        if (dim == 2) k_interp_t<2, double><<<grid, b, 0, s>>>(q, (const double*)moments, N, qdot, advect, g);
+        else k_interp_t<3, double><<<grid, b, 0, s>>>(q, (const double*)moments, N, qdot, advect, g);
     } else {
-        if (dim == 2) k_interp<2, float><<<grid, b, 0, s>>>(q, (const float*)moments, N, qdot, advect, g);
-        else k_interp<3, float><<<grid, b, 0, s>>>(q, (const float*)moments, N, qdot, advect, g);
+        if (dim == 2) k_interp_t<2, float><<<grid, b, 0, s>>>(q, (const float*)moments, N, qdot, advect, g);
+        else k_interp_t<3, float><<<grid, b, 0, s>>>(q, (const float*)moments, N, qdot, advect, g);
     }
 }
 

@@ -10,10 +10,15 @@
 
 namespace iblb {
 
+// x^k, k >= 0, by repeated squaring (FP64 products are costly on this GPU)
 __device__ __forceinline__ double ipow(double x, int k)
 {
     double r = 1.0;
-    for (int i = 0; i < k; i++) r *= x;
+    while (k > 0) {
+        if (k & 1) r *= x;
+        k >>= 1;
+        if (k) x *= x;
+    }
     return r;
 }
 
@@ -36,70 +41,136 @@ __device__ __forceinline__ R delta4r(R r)
     return R(0);
 }
 
-// One warp per node.  Lanes 0 .. D-1 split the node coordinate of their axis
-// into floor and fraction (FP64, once per axis); lanes 0 .. 4*D-1 then
-// evaluate the 1D weights of the node (axis = lane / 4, offset o = lane % 4,
-// distance to the stencil line = fraction + 1 - o) in the weight precision R,
-// with the lattice index of that stencil line (wrapped on periodic axes, -1
-// on a solid layer or outside the lattice along the wall axis).  Every lane
-// then forms the tensor-product weights of its stencil points from warp
-// shuffles.  All lanes must call it.
+// One thread per node: the node's 4 stencil lines per axis, their 1D
+// weights in the weight precision R (from an FP64 floor / fraction split of
+// the node coordinate, once per axis) and lattice indices (wrapped on periodic axes, -1 on
+// a solid layer or outside the lattice along the wall axis).  Returns false
+// for a diverged node (it touches nothing).
 template <int D, typename R>
-__device__ __forceinline__ void node_weights(const GridParams& g, const double* __restrict__ q,
-                                             int node, int lane, R& wk, int& ik)
+__device__ __forceinline__ bool node_lines(const GridParams& g, const double* __restrict__ q,
+                                           int node, R (&w)[3][4], int (&ix)[3][4])
 {
-    int base = 0, ok = 0;
-    R frac = R(0);
-    if (lane < D) {
-        const double qk = q[D * node + lane];
-        if (fabs(qk) < 1.0e9) {   // a diverged node touches nothing
-            const double fl = floor(qk);
-            base = (int)fl - 1;
-            frac = (R)(qk - fl);
-            ok = 1;
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+#pragma unroll
+        for (int o = 0; o < 4; o++) {
+            w[k][o] = (k < D) ? R(0) : (o == 0 ? R(1) : R(0));
+            ix[k][o] = (k < D) ? -1 : (o == 0 ? 0 : -1);
+        }
+#pragma unroll
+    for (int k = 0; k < D; k++) {
+        const double qk = q[D * node + k];
+        if (!(fabs(qk) < 1.0e9)) {
+            ok = false;
+            continue;
+        }
+        const double fl = floor(qk);
+        const int base = (int)fl - 1;
+        const R fr = (R)(qk - fl);
+        const int ext = k == 0 ? g.nx : (k == 1 ? g.ny : g.nz);
+#pragma unroll
+        for (int o = 0; o < 4; o++) {
+            w[k][o] = delta4r<R>(fr + (R)(1 - o));
+            const int i = base + o;
+            if (k == D - 1 && g.walls) {
+                ix[k][o] = (i <= 0 || i >= ext - 1) ? -1 : i;
+            } else {
+                const int r = i % ext;
+                ix[k][o] = r < 0 ? r + ext : r;
+            }
         }
     }
-    const int k = lane >> 2;
-    const int src = k < D ? k : 0;
-    const int b = __shfl_sync(0xffffffffu, base, src);
-    const R fr = __shfl_sync(0xffffffffu, frac, src);
-    const int okk = __shfl_sync(0xffffffffu, ok, src);
-    wk = R(0);
-    ik = -1;
-    if (lane < 4 * D && okk) {
-        const int o = lane & 3;
-        const int ext = k == 0 ? g.nx : (k == 1 ? g.ny : g.nz);
-        const int i = b + o;
-        wk = delta4r<R>(fr + (R)(1 - o));
-        if (k == D - 1 && g.walls) {
-            ik = (i <= 0 || i >= ext - 1) ? -1 : i;
-        } else {
-            const int r = i % ext;
-            ik = r < 0 ? r + ext : r;
+    return ok;
+}
+
+// Spread of node j by one thread: its 16 (2D) / 64 (3D) stencil points in
+// turn, one fire-and-forget vector addition per point in FP32 (a thread
+// never waits on its additions, so many are in flight per SM); the band
+// segments of the stencil rows are flagged once per row and segment.
+template <int D, typename R>
+__device__ __forceinline__ void spread_node(const GridParams& g, const double* __restrict__ q,
+                                            const double* __restrict__ phi, int j,
+                                            R* __restrict__ F, uint8_t* __restrict__ flags)
+{
+    R w[3][4];
+    int ix[3][4];
+    if (!node_lines<D, R>(g, q, j, w, ix)) return;
+    R ph[3] = {R(0), R(0), R(0)};
+    for (int k = 0; k < D; k++) ph[k] = (R)phi[D * j + k];
+    const int n2 = (D == 3) ? 4 : 1;
+    for (int o2 = 0; o2 < n2; o2++) {
+        const int i2 = ix[2][o2];
+        if (i2 < 0) continue;
+#pragma unroll
+        for (int o1 = 0; o1 < 4; o1++) {
+            const int i1 = ix[1][o1];
+            if (i1 < 0) continue;
+            const long long row = (long long)i2 * g.ny + i1;
+            const R w12 = w[1][o1] * w[2][o2];
+            int last_seg = -1;
+#pragma unroll
+            for (int o0 = 0; o0 < 4; o0++) {
+                const R ww = w[0][o0] * w12;
+                if (ww == R(0)) continue;
+                const int i0 = ix[0][o0];
+                const long long cell = row * g.nx + i0;
+                if constexpr (sizeof(R) == 4)
+                    atomicAdd(reinterpret_cast<float4*>(F) + cell,
+                              make_float4(ph[0] * ww, ph[1] * ww, D == 3 ? ph[2] * ww : 0.f, 0.f));
+                else
+                    for (int k = 0; k < D; k++) atomicAdd(&F[k * g.ncell + cell], ph[k] * ww);
+                if ((i0 >> 5) != last_seg) {
+                    last_seg = i0 >> 5;
+                    flags[row * g.nseg_x + last_seg] = 1;
+                }
+            }
         }
     }
 }
 
-// Weight and cell of stencil point s; all lanes must call it (shuffles).
+// Interpolated velocity at node j by one thread: the 16 / 64 velocity reads
+// of its stencil, 16 issued at a time (one 4 x 4 plane of points) before any
+// is used.
 template <int D, typename R>
-__device__ __forceinline__ bool point_of(const GridParams& g, R wk, int ik, int s, R& w,
-                                         long long& row, int& ix)
+__device__ __forceinline__ void interp_node(const GridParams& g, const double* __restrict__ q,
+                                            const R* __restrict__ mom, int j, R (&acc)[3])
 {
-    const int o0 = s & 3, o1 = (s >> 2) & 3, o2 = (s >> 4) & 3;
-    const R w0 = __shfl_sync(0xffffffffu, wk, o0);
-    const int i0 = __shfl_sync(0xffffffffu, ik, o0);
-    const R w1 = __shfl_sync(0xffffffffu, wk, 4 + o1);
-    const int i1 = __shfl_sync(0xffffffffu, ik, 4 + o1);
-    R w2 = R(1);
-    int i2 = 0;
-    if (D == 3) {
-        w2 = __shfl_sync(0xffffffffu, wk, 8 + o2);
-        i2 = __shfl_sync(0xffffffffu, ik, 8 + o2);
+    R w[3][4];
+    int ix[3][4];
+    acc[0] = acc[1] = acc[2] = R(0);
+    if (!node_lines<D, R>(g, q, j, w, ix)) return;
+    const int n2 = (D == 3) ? 4 : 1;
+    for (int o2 = 0; o2 < n2; o2++) {
+        const int i2 = ix[2][o2];
+        if (i2 < 0) continue;
+        R ux[16], uy[16], uz[16];
+#pragma unroll
+        for (int p = 0; p < 16; p++) {
+            const int o1 = p >> 2, o0 = p & 3;
+            const int i1 = ix[1][o1], i0 = ix[0][o0];
+            ux[p] = uy[p] = uz[p] = R(0);
+            if (i1 < 0) continue;
+            const long long cell = ((long long)i2 * g.ny + i1) * g.nx + i0;
+            if constexpr (sizeof(R) == 4) {
+                const float4 m = reinterpret_cast<const float4*>(mom)[cell];
+                ux[p] = m.y;
+                uy[p] = m.z;
+                uz[p] = m.w;
+            } else {
+                ux[p] = mom[g.ncell + cell];
+                uy[p] = mom[2 * g.ncell + cell];
+                if (D == 3) uz[p] = mom[3 * g.ncell + cell];
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < 16; p++) {
+            const R ww = w[0][p & 3] * w[1][p >> 2] * w[2][o2];
+            acc[0] += ww * ux[p];
+            acc[1] += ww * uy[p];
+            acc[2] += ww * uz[p];
+        }
     }
-    w = w0 * w1 * w2;
-    row = (long long)i2 * g.ny + i1;
-    ix = i0;
-    return i0 >= 0 && i1 >= 0 && i2 >= 0;
 }
 
 // ------------------------------------------------------------------ A1 pieces
@@ -191,21 +262,25 @@ __device__ __forceinline__ void ring_node_force(const double* __restrict__ q, in
     const double cx = q[2 * jp], cy = q[2 * jp + 1];
     const double s0x = bx - ax, s0y = by - ay;   // segment j-1
     const double s1x = cx - bx, s1y = cy - by;   // segment j
+    // FP64 divisions are costly on this GPU: one reciprocal per length,
+    // then products
     const double l0 = sqrt(s0x * s0x + s0y * s0y);
     const double l1 = sqrt(s1x * s1x + s1y * s1y);
-    double fsx = fp.sigma * (s1x / l1) - fp.sigma * (s0x / l0);
-    double fsy = fp.sigma * (s1y / l1) - fp.sigma * (s0y / l0);
+    const double il0 = 1.0 / l0, il1 = 1.0 / l1;
+    const double t0x = s0x * il0, t0y = s0y * il0, t1x = s1x * il1, t1y = s1y * il1;
+    double fsx = fp.sigma * t1x - fp.sigma * t0x;
+    double fsy = fp.sigma * t1y - fp.sigma * t0y;
     if (fp.eref) {
         const double la0 = l0 / fp.eref[jm], la1 = l1 / fp.eref[j];
         const double T0 = fp.Gs * (1.0 + fp.Cs) * la0 * (la0 * la0 - 1.0);
         const double T1 = fp.Gs * (1.0 + fp.Cs) * la1 * (la1 * la1 - 1.0);
-        fsx += T1 * (s1x / l1) - T0 * (s0x / l0);
-        fsy += T1 * (s1y / l1) - T0 * (s0y / l0);
+        fsx += T1 * t1x - T0 * t0x;
+        fsy += T1 * t1y - T0 * t0y;
     }
-    const double nsx = s0y / l0 + s1y / l1;
-    const double nsy = -s0x / l0 - s1x / l1;
-    const double nl = sqrt(nsx * nsx + nsy * nsy);
-    const double nhx = nsx / nl, nhy = nsy / nl;
+    const double nsx = t0y + t1y;
+    const double nsy = -t0x - t1x;
+    const double inl = 1.0 / sqrt(nsx * nsx + nsy * nsy);
+    const double nhx = nsx * inl, nhy = nsy * inl;
     const double ch = l0 + l1;
     double pi = 0.0;
     if (fp.wetting) {
@@ -213,8 +288,8 @@ __device__ __forceinline__ void ring_node_force(const double* __restrict__ q, in
         if (!(d > 0.0)) atomicOr(err, ERR_NODE_IN_WALL);
         pi = wetting_pi(fp, d);
     }
-    phi[2 * j] = fsx + (-ch * pi * nhx) / 2.0;
-    phi[2 * j + 1] = fsy + (-ch * pi * nhy) / 2.0;
+    phi[2 * j] = fsx - 0.5 * (ch * pi * nhx);
+    phi[2 * j + 1] = fsy - 0.5 * (ch * pi * nhy);
     if (nrm) {
         nrm[2 * j] = nhx;
         nrm[2 * j + 1] = nhy;
@@ -242,25 +317,36 @@ __device__ __forceinline__ void face_records(const double* __restrict__ q,
     const double ac[3] = {P[2][0] - P[0][0], P[2][1] - P[0][1], P[2][2] - P[0][2]};
     const double nf[3] = {ab[1] * ac[2] - ab[2] * ac[1], ab[2] * ac[0] - ab[0] * ac[2],
                           ab[0] * ac[1] - ab[1] * ac[0]};
-    const double nlen = sqrt(nf[0] * nf[0] + nf[1] * nf[1] + nf[2] * nf[2]);
-    const double inv = 1.0 / nlen;
+    // one reciprocal square root gives both the unit normal and the area
+    const double n2 = nf[0] * nf[0] + nf[1] * nf[1] + nf[2] * nf[2];
+    const double inv = rsqrt(n2);
     const double nu[3] = {nf[0] * inv, nf[1] * inv, nf[2] * inv};
-    const double area = 0.5 * nlen;
-    double fel[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    if (fp.eref) face_elastic_force(P[0], P[1], P[2], fp.eref + 5 * (long long)f, fp.Gs, fp.Cs, fel);
-    for (int v = 0; v < 3; v++) {
-        const double* nxt = P[(v + 1) % 3];
-        const double* prv = P[(v + 2) % 3];
-        const double e3[3] = {prv[0] - nxt[0], prv[1] - nxt[1], prv[2] - nxt[2]};
-        const double hs = 0.5 * fp.sigma;
-        double* r = rec + (long long)ENTRY_REC * entry_pos[3 * f + v];
-        r[0] = fel[v][0] - hs * (nu[1] * e3[2] - nu[2] * e3[1]);
-        r[1] = fel[v][1] - hs * (nu[2] * e3[0] - nu[0] * e3[2]);
-        r[2] = fel[v][2] - hs * (nu[0] * e3[1] - nu[1] * e3[0]);
-        r[3] = nu[0];
-        r[4] = nu[1];
-        r[5] = nu[2];
-        r[6] = area;
+    const double area = 0.5 * (n2 * inv);
+    // tension at corner v: -sigma/2 nu x (prev - next); the opposite edges
+    // of corners b and c are -ac and ab, and the three corner forces sum to
+    // zero, so corner a takes minus the other two
+    const double hs = 0.5 * fp.sigma;
+    const double hn[3] = {hs * nu[0], hs * nu[1], hs * nu[2]};
+    double ft[3][3];
+    ft[1][0] = hn[1] * ac[2] - hn[2] * ac[1];
+    ft[1][1] = hn[2] * ac[0] - hn[0] * ac[2];
+    ft[1][2] = hn[0] * ac[1] - hn[1] * ac[0];
+    ft[2][0] = ab[1] * hn[2] - ab[2] * hn[1];
+    ft[2][1] = ab[2] * hn[0] - ab[0] * hn[2];
+    ft[2][2] = ab[0] * hn[1] - ab[1] * hn[0];
+    for (int k = 0; k < 3; k++) ft[0][k] = -(ft[1][k] + ft[2][k]);
+    if (fp.eref) {
+        double fel[3][3];
+        face_elastic_force(P[0], P[1], P[2], fp.eref + 5 * (long long)f, fp.Gs, fp.Cs, fel);
+        for (int v = 0; v < 3; v++)
+            for (int k = 0; k < 3; k++) ft[v][k] += fel[v][k];
+    }
+    for (int v = 0; v < 3; v++) {  // 16-byte stores of the 64-byte record
+        double2* r = reinterpret_cast<double2*>(rec + (long long)ENTRY_REC * entry_pos[3 * f + v]);
+        r[0] = make_double2(ft[v][0], ft[v][1]);
+        r[1] = make_double2(ft[v][2], nu[0]);
+        r[2] = make_double2(nu[1], nu[2]);
+        r[3] = make_double2(area, 0.0);
     }
 }
 
@@ -275,23 +361,27 @@ __device__ __forceinline__ void mesh_node_force(const double* __restrict__ q, in
     double fs[3] = {0, 0, 0}, ns[3] = {0, 0, 0}, area = 0.0;
     const int e0 = csr_ptr[j], e1 = csr_ptr[j + 1];
     for (int e = e0; e < e1; e++) {
-        const double* r = rec + (long long)ENTRY_REC * e;
-        for (int k = 0; k < 3; k++) {
-            fs[k] += r[k];
-            ns[k] += r[3 + k];
-        }
-        area += r[6];
+        const double2* r = reinterpret_cast<const double2*>(rec + (long long)ENTRY_REC * e);
+        const double2 a = r[0], b = r[1], c = r[2], d = r[3];
+        fs[0] += a.x;
+        fs[1] += a.y;
+        fs[2] += b.x;
+        ns[0] += b.y;
+        ns[1] += c.x;
+        ns[2] += c.y;
+        area += d.x;
     }
-    const double nl = sqrt(ns[0] * ns[0] + ns[1] * ns[1] + ns[2] * ns[2]);
-    const double nh[3] = {ns[0] / nl, ns[1] / nl, ns[2] / nl};
+    const double inl = rsqrt(ns[0] * ns[0] + ns[1] * ns[1] + ns[2] * ns[2]);
+    const double nh[3] = {ns[0] * inl, ns[1] * inl, ns[2] * inl};
     double pi = 0.0;
     if (fp.wetting) {
         const double d = q[3 * j + 2] - fp.wall_plane;
         if (!(d > 0.0)) atomicOr(err, ERR_NODE_IN_WALL);
         pi = wetting_pi(fp, d);
     }
+    const double c = (area * pi) * (1.0 / 3.0);
     for (int k = 0; k < 3; k++) {
-        phi[3 * j + k] = fs[k] + (-area * pi * nh[k]) / 3.0;
+        phi[3 * j + k] = fs[k] - c * nh[k];
         if (nrm) nrm[3 * j + k] = nh[k];
     }
     if (chi) chi[j] = area;

@@ -167,16 +167,7 @@ k_stream_collide(const typename StorageT<ST>::S* __restrict__ fin,
         Fz = (R)p.body[2];
     }
 
-    if (band) {
-        Fx += F[cell];
-        Fy += F[nc + cell];
-        F[cell] = 0;
-        F[nc + cell] = 0;
-        if (D == 3) {
-            Fz += F[2 * nc + cell];
-            F[2 * nc + cell] = 0;
-        }
-    }
+    if (band) take_band_force<D, R>(F, nc, cell, Fx, Fy, Fz);
     CellMoments<Q, R> mo;
     if constexpr (ST == ST_FP16)
         mo = cell_moments<Q, R>(g, Fx, Fy, Fz, (R)p.inv_scale);
@@ -201,12 +192,7 @@ k_stream_collide(const typename StorageT<ST>::S* __restrict__ fin,
             store_cell<Q, ST, CS>(fout, nc, cell, g, p.scale, 0u);
     }
 
-    if (WRITE_ALL || band) {
-        mom[cell] = mo.drho;
-        mom[nc + cell] = mo.ux;
-        mom[2 * nc + cell] = mo.uy;
-        if (D == 3) mom[3 * nc + cell] = mo.uz;
-    }
+    if (WRITE_ALL || band) put_moments<D, R>(mom, nc, cell, mo.drho, mo.ux, mo.uy, mo.uz);
     if (!isfinite(mo.drho)) atomicOr(p.err, ERR_NONFINITE);
     if (lane == 0 && band) flags[seg] = 0;
 }
@@ -444,26 +430,24 @@ k_stream_collide2(const typename StorageT<ST>::S* __restrict__ fin,
     if (!active) return;
 
     float2 Fx = p2((float)p.body[0]), Fy = p2((float)p.body[1]), Fz = p2((float)p.body[2]);
-    if (band) {
-        Fx = add2(Fx, *reinterpret_cast<const float2*>(F + cell));
-        Fy = add2(Fy, *reinterpret_cast<const float2*>(F + nc + cell));
-        *reinterpret_cast<float2*>(F + cell) = p2(0.f);
-        *reinterpret_cast<float2*>(F + nc + cell) = p2(0.f);
-        if (D == 3) {
-            Fz = add2(Fz, *reinterpret_cast<const float2*>(F + 2 * nc + cell));
-            *reinterpret_cast<float2*>(F + 2 * nc + cell) = p2(0.f);
-        }
+    if (band) {  // float4 per cell: (Fx, Fy, Fz, 0)
+        float4* F4 = reinterpret_cast<float4*>(F);
+        const float4 a = F4[cell], b = F4[cell + 1];
+        Fx = add2(Fx, make_float2(a.x, b.x));
+        Fy = add2(Fy, make_float2(a.y, b.y));
+        if (D == 3) Fz = add2(Fz, make_float2(a.z, b.z));
+        F4[cell] = make_float4(0.f, 0.f, 0.f, 0.f);
+        F4[cell + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     const CellMoments2 mo = cell_moments2<Q>(g, Fx, Fy, Fz);
     cell_collide2<Q>(g, mo, (float)p.omega, Fx, Fy, Fz);
     const unsigned seed = ST == ST_FP16 ? sr_seed(step, cell) : 0u;
 #pragma unroll
     for (int i = 0; i < Q; i++) P::store2(fout, (long long)i * nc + cell, g[i], p.scale, sr_bits(seed, i));
-    if (WRITE_ALL || band) {
-        *reinterpret_cast<float2*>(mom + cell) = mo.drho;
-        *reinterpret_cast<float2*>(mom + nc + cell) = mo.ux;
-        *reinterpret_cast<float2*>(mom + 2 * nc + cell) = mo.uy;
-        if (D == 3) *reinterpret_cast<float2*>(mom + 3 * nc + cell) = mo.uz;
+    if (WRITE_ALL || band) {  // float4 per cell: (drho, ux, uy, uz)
+        float4* m4 = reinterpret_cast<float4*>(mom);
+        m4[cell] = make_float4(mo.drho.x, mo.ux.x, mo.uy.x, D == 3 ? mo.uz.x : 0.f);
+        m4[cell + 1] = make_float4(mo.drho.y, mo.ux.y, mo.uy.y, D == 3 ? mo.uz.y : 0.f);
     }
     if (!isfinite(mo.drho.x) || !isfinite(mo.drho.y)) atomicOr(p.err, ERR_NONFINITE);
     if ((lane & 15) == 0 && band) flags[seg] = 0;
@@ -608,22 +592,8 @@ k_stream_collide_y2(const typename StorageT<ST>::S* __restrict__ fin,
                            P::load(pl, (zb + (unsigned)syB) * (unsigned)nx + (unsigned)sx));
     }
     float2 Fx = p2(p.body_f[0]), Fy = p2(p.body_f[1]), Fz = p2(p.body_f[2]);
-    if (bandA) {
-        Fx.x += F[cellA];
-        Fy.x += F[nc + cellA];
-        Fz.x += F[2 * nc + cellA];
-        F[cellA] = 0.f;
-        F[nc + cellA] = 0.f;
-        F[2 * nc + cellA] = 0.f;
-    }
-    if (bandB && hasB) {
-        Fx.y += F[cellB];
-        Fy.y += F[nc + cellB];
-        Fz.y += F[2 * nc + cellB];
-        F[cellB] = 0.f;
-        F[nc + cellB] = 0.f;
-        F[2 * nc + cellB] = 0.f;
-    }
+    if (bandA) take_band_force<3, float>(F, nc, cellA, Fx.x, Fy.x, Fz.x);
+    if (bandB && hasB) take_band_force<3, float>(F, nc, cellB, Fx.y, Fy.y, Fz.y);
     const float ginv = (ST == ST_FP16) ? p.inv_scale : 1.0f;
     const float gsc = (ST == ST_FP16) ? p.scale : 1.0f;
     const CellMoments2 mo = cell_moments2<Q>(g, Fx, Fy, Fz, ginv);
@@ -647,18 +617,9 @@ k_stream_collide_y2(const typename StorageT<ST>::S* __restrict__ fin,
             if (hasB) pl[cellB] = g[i].y;
         }
     }
-    if (WRITE_ALL || bandA) {
-        mom[cellA] = mo.drho.x;
-        mom[nc + cellA] = mo.ux.x;
-        mom[2 * nc + cellA] = mo.uy.x;
-        mom[3 * nc + cellA] = mo.uz.x;
-    }
-    if (hasB && (WRITE_ALL || bandB)) {
-        mom[cellB] = mo.drho.y;
-        mom[nc + cellB] = mo.ux.y;
-        mom[2 * nc + cellB] = mo.uy.y;
-        mom[3 * nc + cellB] = mo.uz.y;
-    }
+    if (WRITE_ALL || bandA) put_moments<3, float>(mom, nc, cellA, mo.drho.x, mo.ux.x, mo.uy.x, mo.uz.x);
+    if (hasB && (WRITE_ALL || bandB))
+        put_moments<3, float>(mom, nc, cellB, mo.drho.y, mo.ux.y, mo.uy.y, mo.uz.y);
     if (!isfinite(mo.drho.x) || (hasB && !isfinite(mo.drho.y))) atomicOr(p.err, ERR_NONFINITE);
     if (lane == 0) {
         if (bandA) flags[rowA * (unsigned)p.g.nseg_x + (x >> 5)] = 0;
@@ -818,10 +779,19 @@ __global__ void k_unpack_moments(GridParams g, const R* __restrict__ mom, double
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
          c += (long long)gridDim.x * blockDim.x) {
         const bool solid = is_solid_cell(g, c);
-        if (rho) rho[c] = solid ? 0.0 : 1.0 + (double)mom[c];
+        R m[4];
+        if constexpr (sizeof(R) == 4) {
+            const float4 v = reinterpret_cast<const float4*>(mom)[c];
+            m[0] = v.x;
+            m[1] = v.y;
+            m[2] = v.z;
+            m[3] = v.w;
+        } else {
+            for (int k = 0; k <= g.dim; k++) m[k] = mom[k * ncell + c];
+        }
+        if (rho) rho[c] = solid ? 0.0 : 1.0 + (double)m[0];
         if (u)
-            for (int k = 0; k < g.dim; k++)
-                u[k * ncell + c] = solid ? 0.0 : (double)mom[(k + 1) * ncell + c];
+            for (int k = 0; k < g.dim; k++) u[k * ncell + c] = solid ? 0.0 : (double)m[k + 1];
     }
 }
 
@@ -840,8 +810,13 @@ __global__ void k_init_moments(GridParams g, R* mom)
 {
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
          c += (long long)gridDim.x * blockDim.x) {
-        mom[c] = is_solid_cell(g, c) ? R(-1) : R(0);
-        for (int k = 0; k < g.dim; k++) mom[(k + 1) * g.ncell + c] = R(0);
+        const R d0 = is_solid_cell(g, c) ? R(-1) : R(0);
+        if constexpr (sizeof(R) == 4) {
+            reinterpret_cast<float4*>(mom)[c] = make_float4(d0, 0.f, 0.f, 0.f);
+        } else {  // [1 + dim][cell]: only the components the buffer holds
+            mom[c] = d0;
+            for (int k = 0; k < g.dim; k++) mom[(k + 1) * g.ncell + c] = R(0);
+        }
     }
 }
 
@@ -857,7 +832,11 @@ __global__ void k_load_velocity(int dim, const double* __restrict__ u, R* mom, l
 {
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
          c += (long long)gridDim.x * blockDim.x)
-        for (int k = 0; k < dim; k++) mom[(k + 1) * ncell + c] = (R)u[k * ncell + c];
+        if constexpr (sizeof(R) == 4)
+            reinterpret_cast<float4*>(mom)[c] =
+                make_float4(0.f, (float)u[c], (float)u[ncell + c], dim == 3 ? (float)u[2 * ncell + c] : 0.f);
+        else
+            for (int k = 0; k < dim; k++) mom[(k + 1) * ncell + c] = (R)u[k * ncell + c];
 }
 
 void launch_load_velocity(int storage, int dim, const double* u, void* moments, long long ncell,
@@ -876,8 +855,16 @@ __global__ void k_unpack_force(GridParams g, const R* __restrict__ F, double b0,
          c += (long long)gridDim.x * blockDim.x) {
         const bool solid = is_solid_cell(g, c);
         const double body[3] = {b0, b1, b2};
-        for (int k = 0; k < g.dim; k++)
-            out[k * g.ncell + c] = solid ? 0.0 : (double)F[k * g.ncell + c] + body[k];
+        R f[3];
+        if constexpr (sizeof(R) == 4) {
+            const float4 v = reinterpret_cast<const float4*>(F)[c];
+            f[0] = v.x;
+            f[1] = v.y;
+            f[2] = v.z;
+        } else {
+            for (int k = 0; k < g.dim; k++) f[k] = F[k * g.ncell + c];
+        }
+        for (int k = 0; k < g.dim; k++) out[k * g.ncell + c] = solid ? 0.0 : (double)f[k] + body[k];
     }
 }
 

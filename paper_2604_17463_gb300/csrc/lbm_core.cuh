@@ -341,6 +341,46 @@ __device__ __forceinline__ void cell_collide(R* g, const CellMoments<Q, R>& m, R
     }
 }
 
+// Band force of a cell: added to (Fx, Fy, Fz) and cleared in the buffer
+// (float4 per cell in FP32, [component][cell] in FP64).
+template <int D, typename R>
+__device__ __forceinline__ void take_band_force(R* __restrict__ F, long long nc, long long cell,
+                                                R& Fx, R& Fy, R& Fz)
+{
+    if constexpr (sizeof(R) == 4) {
+        float4* F4 = reinterpret_cast<float4*>(F);
+        const float4 f = F4[cell];
+        Fx += f.x;
+        Fy += f.y;
+        if (D == 3) Fz += f.z;
+        F4[cell] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+        Fx += F[cell];
+        Fy += F[nc + cell];
+        F[cell] = 0;
+        F[nc + cell] = 0;
+        if (D == 3) {
+            Fz += F[2 * nc + cell];
+            F[2 * nc + cell] = 0;
+        }
+    }
+}
+
+// Moments of a cell (drho, u) into the moment buffer.
+template <int D, typename R>
+__device__ __forceinline__ void put_moments(R* __restrict__ mom, long long nc, long long cell,
+                                            R drho, R ux, R uy, R uz)
+{
+    if constexpr (sizeof(R) == 4) {
+        reinterpret_cast<float4*>(mom)[cell] = make_float4(drho, ux, uy, D == 3 ? uz : 0.f);
+    } else {
+        mom[cell] = drho;
+        mom[nc + cell] = ux;
+        mom[2 * nc + cell] = uy;
+        if (D == 3) mom[3 * nc + cell] = uz;
+    }
+}
+
 // ------------------------------------------------------------------ packed pairs
 // Two cells at once in packed FP32x2 arithmetic (Blackwell FFMA2 / FADD2 /
 // FMUL2): the same moments and pair-symmetric collision as above, with the

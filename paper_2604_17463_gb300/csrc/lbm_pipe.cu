@@ -375,26 +375,12 @@ k_sc_pipe(const typename StorageT<ST>::S* __restrict__ fin,
                 g[i] = T::load(pl, idx, p.inv_scale);
             }
             R Fx = param_body<R>(p, 0), Fy = param_body<R>(p, 1), Fz = param_body<R>(p, 2);
-            if (band) {
-                Fx += F[cell];
-                Fy += F[nc + cell];
-                F[cell] = 0;
-                F[nc + cell] = 0;
-                if (D == 3) {
-                    Fz += F[2 * nc + cell];
-                    F[2 * nc + cell] = 0;
-                }
-            }
+            if (band) take_band_force<D, R>(F, nc, cell, Fx, Fy, Fz);
             const CellMoments<Q, R> mo = cell_moments<Q, R>(g, Fx, Fy, Fz);
             cell_collide<Q, R>(g, mo, omega, Fx, Fy, Fz);
             store_cell<Q, ST, false>(fout, nc, cell, g, p.scale,
                                      ST == ST_FP16 ? sr_seed(step, cell) : 0u);
-            if (WRITE_ALL || band) {
-                mom[cell] = mo.drho;
-                mom[nc + cell] = mo.ux;
-                mom[2 * nc + cell] = mo.uy;
-                if (D == 3) mom[3 * nc + cell] = mo.uz;
-            }
+            if (WRITE_ALL || band) put_moments<D, R>(mom, nc, cell, mo.drho, mo.ux, mo.uy, mo.uz);
             if (!isfinite(mo.drho)) atomicOr(p.err, ERR_NONFINITE);
             if (lane == 0 && band) flags[seg] = 0;
         }

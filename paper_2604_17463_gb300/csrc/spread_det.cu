@@ -6,7 +6,7 @@
 // with atomics in ib.cu adds in whatever order the hardware serves them).
 //
 // Per step:
-//   1. k_det_bin     per node: the 1D delta weights (as in ib.cu), the
+//   1. k_det_bin     per node: the 1D delta weights (as node_lines), the
 //                    stencil origin o = floor(q) - 1 per axis, the node's
 //                    bin (a tile of DT^D stencil origins), a count per bin,
 //                    and the cell tiles its stencil touches (each appended
@@ -86,7 +86,7 @@ __global__ void k_det_bin(const DetSlot* __restrict__ slots, const int2* __restr
         }
         const double fl = floor(qk);
         o[k] = (int)fl - 1;
-        const R fr = (R)(qk - fl);  // as node_weights: FP64 split, weights in R
+        const R fr = (R)(qk - fl);  // as node_lines: FP64 split, weights in R
         for (int s = 0; s < 4; s++) wts[(long long)it * 12 + 4 * k + s] = delta4r<R>(fr + (R)(1 - s));
         org[3 * it + k] = o[k];
     }
@@ -283,7 +283,10 @@ k_det_gather(const DetSlot* __restrict__ slots, const int2* __restrict__ items,
         if (!touched) continue;
         const long long cell = ((long long)x[2] * g.ny + x[1]) * g.nx + x[0];
         R* F = (R*)d.F;
-        for (int k = 0; k < D; k++) F[(long long)k * g.ncell + cell] = acc[k];
+        if constexpr (sizeof(R) == 4)  // float4 per cell
+            reinterpret_cast<float4*>(F)[cell] = make_float4(acc[0], acc[1], D == 3 ? acc[2] : 0.f, 0.f);
+        else
+            for (int k = 0; k < D; k++) F[(long long)k * g.ncell + cell] = acc[k];
         if (d.flags_by_fluid) {
             d.flags[(cell - d.fluid_off) >> 5] = 1;
         } else {

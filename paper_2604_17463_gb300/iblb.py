@@ -71,6 +71,7 @@ class Tuning(ctypes.Structure):
         ("ctas_per_sm", ctypes.c_int),
         ("consumer_warps", ctypes.c_int),
         ("wait_limit_cycles", ctypes.c_longlong),
+        ("ib_per_node", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -300,9 +301,9 @@ def iblb_step_profiled(h, n_steps: int) -> np.ndarray:
 
 def iblb_set_tuning(h, variant: int, block_x: int = 128, streaming_stores: int = 0,
                     rows_per_tile: int = 2, ctas_per_sm: int = 2, consumer_warps: int = 8,
-                    wait_limit_cycles: int = 0):
+                    wait_limit_cycles: int = 0, ib_per_node: int = 0):
     t = Tuning(int(variant), int(block_x), int(streaming_stores), int(rows_per_tile),
-               int(ctas_per_sm), int(consumer_warps), int(wait_limit_cycles))
+               int(ctas_per_sm), int(consumer_warps), int(wait_limit_cycles), int(ib_per_node))
     _check(h, load().iblb_set_tuning(h, ctypes.byref(t)))
 
 
@@ -428,9 +429,9 @@ class Simulation:
         return qd
 
     def set_tuning(self, variant, block_x=128, streaming_stores=0, rows_per_tile=2,
-                   ctas_per_sm=2, consumer_warps=8, wait_limit_cycles=0):
+                   ctas_per_sm=2, consumer_warps=8, wait_limit_cycles=0, ib_per_node=0):
         iblb_set_tuning(self.h, variant, block_x, streaming_stores, rows_per_tile, ctas_per_sm,
-                        consumer_warps, wait_limit_cycles)
+                        consumer_warps, wait_limit_cycles, ib_per_node)
 
     def clear_faults(self):
         _check(self.h, load().iblb_clear_faults(self.h))
