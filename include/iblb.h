@@ -242,12 +242,17 @@ enum {
     IBLB_K_SPREAD = 1,
     IBLB_K_STREAM_COLLIDE = 2,
     IBLB_K_INTERP_ADVECT = 3,
-    IBLB_K_COUNT = 4
+    IBLB_K_BAND_CELLS = 4,  /* overlapped step: the second pass over the band cells */
+    IBLB_K_COUNT = 5
 };
 
 /* Run n_steps outside any CUDA graph with a CUDA event pair around every
  * kernel launch; kernel_ms[IBLB_K_COUNT] receives the summed device time of
- * each kernel (ms).  Synchronises. */
+ * each kernel (ms).  When iblb_step would overlap (iblb_tuning.step_overlap),
+ * the profiled steps run the same kernels one after the other on one
+ * stream: IBLB_K_STREAM_COLLIDE is then the bulk pass (every cell, body
+ * force only) and IBLB_K_BAND_CELLS the band pass; otherwise the band
+ * bucket is 0.  Synchronises. */
 iblb_status iblb_step_profiled(iblb_handle h, int n_steps, double* kernel_ms);
 
 /* Launch shape of the stream-collide kernel (results do not depend on it).
@@ -281,16 +286,31 @@ typedef struct {
                                      incomplete); 0 = about 2 s.  Copies in
                                      flight are always waited for (bounded by
                                      about 2 s) before the kernel exits. */
-    int ib_per_node;              /* 3D interfaces: 0 (default) spreads and
-                                     interpolates by spatial groups of nodes
-                                     (the nodes of one 8 x 8 x 8 tile of the
-                                     lattice; each group sums its stencils in,
-                                     or reads them from, a box of the lattice
-                                     in shared memory); 1 uses one thread per
-                                     node with one global addition per
-                                     stencil point.  Results differ only by
-                                     the order of the additions.  Not changed
-                                     by iblb_autotune. */
+    int ib_grouped;               /* 3D interfaces: 0 (default) spreads and
+                                     interpolates with one thread per node
+                                     and one global addition (read) per
+                                     stencil point; 1 by spatial groups of
+                                     nodes (the nodes of one 8 x 8 x 8 tile
+                                     of the lattice; a group sums its
+                                     stencils in, or reads them from, a box
+                                     of the lattice in shared memory).
+                                     Results differ only by the order of the
+                                     additions.  Not changed by
+                                     iblb_autotune. */
+    int step_overlap;             /* iblb_step with an interface: 0 (default)
+                                     overlaps on lattices of at least 2^20
+                                     cells, 1 always, 2 never.  Overlapped, a
+                                     step runs the stream-collide of every
+                                     cell with the body force only on one
+                                     stream while the nodal forces are
+                                     computed and spread on another, then
+                                     updates the cells of the flagged band
+                                     segments again, from the same sources,
+                                     with their force density (the same
+                                     arithmetic as one pass).  Not used with
+                                     a viscosity ratio, nor by
+                                     iblb_step_profiled.  Not changed by
+                                     iblb_autotune. */
 } iblb_tuning;
 
 /* Set / read the launch shape.  iblb_set_tuning synchronises. */

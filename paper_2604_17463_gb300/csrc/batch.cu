@@ -1143,7 +1143,8 @@ iblb_status batch_run(iblb_batch_s* b, int max_steps, int* n_completed, double* 
 {
     int completed = 0;
     int left = max_steps;
-    cudaEvent_t ev[IBLB_K_COUNT + 1] = {};
+    constexpr int PHASES = 4;  // forces, spread, stream-collide, interpolation
+    cudaEvent_t ev[PHASES + 1] = {};
     if (kernel_ms) {
         for (int k = 0; k < IBLB_K_COUNT; k++) kernel_ms[k] = 0.0;
         if (sc_bytes) *sc_bytes = 0.0;
@@ -1207,7 +1208,7 @@ iblb_status batch_run(iblb_batch_s* b, int max_steps, int* n_completed, double* 
                     st = bfail(b, IBLB_ECUDA, std::string("profiled step: ") + cudaGetErrorString(e));
                     break;
                 }
-                for (int q = 0; q < IBLB_K_COUNT; q++) {
+                for (int q = 0; q < PHASES; q++) {
                     float ms = 0.f;
                     cudaEventElapsedTime(&ms, ev[q], ev[q + 1]);
                     kernel_ms[q] += ms;

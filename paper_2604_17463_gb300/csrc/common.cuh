@@ -138,8 +138,10 @@ struct Tuning {
     int ctas_per_sm = 2;        // pipelined kernel: resident CTAs per SM (1 or 2)
     int consumer_warps = 8;     // pipelined kernel: 8 (2 CTAs/SM), 16 or 24 (1 CTA/SM)
     long long wait_limit = 0;   // pipelined kernel: clock cycles a wait may take (0: ~2 s)
-    int ib_per_node = 0;        // 3D interfaces: 1 spreads / interpolates one thread per node
-                                // instead of by spatial groups of nodes
+    int ib_grouped = 0;         // 3D interfaces: 1 spreads / interpolates by spatial groups of
+                                // nodes (ib_groups.cu) instead of one thread per node
+    int step_overlap = 0;       // 0: overlapped step on lattices of >= 2^20 cells; 1: always;
+                                // 2: never (see enqueue_step_overlapped)
 };
 
 // Shape of the pipelined stream-collide launch (see lbm_pipe.cu).
@@ -200,6 +202,16 @@ cudaError_t prepare_stream_collide_pipe(const SmemLimits& lim);
 cudaError_t launch_stream_collide_pipe(int Q, int storage, bool write_all, const void* fin,
                                        void* fout, void* moments, void* F, uint8_t* flags,
                                        const StreamParams& p, const PipeShape& ps, cudaStream_t s);
+
+// Band cells of the overlapped step (lbm.cu): after a bulk pass with
+// flags == nullptr, list the flagged segments (list: one int per segment
+// at most, count: one int, reset here) and update their cells again with
+// the force density and the moments; the flags are cleared.  Three
+// operations on stream s (a 4-byte memset and two kernels).
+void launch_band_cells(int Q, int storage, const void* fin, void* fout, void* moments, void* F,
+                       uint8_t* flags, int* list, int* count, const StreamParams& p,
+                       int sm_count, cudaStream_t s);
+constexpr int BAND_KERNELS = 2;
 
 // Host FP64 <-> device storage conversion of populations ([Q][ncell], f_i).
 void launch_pack_populations(int Q, int storage, const double* f, void* dst, long long ncell,

@@ -46,7 +46,11 @@ struct iblb_sim {
     SmemLimits smem{};
     ForceParams fp{};
     cudaStream_t stream = nullptr;
-    cudaStream_t cap = nullptr;  // private stream used only for graph capture
+    cudaStream_t cap = nullptr;  // private stream used only for graph capture (IB chain)
+    cudaStream_t cap2 = nullptr; // second capture stream: the bulk stream-collide pass
+    cudaEvent_t ev_top = nullptr, ev_band = nullptr, ev_bulk = nullptr;  // overlapped step
+    int* band_list = nullptr;    // flagged segments of the overlapped step [nflags]
+    int* band_count = nullptr;
     void* f[2] = {nullptr, nullptr};
     int cur = 0;
     void* mom = nullptr;       // drho [ncell], u [dim][ncell]
@@ -131,12 +135,23 @@ void clear_graphs(iblb_sim* h)
 
 int force_kernels(const iblb_sim* h) { return h->dim == 3 ? 2 : 1; }
 int spread_kernels(const iblb_sim* h) { return h->det ? DET_KERNELS : 1; }
-bool use_groups(const iblb_sim* h) { return h->grouped && !h->tune.ib_per_node; }
+bool use_groups(const iblb_sim* h) { return h->grouped && h->tune.ib_grouped; }
 int regroup_kernels(const iblb_sim* h) { return use_groups(h) ? REGROUP_KERNELS : 0; }
+// The overlapped step (enqueue_step_overlapped): with an interface, no
+// viscosity ratio, and (automatic mode) a lattice of at least 2^20 cells.
+bool overlapped(const iblb_sim* h)
+{
+    if (h->N == 0 || h->two_tau || h->tune.step_overlap == 2) return false;
+    return h->tune.step_overlap == 1 || h->g.ncell >= (1LL << 20);
+}
 int kernels_per_step(const iblb_sim* h)
 {
     return (h->N > 0 ? 2 + force_kernels(h) + spread_kernels(h) : 1) +
            ((h->two_tau && h->N > 0) ? 1 : 0);
+}
+int graph_kernels_per_step(const iblb_sim* h)
+{
+    return kernels_per_step(h) + (overlapped(h) ? BAND_KERNELS : 0);
 }
 
 // Spatial groups of the nodes for the grouped spread / interpolation of a
@@ -176,33 +191,37 @@ void enqueue_classify(iblb_sim* h, cudaStream_t s)
         launch_classify(h->dim, h->q, h->N, h->tri, h->M, h->g, h->col_cnt, h->col_z, h->err, s);
 }
 
-cudaError_t launch_sc(iblb_sim* h, cudaStream_t s, bool write_all)
+// Stream-collide of every fluid cell; bulk: without the band (flags
+// ignored, body force only), the pass the overlapped step redoes the band
+// cells after.
+cudaError_t launch_sc(iblb_sim* h, cudaStream_t s, bool write_all, bool bulk = false)
 {
+    uint8_t* flags = bulk ? nullptr : h->flags;
     // the step counter of the binary16 rounding follows the buffer parity
     StreamParams sp = h->sp;
     sp.rng_in = h->rng + h->cur;
     sp.rng_out = h->rng + (h->cur ^ 1);
     if (h->two_tau || h->moving) {  // the plain kernel carries tau(x) and moving walls
         launch_stream_collide(h->Q, h->storage, write_all, h->f[h->cur], h->f[h->cur ^ 1], h->mom,
-                              h->F, h->flags, sp, h->tune, s);
+                              h->F, flags, sp, h->tune, s);
         return cudaPeekAtLastError();
     }
     if (h->tune.variant == 2 && pair_kernel_ok(h->storage, h->g)) {
         launch_stream_collide_pairs(h->Q, h->storage, write_all, h->f[h->cur], h->f[h->cur ^ 1],
-                                    h->mom, h->F, h->flags, sp, h->tune, s);
+                                    h->mom, h->F, flags, sp, h->tune, s);
         return cudaPeekAtLastError();
     }
     if (h->tune.variant == 3 && rowpair_kernel_ok(h->Q, h->storage, h->g)) {
         launch_stream_collide_rowpairs(h->storage, write_all, h->f[h->cur], h->f[h->cur ^ 1],
-                                       h->mom, h->F, h->flags, sp, h->tune, s);
+                                       h->mom, h->F, flags, sp, h->tune, s);
         return cudaPeekAtLastError();
     }
     if (h->tune.variant == 1 && h->pipe_ok)
         return launch_stream_collide_pipe(h->Q, h->storage, write_all, h->f[h->cur],
-                                          h->f[h->cur ^ 1], h->mom, h->F, h->flags, sp,
+                                          h->f[h->cur ^ 1], h->mom, h->F, flags, sp,
                                           h->pipe, s);
     launch_stream_collide(h->Q, h->storage, write_all, h->f[h->cur], h->f[h->cur ^ 1], h->mom,
-                          h->F, h->flags, sp, h->tune, s);
+                          h->F, flags, sp, h->tune, s);
     return cudaPeekAtLastError();
 }
 
@@ -222,6 +241,36 @@ void enqueue_step(iblb_sim* h, cudaStream_t s, bool write_all, bool regroup)
     h->cur ^= 1;
 }
 
+// One overlapped time step under graph capture.  Stream b runs the bulk
+// stream-collide (every cell, body force only) while stream a computes the
+// nodal forces and spreads them; a then redoes the flagged band cells with
+// their force density (after the bulk pass, from the same sources), and
+// interpolates.  The bulk pass of the next step waits for this step's band
+// cells only, so it runs beside the interpolation and the next forces.  On
+// the last step (moments written everywhere) the bulk pass also waits for
+// the previous interpolation, which reads the moments it overwrites.
+void enqueue_step_overlapped(iblb_sim* h, cudaStream_t a, cudaStream_t b, bool write_all,
+                             bool regroup, bool first)
+{
+    if (first || write_all) cudaEventRecord(h->ev_top, a);
+    cudaStreamWaitEvent(b, (first || write_all) ? h->ev_top : h->ev_band, 0);
+    launch_sc(h, b, write_all, true);
+    cudaEventRecord(h->ev_bulk, b);
+    if (regroup) enqueue_regroup(h, a);
+    launch_forces(h->dim, h->q, h->N, h->M, h->tri, h->csr_ptr, h->entry_pos, h->entry_rec, h->fp,
+                  h->phi, nullptr, nullptr, h->err, a);
+    enqueue_spread(h, a);
+    cudaStreamWaitEvent(a, h->ev_bulk, 0);
+    StreamParams sp = h->sp;
+    sp.rng_in = h->rng + h->cur;
+    sp.rng_out = nullptr;
+    launch_band_cells(h->Q, h->storage, h->f[h->cur], h->f[h->cur ^ 1], h->mom, h->F, h->flags,
+                      h->band_list, h->band_count, sp, h->sm_count, a);
+    cudaEventRecord(h->ev_band, a);
+    enqueue_interp(h, a, h->mom, nullptr, true);
+    h->cur ^= 1;
+}
+
 iblb_status get_graph(iblb_sim* h, int steps, bool last, cudaGraphExec_t* out)
 {
     auto key = std::make_tuple(h->cur, steps, last ? 1 : 0);
@@ -234,13 +283,22 @@ iblb_status get_graph(iblb_sim* h, int steps, bool last, cudaGraphExec_t* out)
     CK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
     // the groups are refreshed once per chunk: positions move by a small
     // fraction of a cell in a chunk, and a group's box follows its nodes
-    for (int k = 0; k < steps; k++) enqueue_step(h, h->cap, last && k == steps - 1, k == 0);
+    const bool ov = overlapped(h);
+    for (int k = 0; k < steps; k++) {
+        const bool wa = last && k == steps - 1;
+        if (ov)
+            enqueue_step_overlapped(h, h->cap, h->cap2, wa, k == 0, k == 0);
+        else
+            enqueue_step(h, h->cap, wa, k == 0);
+    }
     cudaGraph_t graph;
     cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
     h->cur = cur0;
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
     cudaGraphExec_t exec;
-    e = cudaGraphInstantiate(&exec, graph, 0);
+    // kernel nodes keep the priorities of their capture streams: the IB chain
+    // is scheduled ahead of the bulk pass's waiting blocks
+    e = cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
     h->graphs[key] = exec;
@@ -445,8 +503,21 @@ iblb_status iblb_create(const iblb_config* cfg, void* cuda_stream, iblb_handle* 
         if ((e = cudaMemcpy(h->d_detslot, &ds, sizeof(DetSlot), cudaMemcpyHostToDevice)) != cudaSuccess)
             return bail(e, "deterministic spread");
     }
-    if ((e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking)) != cudaSuccess)
-        return bail(e, "stream");
+    {
+        // capture streams: the IB chain at the highest priority, the bulk
+        // stream-collide pass at the lowest
+        int lo = 0, hi = 0;
+        if ((e = cudaDeviceGetStreamPriorityRange(&lo, &hi)) != cudaSuccess ||
+            (e = cudaStreamCreateWithPriority(&h->cap, cudaStreamNonBlocking, hi)) != cudaSuccess ||
+            (e = cudaStreamCreateWithPriority(&h->cap2, cudaStreamNonBlocking, lo)) != cudaSuccess)
+            return bail(e, "stream");
+        for (cudaEvent_t* ev : {&h->ev_top, &h->ev_band, &h->ev_bulk})
+            if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess)
+                return bail(e, "events");
+        if ((e = cudaMalloc(&h->band_list, sizeof(int) * (size_t)h->nflags)) != cudaSuccess ||
+            (e = cudaMalloc(&h->band_count, sizeof(int))) != cudaSuccess)
+            return bail(e, "band list");
+    }
     // rest state: deviations are zero in every storage form
     cudaMemsetAsync(h->f[0], 0, pop_bytes, h->stream);
     cudaMemsetAsync(h->f[1], 0, pop_bytes, h->stream);
@@ -510,6 +581,11 @@ void iblb_destroy(iblb_handle h)
     free_dev(h->eref);
     free_groups(h);
     if (h->cap) cudaStreamDestroy(h->cap);
+    if (h->cap2) cudaStreamDestroy(h->cap2);
+    for (cudaEvent_t ev : {h->ev_top, h->ev_band, h->ev_bulk})
+        if (ev) cudaEventDestroy(ev);
+    free_dev(h->band_list);
+    free_dev(h->band_count);
     delete h;
 }
 
@@ -627,7 +703,7 @@ iblb_status iblb_step(iblb_handle h, int n_steps)
         iblb_status st = get_graph(h, k, last, &ge);
         if (st != IBLB_OK) return st;
         CK(h, cudaGraphLaunch(ge, h->stream));
-        g_launches += (long long)k * kernels_per_step(h) + (h->N > 0 ? regroup_kernels(h) : 0);
+        g_launches += (long long)k * graph_kernels_per_step(h) + (h->N > 0 ? regroup_kernels(h) : 0);
         h->cur ^= (k & 1);
         left -= k;
     }
@@ -895,15 +971,20 @@ iblb_status iblb_step_profiled(iblb_handle h, int n_steps, double* kernel_ms)
 {
     if (!h || !kernel_ms || n_steps < 0) return IBLB_EINVAL;
     for (int k = 0; k < IBLB_K_COUNT; k++) kernel_ms[k] = 0.0;
-    cudaEvent_t ev[IBLB_K_COUNT + 1];
+    // events around: forces, spread, stream-collide, band cells, interpolation
+    constexpr int NEV = 6;
+    const int bucket[NEV - 1] = {IBLB_K_FORCES, IBLB_K_SPREAD, IBLB_K_STREAM_COLLIDE,
+                                 IBLB_K_BAND_CELLS, IBLB_K_INTERP_ADVECT};
+    cudaEvent_t ev[NEV];
     for (auto& e : ev) CK(h, cudaEventCreate(&e));
+    const bool ov = overlapped(h);
     for (int t = 0; t < n_steps; t++) {
         const bool last = (t == n_steps - 1);
         const bool ib = h->N > 0;
-        cudaEventRecord(ev[0], h->stream);
         // groups refreshed every 32 steps (timed with the spread), as in the
         // graph-replayed chunks
         const bool regroup = ib && t % 32 == 0;
+        cudaEventRecord(ev[0], h->stream);
         if (ib)
             launch_forces(h->dim, h->q, h->N, h->M, h->tri, h->csr_ptr, h->entry_pos, h->entry_rec, h->fp, h->phi,
                           nullptr, nullptr, h->err, h->stream);
@@ -912,17 +993,25 @@ iblb_status iblb_step_profiled(iblb_handle h, int n_steps, double* kernel_ms)
         if (ib) enqueue_spread(h, h->stream);
         enqueue_classify(h, h->stream);
         cudaEventRecord(ev[2], h->stream);
-        launch_sc(h, h->stream, last);
+        launch_sc(h, h->stream, last, ov);
         cudaEventRecord(ev[3], h->stream);
-        if (ib) enqueue_interp(h, h->stream, h->mom, nullptr, true);
+        if (ov) {
+            StreamParams sp = h->sp;
+            sp.rng_in = h->rng + h->cur;
+            sp.rng_out = nullptr;
+            launch_band_cells(h->Q, h->storage, h->f[h->cur], h->f[h->cur ^ 1], h->mom, h->F,
+                              h->flags, h->band_list, h->band_count, sp, h->sm_count, h->stream);
+        }
         cudaEventRecord(ev[4], h->stream);
+        if (ib) enqueue_interp(h, h->stream, h->mom, nullptr, true);
+        cudaEventRecord(ev[5], h->stream);
         h->cur ^= 1;
-        g_launches += kernels_per_step(h) + (regroup ? regroup_kernels(h) : 0);
-        CK(h, cudaEventSynchronize(ev[4]));
-        for (int k = 0; k < IBLB_K_COUNT; k++) {
+        g_launches += graph_kernels_per_step(h) + (regroup ? regroup_kernels(h) : 0);
+        CK(h, cudaEventSynchronize(ev[5]));
+        for (int k = 0; k < NEV - 1; k++) {
             float ms = 0.f;
             CK(h, cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
-            kernel_ms[k] += ms;
+            kernel_ms[bucket[k]] += ms;
         }
     }
     for (auto& e : ev) cudaEventDestroy(e);
@@ -942,6 +1031,8 @@ iblb_status iblb_set_tuning(iblb_handle h, const iblb_tuning* t)
           (t->ctas_per_sm == 1 && (t->consumer_warps == 16 || t->consumer_warps == 24))))
         return fail(h, IBLB_EINVAL, "ctas_per_sm 2 with 8 consumer warps, or 1 with 16 or 24");
     if (t->wait_limit_cycles < 0) return fail(h, IBLB_EINVAL, "wait_limit_cycles must be >= 0");
+    if (t->step_overlap < 0 || t->step_overlap > 2)
+        return fail(h, IBLB_EINVAL, "step_overlap must be 0, 1 or 2");
     CK(h, cudaStreamSynchronize(h->stream));
     clear_graphs(h);
     Tuning tu;
@@ -952,7 +1043,8 @@ iblb_status iblb_set_tuning(iblb_handle h, const iblb_tuning* t)
     tu.ctas_per_sm = t->ctas_per_sm;
     tu.consumer_warps = t->consumer_warps;
     tu.wait_limit = t->wait_limit_cycles;
-    tu.ib_per_node = t->ib_per_node ? 1 : 0;
+    tu.ib_grouped = t->ib_grouped ? 1 : 0;
+    tu.step_overlap = t->step_overlap;
     apply_tuning(h, tu);
     return IBLB_OK;
 }
@@ -967,7 +1059,8 @@ iblb_status iblb_get_tuning(iblb_handle h, iblb_tuning* t)
     t->ctas_per_sm = h->tune.ctas_per_sm;
     t->consumer_warps = h->tune.consumer_warps;
     t->wait_limit_cycles = h->tune.wait_limit;
-    t->ib_per_node = h->tune.ib_per_node;
+    t->ib_grouped = h->tune.ib_grouped;
+    t->step_overlap = h->tune.step_overlap;
     return IBLB_OK;
 }
 
@@ -1001,7 +1094,8 @@ iblb_status iblb_autotune(iblb_handle h, int trials, iblb_tuning* chosen)
         }
     for (auto& c : cands) {  // the autotuner chooses the stream-collide shape only
         c.wait_limit = h->tune.wait_limit;
-        c.ib_per_node = h->tune.ib_per_node;
+        c.ib_grouped = h->tune.ib_grouped;
+        c.step_overlap = h->tune.step_overlap;
     }
     CK(h, cudaStreamSynchronize(h->stream));
     cudaEvent_t e0, e1;

@@ -2,14 +2,16 @@
 // interface by spatial groups of nodes, with the stencils of a group summed
 // in (or read from) a box of the lattice held in shared memory.
 //
-// Why: on a paper-scale mesh (59 292 nodes of a hemispherical cap) every
-// lattice cell near the surface receives ~50 stencil contributions, and a
-// spread with one global vector addition per stencil point is bound by the
-// L2 atomic rate.  Nodes of one 8 x 8 x 8 tile of the lattice are ~14x fewer
-// cells than stencil points: summing a group's stencils in shared memory and
-// adding each touched cell once to global memory cuts the global additions
-// by that factor; interpolation reads each cell of the box once instead of
-// once per stencil point.
+// On a paper-scale mesh (59 292 nodes of a hemispherical cap) every lattice
+// cell near the surface receives ~50 stencil contributions; the nodes of
+// one 8 x 8 x 8 tile touch ~14x fewer cells than they have stencil points,
+// so summing a group's stencils in shared memory adds each touched cell once
+// to global memory, and interpolation reads each cell of the box once.  On
+// GB300 both measured slower than one thread per node with global vector
+// additions (spread 61 against 44 us, interpolation 21 against 18 us per
+// step on that mesh): the per-node additions are fire-and-forget, while a
+// group waits on its box at every barrier and its shared-memory additions
+// collide or cost shuffles.  Selected with iblb_tuning.ib_grouped.
 //
 // Grouping (regroup, three kernels): each node is counted in the tile of its
 // cell (periodic axes wrapped), the tiles are scanned (one block) into node
@@ -119,7 +121,16 @@ struct GroupBox {
     int m[3];   // smallest offset
     int E[3];   // box extent
     int vol;    // cells; INT_MAX above the capacity, 0 for no node
+    float inv_e0, inv_e01;  // 1 / E0 and 1 / (E0 E1), for box_cell
 };
+
+// floor(c / d) for 0 <= c < 2048 from a correctly rounded 1 / d: the
+// relative error of (c + 1/2) (1/d) is below 2^-22, less than the distance
+// (1/2) / d of (c + 1/2) / d from the nearest integer.
+__device__ __forceinline__ int small_div(int c, float inv_d)
+{
+    return (int)(((float)c + 0.5f) * inv_d);
+}
 
 __device__ __forceinline__ int origin_of(const GridParams& g, double x, int k)
 {
@@ -186,15 +197,17 @@ __device__ __forceinline__ void group_box(const GridParams& g, const double* __r
     }
     bx.vol = (empty || vol > cap) ? INT_MAX : (int)vol;
     if (empty) bx.vol = 0;
+    bx.inv_e0 = empty ? 0.f : 1.0f / (float)bx.E[0];
+    bx.inv_e01 = empty ? 0.f : 1.0f / (float)(bx.E[0] * bx.E[1]);
     if (!valid) d[0] = INT_MIN;  // marks "no node" for the caller
 }
 
-// Global cell of box cell c (-1: outside the lattice along the wall axis).
+// Global cell of box cell c < vol <= 2048 (-1: outside the lattice along
+// the wall axis).
 __device__ __forceinline__ long long box_cell(const GridParams& g, const GroupBox& bx, int c)
 {
-    const int exy = bx.E[0] * bx.E[1];
-    const int lz = c / exy, rem = c - lz * exy;
-    const int ly = rem / bx.E[0], lx = rem - ly * bx.E[0];
+    const int lz = small_div(c, bx.inv_e01), rem = c - lz * (bx.E[0] * bx.E[1]);
+    const int ly = small_div(rem, bx.inv_e0), lx = rem - ly * bx.E[0];
     const int gx = wrap_mod(bx.r[0] + bx.m[0] + lx, g.nx);
     const int gy = wrap_mod(bx.r[1] + bx.m[1] + ly, g.ny);
     int gz = bx.r[2] + bx.m[2] + lz;
@@ -221,7 +234,25 @@ __device__ __forceinline__ void node_weights3(const double* __restrict__ q, int 
     }
 }
 
-// Spread: one CTA per group (persistent over the groups).
+// Select a[i], i in 0..3 (register arrays stay in registers).
+template <typename R>
+__device__ __forceinline__ R sel4(const R (&a)[4], int i)
+{
+    return i == 0 ? a[0] : (i == 1 ? a[1] : (i == 2 ? a[2] : a[3]));
+}
+
+__device__ __forceinline__ int wrap_once(int i, int n)
+{
+    while (i >= n) i -= n;
+    return i;
+}
+
+// Spread: one CTA per group (persistent over the groups).  Each thread
+// computes its node's 1D weights; then each warp adds the stencils of its
+// 32 nodes one node at a time, lane k taking stencil points k and k + 32
+// (x offset k & 3, y offset (k >> 2) & 3, z offset k >> 4 and 2 + (k >> 4)),
+// so the 32 shared-memory additions of an instruction go to 32 different
+// cells.  Then every touched cell of the box is added once to F.
 template <typename R>
 __global__ void __launch_bounds__(GROUP_NODES)
 k_spread_grouped(const double* __restrict__ q, const double* __restrict__ phi,
@@ -230,6 +261,8 @@ k_spread_grouped(const double* __restrict__ q, const double* __restrict__ phi,
     constexpr int cap = box_cap<R>();
     __shared__ R sb[3][cap];
     __shared__ int s_red[6][GROUP_NODES / 32];
+    const int lane = threadIdx.x & 31;
+    const int o0 = lane & 3, o1 = (lane >> 2) & 3, o2a = lane >> 4;
     const int ngroups = *ng.ngroups;
     for (int gi = blockIdx.x; gi < ngroups; gi += gridDim.x) {
         const int2 dsc = ng.desc[gi];
@@ -245,41 +278,57 @@ k_spread_grouped(const double* __restrict__ q, const double* __restrict__ phi,
             continue;
         }
         for (int c = threadIdx.x; c < bx.vol; c += GROUP_NODES) sb[0][c] = sb[1][c] = sb[2][c] = R(0);
-        __syncthreads();
+        // this thread's node: weights, force, box offsets and lattice origin
+        R w[3][4] = {};
+        R ph[3] = {R(0), R(0), R(0)};
+        int ob[3] = {0, 0, 0}, go[3] = {0, 0, 0};
         if (has) {
-            R w[3][4];
             node_weights3<R>(q, j, w);
-            const R p0 = (R)phi[3 * j], p1 = (R)phi[3 * j + 1], p2 = (R)phi[3 * j + 2];
-            const int bz = bx.r[2] + bx.m[2] + (d[2] - bx.m[2]);  // origin along z
-            const int ox = d[0] - bx.m[0], oy = d[1] - bx.m[1], oz = d[2] - bx.m[2];
-            const int gx0 = wrap_mod(bx.r[0] + d[0], g.nx);
-            for (int o2 = 0; o2 < 4; o2++) {
-                int gz = bz + o2;
+            for (int k = 0; k < 3; k++) {
+                ph[k] = (R)phi[3 * j + k];
+                ob[k] = d[k] - bx.m[k];
+            }
+            go[0] = wrap_mod(bx.r[0] + d[0], g.nx);
+            go[1] = wrap_mod(bx.r[1] + d[1], g.ny);
+            go[2] = (g.walls) ? bx.r[2] + d[2] : wrap_mod(bx.r[2] + d[2], g.nz);
+        }
+        __syncthreads();
+        const unsigned hasm = __ballot_sync(0xffffffffu, has);
+        for (int n = 0; n < 32; n++) {
+            if (!((hasm >> n) & 1u)) continue;
+            R s0[4], s1[4], s2[4];
+#pragma unroll
+            for (int o = 0; o < 4; o++) {
+                s0[o] = __shfl_sync(0xffffffffu, w[0][o], n);
+                s1[o] = __shfl_sync(0xffffffffu, w[1][o], n);
+                s2[o] = __shfl_sync(0xffffffffu, w[2][o], n);
+            }
+            const R p0 = __shfl_sync(0xffffffffu, ph[0], n);
+            const R p1 = __shfl_sync(0xffffffffu, ph[1], n);
+            const R p2 = __shfl_sync(0xffffffffu, ph[2], n);
+            const int bxo = __shfl_sync(0xffffffffu, ob[0], n);
+            const int byo = __shfl_sync(0xffffffffu, ob[1], n);
+            const int bzo = __shfl_sync(0xffffffffu, ob[2], n);
+            const int gx = wrap_once(__shfl_sync(0xffffffffu, go[0], n) + o0, g.nx);
+            const int gy = wrap_once(__shfl_sync(0xffffffffu, go[1], n) + o1, g.ny);
+            const int gz0 = __shfl_sync(0xffffffffu, go[2], n);
+            const R w0 = sel4(s0, o0), w1 = sel4(s1, o1);
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int o2 = o2a + 2 * h;
+                const R ww = w0 * (w1 * sel4(s2, o2));
+                int gz = gz0 + o2;
                 if (g.walls) {
                     if (gz <= 0 || gz >= g.nz - 1) continue;
                 } else {
-                    gz = wrap_mod(gz, g.nz);
+                    gz = wrap_once(gz, g.nz);
                 }
-#pragma unroll
-                for (int o1 = 0; o1 < 4; o1++) {
-                    const R w12 = w[1][o1] * w[2][o2];
-                    const int l0 = ((oz + o2) * bx.E[1] + (oy + o1)) * bx.E[0] + ox;
-                    const long long row = (long long)gz * g.ny + wrap_mod(bx.r[1] + d[1] + o1, g.ny);
-                    int last_seg = -1;
-#pragma unroll
-                    for (int o0 = 0; o0 < 4; o0++) {
-                        const R ww = w[0][o0] * w12;
-                        if (ww == R(0)) continue;
-                        atomicAdd(&sb[0][l0 + o0], p0 * ww);
-                        atomicAdd(&sb[1][l0 + o0], p1 * ww);
-                        atomicAdd(&sb[2][l0 + o0], p2 * ww);
-                        const int gx = wrap_mod(gx0 + o0, g.nx);
-                        if ((gx >> 5) != last_seg) {
-                            last_seg = gx >> 5;
-                            flags[row * g.nseg_x + last_seg] = 1;
-                        }
-                    }
-                }
+                if (ww == R(0)) continue;
+                const int l = ((bzo + o2) * bx.E[1] + (byo + o1)) * bx.E[0] + bxo + o0;
+                atomicAdd(&sb[0][l], p0 * ww);
+                atomicAdd(&sb[1][l], p1 * ww);
+                atomicAdd(&sb[2][l], p2 * ww);
+                flags[((long long)gz * g.ny + gy) * g.nseg_x + (gx >> 5)] = 1;
             }
         }
         __syncthreads();
@@ -301,14 +350,19 @@ k_spread_grouped(const double* __restrict__ q, const double* __restrict__ phi,
 }
 
 // Interpolation (+ advection): the group's box of velocities is read once
-// into shared memory, then each thread sums its node's 64 stencil points.
+// into shared memory (float4 (drho, ux, uy, uz) per cell in FP32, as the
+// moments are stored; three FP64 arrays otherwise), four cells per thread in
+// flight, then each thread sums its node's 64 stencil points from there.
 template <typename R>
 __global__ void __launch_bounds__(GROUP_NODES)
 k_interp_grouped(double* __restrict__ q, const R* __restrict__ mom, NodeGroups ng,
                  double* __restrict__ qdot, int advect, GridParams g)
 {
     constexpr int cap = box_cap<R>();
-    __shared__ R sb[3][cap];
+    constexpr bool F32 = sizeof(R) == 4;
+    __shared__ __align__(16) unsigned char smem[F32 ? cap * 16 : cap * 3 * 8];
+    float4* sb4 = reinterpret_cast<float4*>(smem);
+    double* sbd = reinterpret_cast<double*>(smem);
     __shared__ int s_red[6][GROUP_NODES / 32];
     const int ngroups = *ng.ngroups;
     for (int gi = blockIdx.x; gi < ngroups; gi += gridDim.x) {
@@ -323,24 +377,34 @@ k_interp_grouped(double* __restrict__ q, const R* __restrict__ mom, NodeGroups n
         if (bx.vol == INT_MAX) {
             if (has) interp_node<3, R>(g, q, mom, j, acc);
         } else {
-            for (int c = threadIdx.x; c < bx.vol; c += GROUP_NODES) {
-                const long long cell = box_cell(g, bx, c);
-                R ux = R(0), uy = R(0), uz = R(0);
-                if (cell >= 0) {
-                    if constexpr (sizeof(R) == 4) {
-                        const float4 m = reinterpret_cast<const float4*>(mom)[cell];
-                        ux = m.y;
-                        uy = m.z;
-                        uz = m.w;
-                    } else {
-                        ux = mom[g.ncell + cell];
-                        uy = mom[2 * g.ncell + cell];
-                        uz = mom[3 * g.ncell + cell];
-                    }
+            constexpr int U = 4;
+            for (int c0 = threadIdx.x; c0 < bx.vol; c0 += U * GROUP_NODES) {
+                long long cell[U];
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const int c = c0 + u * GROUP_NODES;
+                    cell[u] = c < bx.vol ? box_cell(g, bx, c) : -1;
                 }
-                sb[0][c] = ux;
-                sb[1][c] = uy;
-                sb[2][c] = uz;
+                if constexpr (F32) {
+                    float4 v[U];
+#pragma unroll
+                    for (int u = 0; u < U; u++)
+                        v[u] = cell[u] >= 0 ? reinterpret_cast<const float4*>(mom)[cell[u]]
+                                            : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int u = 0; u < U; u++)
+                        if (c0 + u * GROUP_NODES < bx.vol) sb4[c0 + u * GROUP_NODES] = v[u];
+                } else {
+                    double v[U][3];
+#pragma unroll
+                    for (int u = 0; u < U; u++)
+                        for (int k = 0; k < 3; k++)
+                            v[u][k] = cell[u] >= 0 ? mom[(k + 1) * g.ncell + cell[u]] : 0.0;
+#pragma unroll
+                    for (int u = 0; u < U; u++)
+                        if (c0 + u * GROUP_NODES < bx.vol)
+                            for (int k = 0; k < 3; k++) sbd[k * cap + c0 + u * GROUP_NODES] = v[u][k];
+                }
             }
             __syncthreads();
             if (has) {
@@ -353,9 +417,16 @@ k_interp_grouped(double* __restrict__ q, const R* __restrict__ mom, NodeGroups n
                         const int o1 = p >> 2, o0 = p & 3;
                         const int l = ((oz + o2) * bx.E[1] + (oy + o1)) * bx.E[0] + ox + o0;
                         const R ww = w[0][o0] * w[1][o1] * w[2][o2];
-                        acc[0] += ww * sb[0][l];
-                        acc[1] += ww * sb[1][l];
-                        acc[2] += ww * sb[2][l];
+                        if constexpr (F32) {
+                            const float4 m = sb4[l];
+                            acc[0] += ww * m.y;
+                            acc[1] += ww * m.z;
+                            acc[2] += ww * m.w;
+                        } else {
+                            acc[0] += ww * sbd[l];
+                            acc[1] += ww * sbd[cap + l];
+                            acc[2] += ww * sbd[2 * cap + l];
+                        }
                     }
                 }
             }

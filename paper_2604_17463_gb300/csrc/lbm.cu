@@ -25,13 +25,17 @@
 
 namespace iblb {
 
-template <int Q, int ST, bool WRITE_ALL, int BLOCK, bool CS, bool EXT = false>
-__global__ void __launch_bounds__(BLOCK)
-k_stream_collide(const typename StorageT<ST>::S* __restrict__ fin,
-                 typename StorageT<ST>::S* __restrict__ fout,
-                 typename StorageT<ST>::R* __restrict__ mom,
-                 typename StorageT<ST>::R* __restrict__ F,
-                 uint8_t* __restrict__ flags, const StreamParams p)
+// One cell (x, y, z) of the plain kernel: pull, moments, collision, store;
+// band != 0: the force density of the cell is added (and cleared) and the
+// moments written.  Shared by the plain kernel and the band-cell kernel of
+// the overlapped step.
+template <int Q, int ST, bool WRITE_ALL, bool CS, bool EXT>
+__device__ __forceinline__ void sc_cell(const typename StorageT<ST>::S* __restrict__ fin,
+                                        typename StorageT<ST>::S* __restrict__ fout,
+                                        typename StorageT<ST>::R* __restrict__ mom,
+                                        typename StorageT<ST>::R* __restrict__ F,
+                                        const StreamParams& p, int x, int y, int z, int band,
+                                        unsigned step)
 {
     using T = StorageT<ST>;
     using R = typename T::R;
@@ -40,28 +44,7 @@ k_stream_collide(const typename StorageT<ST>::S* __restrict__ fin,
     const int nx = p.g.nx, ny = p.g.ny;
     const long long nc = p.g.ncell;
     const int walls = p.g.walls;
-    const int woff = walls ? 1 : 0;
-
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    int y, z;
-    if (D == 2) {
-        y = blockIdx.y + woff;
-        z = 0;
-    } else {
-        y = blockIdx.y;
-        z = blockIdx.z + woff;
-    }
-    const int lane = threadIdx.x & 31;
     const long long row = (long long)z * ny + y;
-    const long long seg = row * p.g.nseg_x + (x >> 5);
-    int band = 0;
-    if (lane == 0 && (x >> 5) < p.g.nseg_x) band = flags[seg];
-    band = __shfl_sync(0xffffffffu, band, 0);
-    unsigned step = 0;
-    if constexpr (ST == ST_FP16)
-        step = sr_step(p.rng_in, p.rng_out,
-                       blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0);
-    if (x >= nx) return;
     const long long cell = row * nx + x;
 
     const int Lw = (D == 2) ? ny : p.g.nz;
@@ -194,6 +177,41 @@ k_stream_collide(const typename StorageT<ST>::S* __restrict__ fin,
 
     if (WRITE_ALL || band) put_moments<D, R>(mom, nc, cell, mo.drho, mo.ux, mo.uy, mo.uz);
     if (!isfinite(mo.drho)) atomicOr(p.err, ERR_NONFINITE);
+}
+
+// The plain kernel: one cell per thread, blocks of BLOCK cells along x.
+// flags == nullptr: every cell takes the body force only (the bulk pass of
+// the overlapped step; the band cells are redone by k_band_sc).
+template <int Q, int ST, bool WRITE_ALL, int BLOCK, bool CS, bool EXT = false>
+__global__ void __launch_bounds__(BLOCK)
+k_stream_collide(const typename StorageT<ST>::S* __restrict__ fin,
+                 typename StorageT<ST>::S* __restrict__ fout,
+                 typename StorageT<ST>::R* __restrict__ mom,
+                 typename StorageT<ST>::R* __restrict__ F,
+                 uint8_t* __restrict__ flags, const StreamParams p)
+{
+    constexpr int D = Stencil<Q>::D;
+    const int woff = p.g.walls ? 1 : 0;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y, z;
+    if (D == 2) {
+        y = blockIdx.y + woff;
+        z = 0;
+    } else {
+        y = blockIdx.y;
+        z = blockIdx.z + woff;
+    }
+    const int lane = threadIdx.x & 31;
+    const long long seg = ((long long)z * p.g.ny + y) * p.g.nseg_x + (x >> 5);
+    int band = 0;
+    if (lane == 0 && flags && (x >> 5) < p.g.nseg_x) band = flags[seg];
+    band = __shfl_sync(0xffffffffu, band, 0);
+    unsigned step = 0;
+    if constexpr (ST == ST_FP16)
+        step = sr_step(p.rng_in, p.rng_out,
+                       blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0);
+    if (x >= p.g.nx) return;
+    sc_cell<Q, ST, WRITE_ALL, CS, EXT>(fin, fout, mom, F, p, x, y, z, band, step);
     if (lane == 0 && band) flags[seg] = 0;
 }
 
@@ -266,6 +284,87 @@ static void launch_sc_t(bool write_all, const void* fin, void* fout, void* mom, 
             if (cs) launch_sc_b<Q, ST, 128, true>(write_all, fin, fout, mom, F, flags, p, s);
             else launch_sc_b<Q, ST, 128, false>(write_all, fin, fout, mom, F, flags, p, s);
             break;
+    }
+}
+
+// ------------------------------------------------------------------ band cells
+// Overlapped step: the bulk pass (any variant, flags == nullptr) updates
+// every cell with the body force only; k_band_list then lists the flagged
+// 32-cell row segments and k_band_sc updates their cells again from the same
+// sources, with the force density and the moments, one warp per segment.
+// The cell arithmetic is the plain kernel's, so the result is that of one
+// pass with the band cells forced.
+__global__ void k_band_list(const uint8_t* __restrict__ flags, long long nseg,
+                            int* __restrict__ list, int* __restrict__ count)
+{
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool set = s < nseg && flags[s] != 0;
+    const unsigned m = __ballot_sync(0xffffffffu, set);
+    if (m == 0u) return;
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(count, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (set) list[base + __popc(m & ((1u << lane) - 1u))] = (int)s;
+}
+
+template <int Q, int ST, bool EXT>
+__global__ void __launch_bounds__(128)
+k_band_sc(const typename StorageT<ST>::S* __restrict__ fin,
+          typename StorageT<ST>::S* __restrict__ fout, typename StorageT<ST>::R* __restrict__ mom,
+          typename StorageT<ST>::R* __restrict__ F, uint8_t* __restrict__ flags,
+          const int* __restrict__ list, const int* __restrict__ count, const StreamParams p)
+{
+    constexpr int D = Stencil<Q>::D;
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    const int n = *count;
+    unsigned step = 0;
+    if constexpr (ST == ST_FP16) step = sr_step(p.rng_in, nullptr, false);
+    for (int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < n; w += nw) {
+        const int s = list[w];
+        const int row = s / p.g.nseg_x;
+        const int x = (s - row * p.g.nseg_x) * 32 + lane;
+        const int y = (D == 2) ? row : row % p.g.ny;
+        const int z = (D == 2) ? 0 : row / p.g.ny;
+        if (x < p.g.nx) sc_cell<Q, ST, false, false, EXT>(fin, fout, mom, F, p, x, y, z, 1, step);
+        __syncwarp();
+        if (lane == 0) flags[s] = 0;
+    }
+}
+
+template <int Q, int ST>
+static void launch_band_t(const void* fin, void* fout, void* mom, void* F, uint8_t* flags,
+                          int* list, int* count, const StreamParams& p, int sm_count,
+                          cudaStream_t s)
+{
+    using T = StorageT<ST>;
+    const long long nseg = (long long)p.g.ny * p.g.nz * p.g.nseg_x;
+    cudaMemsetAsync(count, 0, sizeof(int), s);
+    k_band_list<<<(unsigned)((nseg + 255) / 256), 256, 0, s>>>(flags, nseg, list, count);
+    auto* a = (const typename T::S*)fin;
+    auto* b = (typename T::S*)fout;
+    auto* m = (typename T::R*)mom;
+    auto* f = (typename T::R*)F;
+    const int grid = 4 * sm_count;
+    if (p.moving)
+        k_band_sc<Q, ST, true><<<grid, 128, 0, s>>>(a, b, m, f, flags, list, count, p);
+    else
+        k_band_sc<Q, ST, false><<<grid, 128, 0, s>>>(a, b, m, f, flags, list, count, p);
+}
+
+void launch_band_cells(int Q, int storage, const void* fin, void* fout, void* moments, void* F,
+                       uint8_t* flags, int* list, int* count, const StreamParams& p,
+                       int sm_count, cudaStream_t s)
+{
+    if (Q == 9) {
+        if (storage == ST_FP64) launch_band_t<9, ST_FP64>(fin, fout, moments, F, flags, list, count, p, sm_count, s);
+        else if (storage == ST_FP32) launch_band_t<9, ST_FP32>(fin, fout, moments, F, flags, list, count, p, sm_count, s);
+        else launch_band_t<9, ST_FP16>(fin, fout, moments, F, flags, list, count, p, sm_count, s);
+    } else {
+        if (storage == ST_FP64) launch_band_t<19, ST_FP64>(fin, fout, moments, F, flags, list, count, p, sm_count, s);
+        else if (storage == ST_FP32) launch_band_t<19, ST_FP32>(fin, fout, moments, F, flags, list, count, p, sm_count, s);
+        else launch_band_t<19, ST_FP16>(fin, fout, moments, F, flags, list, count, p, sm_count, s);
     }
 }
 
@@ -355,7 +454,7 @@ k_stream_collide2(const typename StorageT<ST>::S* __restrict__ fin,
     // band flags: lanes 0-15 share one 32-cell segment, lanes 16-31 the next
     const long long seg = row * p.g.nseg_x + (x0 >> 5);
     int fl = 0;
-    if ((lane & 15) == 0 && active) fl = flags[seg];
+    if ((lane & 15) == 0 && active && flags) fl = flags[seg];
     const int band = __shfl_sync(0xffffffffu, fl, lane & 16);
     unsigned step = 0;
     if constexpr (ST == ST_FP16)
@@ -541,7 +640,7 @@ k_stream_collide_y2(const typename StorageT<ST>::S* __restrict__ fin,
     const unsigned rowA = (unsigned)z * (unsigned)ny + (unsigned)y0;
     const unsigned rowB = hasB ? rowA + 1u : rowA;
     int fa = 0, fb = 0;
-    if (lane == 0 && (x >> 5) < p.g.nseg_x) {
+    if (lane == 0 && flags && (x >> 5) < p.g.nseg_x) {
         fa = flags[rowA * (unsigned)p.g.nseg_x + (x >> 5)];
         fb = hasB ? flags[rowB * (unsigned)p.g.nseg_x + (x >> 5)] : 0;
     }

@@ -354,7 +354,7 @@ k_sc_pipe(const typename StorageT<ST>::S* __restrict__ fin,
             const long long cell = rowl * nx + x;
             const long long seg = rowl * p.g.nseg_x + (x >> 5);
             int band = 0;
-            if (lane == 0) band = flags[seg];
+            if (lane == 0 && flags) band = flags[seg];
             band = __shfl_sync(0xffffffffu, band, 0);
 
             R g[Q];

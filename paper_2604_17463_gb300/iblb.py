@@ -26,8 +26,8 @@ IBLB_OK = 0
 STATUS = {0: "IBLB_OK", 1: "IBLB_EINVAL", 2: "IBLB_ENOMEM", 3: "IBLB_ECUDA",
           4: "IBLB_ENODE_IN_WALL", 5: "IBLB_ENONFINITE", 6: "IBLB_ETIMEOUT", 7: "IBLB_EAGAIN",
           8: "IBLB_ECLASSIFY"}
-K_FORCES, K_SPREAD, K_STREAM_COLLIDE, K_INTERP_ADVECT, K_COUNT = 0, 1, 2, 3, 4
-KERNEL_NAMES = ["forces", "spread", "stream_collide", "interp_advect"]
+K_FORCES, K_SPREAD, K_STREAM_COLLIDE, K_INTERP_ADVECT, K_BAND_CELLS, K_COUNT = 0, 1, 2, 3, 4, 5
+KERNEL_NAMES = ["forces", "spread", "stream_collide", "interp_advect", "band_cells"]
 
 
 class IBLBError(RuntimeError):
@@ -71,7 +71,8 @@ class Tuning(ctypes.Structure):
         ("ctas_per_sm", ctypes.c_int),
         ("consumer_warps", ctypes.c_int),
         ("wait_limit_cycles", ctypes.c_longlong),
-        ("ib_per_node", ctypes.c_int),
+        ("ib_grouped", ctypes.c_int),
+        ("step_overlap", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -301,9 +302,10 @@ def iblb_step_profiled(h, n_steps: int) -> np.ndarray:
 
 def iblb_set_tuning(h, variant: int, block_x: int = 128, streaming_stores: int = 0,
                     rows_per_tile: int = 2, ctas_per_sm: int = 2, consumer_warps: int = 8,
-                    wait_limit_cycles: int = 0, ib_per_node: int = 0):
+                    wait_limit_cycles: int = 0, ib_grouped: int = 0, step_overlap: int = 0):
     t = Tuning(int(variant), int(block_x), int(streaming_stores), int(rows_per_tile),
-               int(ctas_per_sm), int(consumer_warps), int(wait_limit_cycles), int(ib_per_node))
+               int(ctas_per_sm), int(consumer_warps), int(wait_limit_cycles), int(ib_grouped),
+               int(step_overlap))
     _check(h, load().iblb_set_tuning(h, ctypes.byref(t)))
 
 
@@ -429,9 +431,10 @@ class Simulation:
         return qd
 
     def set_tuning(self, variant, block_x=128, streaming_stores=0, rows_per_tile=2,
-                   ctas_per_sm=2, consumer_warps=8, wait_limit_cycles=0, ib_per_node=0):
+                   ctas_per_sm=2, consumer_warps=8, wait_limit_cycles=0, ib_grouped=0,
+                   step_overlap=0):
         iblb_set_tuning(self.h, variant, block_x, streaming_stores, rows_per_tile, ctas_per_sm,
-                        consumer_warps, wait_limit_cycles, ib_per_node)
+                        consumer_warps, wait_limit_cycles, ib_grouped, step_overlap)
 
     def clear_faults(self):
         _check(self.h, load().iblb_clear_faults(self.h))

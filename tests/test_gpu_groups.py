@@ -1,9 +1,9 @@
-"""Grouped spreading and interpolation of 3D interfaces (Eq. 7-8), the
-default: the nodes of one 8 x 8 x 8 lattice tile form a group, whose
+"""Grouped spreading and interpolation of 3D interfaces (Eq. 7-8, tuning
+ib_grouped = 1): the nodes of one 8 x 8 x 8 lattice tile form a group, whose
 stencils are summed in (or read from) a box of the lattice in shared memory.
 
-Checked against the FP64 oracle and against the per-node kernels (tuning
-ib_per_node = 1):
+Checked against the FP64 oracle and against the per-node kernels (the
+default):
 - the force field and the band flags it leaves (FP64 to 1e-13, FP32 to 1e-6
   of the largest component);
 - the interpolated velocity;
@@ -72,8 +72,8 @@ def test_force_field_grouped(which, storage, tol):
     Fo, bad = o.force_field()
     g = iblb.Simulation.from_workload(wl, storage=storage)
     a = iblb.Simulation.from_workload(wl, storage=storage)
-    a.set_tuning(0, 128, ib_per_node=1)
-    assert g.tuning()["ib_per_node"] == 0 and a.tuning()["ib_per_node"] == 1
+    g.set_tuning(0, 128, ib_grouped=1)
+    assert g.tuning()["ib_grouped"] == 1 and a.tuning()["ib_grouped"] == 0
     Fg, Fa = g.force_field(), a.force_field()
     scale = np.max(np.abs(Fo[:3]))
     assert scale > 0
@@ -92,6 +92,7 @@ def test_interpolate_grouped(which, storage, tol):
     wl = CASES[which]()
     o = oracle_from_workload(wl)
     g = iblb.Simulation.from_workload(wl, storage=storage)
+    g.set_tuning(0, 128, ib_grouped=1)
     rng = np.random.default_rng(77)
     u = rng.normal(size=(3,) + o.shape) * 1e-3
     qo = o.interpolate(u)
@@ -106,6 +107,7 @@ def test_full_step_grouped_fp64(which, steps):
     wl = CASES[which]()
     o = oracle_from_workload(wl)
     g = iblb.Simulation.from_workload(wl)
+    g.set_tuning(0, 128, ib_grouped=1)
     assert o.step(steps) == 0
     g.step(steps)
     ro, uo, qo = o.fields()
@@ -134,6 +136,7 @@ def test_strong_shear_moves_nodes_between_regroups():
     steps = 70
     o = oracle_from_workload(wl)
     g = iblb.Simulation.from_workload(wl)
+    g.set_tuning(0, 128, ib_grouped=1)
     u = shear_u(o.shape, 0.012)
     o.set_equilibrium(u)
     g.set_equilibrium(u)
@@ -155,16 +158,18 @@ def test_grouped_matches_per_node_reduced_precision(storage):
     steps = 70
     g = iblb.Simulation.from_workload(wl, storage=storage)
     a = iblb.Simulation.from_workload(wl, storage=storage)
-    a.set_tuning(0, 128, ib_per_node=1)
-    g.set_tuning(0, 128)
+    a.set_tuning(0, 128)
+    g.set_tuning(0, 128, ib_grouped=1)
     g.step(steps)
     a.step(steps)
     rg, ug, qg = g.fields()
     ra, ua, qa = a.fields()
     m = fluid_mask(rg.shape, 3)
-    tol = 1e-5 if storage == iblb.FP32_DEV else 1e-3
+    # binary16: a different order of the FP32 force additions changes the
+    # stochastically rounded bits, and the runs drift apart by ~1e-3 of u
+    tol, qtol = (1e-5, 1e-6) if storage == iblb.FP32_DEV else (1e-3, 2e-5)
     assert rel_l2(ug[:, m], ua[:, m]) < tol
-    assert np.max(np.abs(qg - qa)) < 1e-6
+    assert np.max(np.abs(qg - qa)) < qtol
     g.close()
     a.close()
 
@@ -172,7 +177,7 @@ def test_grouped_matches_per_node_reduced_precision(storage):
 def test_autotune_keeps_the_ib_choice():
     wl = small_3d()
     g = iblb.Simulation.from_workload(wl, storage=iblb.FP32_DEV)
-    g.set_tuning(0, 128, ib_per_node=1)
+    g.set_tuning(0, 128, ib_grouped=1)
     t = g.autotune(trials=2)
-    assert t["ib_per_node"] == 1 and g.tuning()["ib_per_node"] == 1
+    assert t["ib_grouped"] == 1 and g.tuning()["ib_grouped"] == 1
     g.close()
