@@ -21,6 +21,7 @@ Other modes (--mode), each printing one JSON line of its own:
             the 4x-downscaled copy against the FP64 oracle
   spread3d  paper-scale 3D spreading (250x250x150 tau sweep, 300x300x250)
   shear     drop in shear flow at Re = 0.01, Ca = 0.05, R0 = 19 against Eq. 16
+  profile   small 3D cases for ncu captures (--case ib-cap | batch3d)
 """
 from __future__ import annotations
 
@@ -782,6 +783,52 @@ def run_spread3d_mode(args):
     return 0
 
 
+def run_profile_mode(args):
+    """Small cases of the 3D kernels for profiler captures (ncu): a few
+    profiled steps (no graphs), one JSON line of per-phase device times.
+      ib-cap   the paper-scale cap mesh (59 292 nodes, 118 580 faces) moved
+               into a 128 x 128 x 64 lattice, FP32 storage, per-node IB
+               kernels (--ib-grouped 1: grouped)
+      batch3d  the first 8 D3Q19 requests of the serving mix in one FP32
+               batch; the profiled steps run inside the NVTX range "run"
+    """
+    import dataclasses
+    import torch
+    from paper_2604_17463_gb300 import iblb
+    from paper_2604_17463_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    out = {"mode": "profile", "case": args.case}
+    if args.case == "ib-cap":
+        wl = W.spread3d_cap(0.59).work
+        wl = dataclasses.replace(wl, nx=128, ny=128, nz=64,
+                                 nodes=wl.nodes - [125.0 - 64.0, 125.0 - 64.0, 0.0])
+        sim = iblb.Simulation.from_workload(wl, storage=iblb.FP32_DEV)
+        sim.set_tuning(0, 64, ib_grouped=args.ib_grouped, step_overlap=2)
+        steps = 6
+        kms = sim.step_profiled(steps) / steps
+        out.update(nodes=int(wl.nodes.shape[0]), faces=int(wl.faces.shape[0]),
+                   lattice=[wl.nx, wl.ny, wl.nz])
+        sim.close()
+    else:
+        reqs = W.config5(count=2000, rate_per_s=1.0)
+        wls = [r.work for r in reqs if r.work.lattice == 19][:8]
+        b = iblb.Batch(iblb.D3Q19, iblb.FP32_DEV, 8 << 30, max_slots=16)
+        for w in wls:
+            if b.admit_workload(w, n_steps=100000) is None:
+                raise RuntimeError("batch3d: a request did not fit")
+        steps = 4
+        torch.cuda.nvtx.range_push("run")
+        _, kms, _ = b.run_profiled(steps)
+        b.sync()
+        torch.cuda.nvtx.range_pop()
+        kms = kms / steps
+        out.update(slots=len(wls), fluid_cells=int(sum(w.fluid_cells for w in wls)))
+        b.close()
+    out["phase_ms"] = {iblb.KERNEL_NAMES[k]: float(kms[k]) for k in range(iblb.K_COUNT)}
+    print(json.dumps(out))
+    return 0
+
+
 def run_kernel2d_mode(args):
     """Stream-collide alone on a plain D2Q9 lattice (--nx x --ny, walls, no
     interface), the launch shape from --tuning or the autotuner: the 2D
@@ -898,7 +945,7 @@ def main():
                     help="drops of the 256-drop set run one at a time for the sequential FP32 "
                          "baseline of the batch object")
     ap.add_argument("--mode", default="step", choices=["step", "batch", "serve", "shear", "spread2d", "spread3d",
-                             "kernel2d"],
+                             "kernel2d", "profile"],
                     help="step: the 3D workload (default); batch / serve: the batched "
                          "and served engines; spread2d / spread3d: the 2D precision sweep "
                          "and the paper-scale 3D spreading runs; shear: the drop in shear")
@@ -924,6 +971,9 @@ def main():
     ap.add_argument("--spread3d-t-mu", type=float, default=50.0,
                     help="spread3d: run length in capillary times")
     ap.add_argument("--shear-t-mu", type=float, default=12.0, help="shear: run length in t_mu")
+    ap.add_argument("--case", default="ib-cap", choices=["ib-cap", "batch3d"],
+                    help="profile: the small case to run (see run_profile_mode)")
+    ap.add_argument("--ib-grouped", type=int, default=0, help="profile ib-cap: grouped IB kernels")
     ap.add_argument("--tuning", default="",
                     help="fixed stream-collide launch shape 'variant,block_x,rows,ctas,warps' "
                          "instead of the autotuner (used for profiler runs)")
@@ -942,6 +992,8 @@ def main():
         return run_spread3d_mode(args)
     if args.mode == "kernel2d":
         return run_kernel2d_mode(args)
+    if args.mode == "profile":
+        return run_profile_mode(args)
     from paper_2604_17463_gb300 import workloads as W
     wl = W.config3()
     if args.impl == "reference":

@@ -92,11 +92,15 @@ constexpr int BT = 128;  // threads per stream-collide block
 // enough bytes are in flight per SM for the HBM bound), and the resident
 // blocks per SM asked of the register allocator; chosen by measurement on
 // the 256-drop set (D2Q9 FP32: 3 segments at 5 blocks beat 2 at 6 or 8 and
-// 4 at 4; D2Q9 binary16: 2 at 6).  FP64 is bound by its arithmetic.  A
-// slot's work items hold cpt segments, a multiple of this.
+// 4 at 4; D2Q9 binary16: 2 at 6) and on 40 D3Q19 requests of the serving
+// mix (FP32: 2 segments at 4 blocks with the next item prefetched, 1.89 ms
+// per launch, beat 1 segment at 5, 6, 7 or 8 blocks, 2.99-3.71 ms, and 2 at
+// 3 blocks, 1.96 ms; binary16: 2 at 4, 1.63 ms, beat 1 at 6 or 8, 2.5 ms).
+// FP64 is bound by its arithmetic.  A slot's work items hold cpt segments,
+// a multiple of this.
 constexpr int b_ilp_of(int Q, int ST)
 {
-    return ST == ST_FP64 ? 1 : (Q == 9 ? (ST == ST_FP32 ? 3 : 2) : (ST == ST_FP16 ? 2 : 1));
+    return ST == ST_FP64 ? 1 : (Q == 9 ? (ST == ST_FP32 ? 3 : 2) : 2);
 }
 template <int Q, int ST> struct BIlp {
     static constexpr int value = b_ilp_of(Q, ST);
@@ -104,7 +108,12 @@ template <int Q, int ST> struct BIlp {
 int b_ilp(int Q, int storage) { return b_ilp_of(Q, storage); }
 
 template <int Q, int ST> struct BMinBlocks {
-    static constexpr int value = ST == ST_FP64 ? (Q == 9 ? 5 : 4) : (Q == 9 ? (ST == ST_FP32 ? 5 : 6) : (ST == ST_FP32 ? 5 : 4));
+    static constexpr int value = ST == ST_FP64 ? (Q == 9 ? 5 : 4) : (Q == 9 ? (ST == ST_FP32 ? 5 : 6) : 4);
+};
+// The next work item is loaded while the current one is processed (D3Q19
+// FP32; measured slower for binary16).
+template <int Q, int ST> struct BPrefetch {
+    static constexpr bool value = Q == 19 && ST == ST_FP32;
 };
 
 // One stream-collide work item: cpt consecutive 32-cell segments x0 ..
@@ -174,8 +183,17 @@ k_b_stream_collide(const SlotDev* __restrict__ slots, const BItem* __restrict__ 
     const int wid = blockIdx.x * (BT / 32) + (threadIdx.x >> 5);
     if (wid >= nitems) return;
 
+    constexpr bool PF = BPrefetch<Q, ST>::value;
+    BItemRegs nxt;
+    if constexpr (PF) nxt = load_item(items, wid);
     for (int it = wid; it < nitems; it += nwarps) {
-        const BItemRegs item = load_item(items, it);
+        BItemRegs item;
+        if constexpr (PF) {
+            item = nxt;
+            if (it + nwarps < nitems) nxt = load_item(items, it + nwarps);
+        } else {
+            item = load_item(items, it);
+        }
         const int cur = item.e.w ^ par;  // cur_base ^ parity
         const S* __restrict__ fin =
             (const S*)(cur ? ptr_of(item.a.z, item.a.w) : ptr_of(item.a.x, item.a.y));
