@@ -21,7 +21,7 @@ Other modes (--mode), each printing one JSON line of its own:
             the 4x-downscaled copy against the FP64 oracle
   spread3d  paper-scale 3D spreading (250x250x150 tau sweep, 300x300x250)
   shear     drop in shear flow at Re = 0.01, Ca = 0.05, R0 = 19 against Eq. 16
-  profile   small 3D cases for ncu captures (--case ib-cap | batch3d)
+  profile   small cases for ncu captures (--case ib-cap | batch3d | batch2d | step3d)
 """
 from __future__ import annotations
 
@@ -791,6 +791,12 @@ def run_profile_mode(args):
                kernels (--ib-grouped 1: grouped)
       batch3d  the first 8 D3Q19 requests of the serving mix in one FP32
                batch; the profiled steps run inside the NVTX range "run"
+      batch2d  the 256 D2Q9 drops of the batched workload in one FP32 batch,
+               likewise inside the NVTX range "run"
+      step3d   the 3D benchmark drop at half the lattice (128 x 128 x 64,
+               R = 20, 2 562 nodes), FP32, the overlapped step's kernels
+               (bulk pass with the launch shape of --tuning, default the
+               x-pair kernel, then the band pass)
     """
     import dataclasses
     import torch
@@ -809,10 +815,25 @@ def run_profile_mode(args):
         out.update(nodes=int(wl.nodes.shape[0]), faces=int(wl.faces.shape[0]),
                    lattice=[wl.nx, wl.ny, wl.nz])
         sim.close()
+    elif args.case == "step3d":
+        nodes, faces = W.icosphere(4, 20.0, (64.0 + 0.31, 64.0 - 0.22, W.WALL_PLANE + 22.0))
+        wl = W.Workload("step3d_128x128x64", 19, 128, 128, 64, 0.8, 1e-3, 1.0, 75.0, 9, 3, 100,
+                        nodes, faces)
+        sim = iblb.Simulation.from_workload(wl, storage=iblb.FP32_DEV)
+        v, bx, rows, ctas, ncw = (int(x) for x in (args.tuning or "2,128,2,2,8").split(","))
+        sim.set_tuning(v, bx, 0, rows, ctas, ncw, step_overlap=1)
+        steps = 6
+        kms = sim.step_profiled(steps) / steps
+        out.update(nodes=int(nodes.shape[0]), lattice=[wl.nx, wl.ny, wl.nz],
+                   tuning=sim.tuning(), fluid_cells=int(sim.fluid_cells))
+        sim.close()
     else:
-        reqs = W.config5(count=2000, rate_per_s=1.0)
-        wls = [r.work for r in reqs if r.work.lattice == 19][:8]
-        b = iblb.Batch(iblb.D3Q19, iblb.FP32_DEV, 8 << 30, max_slots=16)
+        if args.case == "batch2d":
+            wls, lat = W.config4(), iblb.D2Q9
+        else:
+            reqs = W.config5(count=2000, rate_per_s=1.0)
+            wls, lat = [r.work for r in reqs if r.work.lattice == 19][:8], iblb.D3Q19
+        b = iblb.Batch(lat, iblb.FP32_DEV, 8 << 30, max_slots=len(wls) + 8)
         for w in wls:
             if b.admit_workload(w, n_steps=100000) is None:
                 raise RuntimeError("batch3d: a request did not fit")
@@ -971,7 +992,7 @@ def main():
     ap.add_argument("--spread3d-t-mu", type=float, default=50.0,
                     help="spread3d: run length in capillary times")
     ap.add_argument("--shear-t-mu", type=float, default=12.0, help="shear: run length in t_mu")
-    ap.add_argument("--case", default="ib-cap", choices=["ib-cap", "batch3d"],
+    ap.add_argument("--case", default="ib-cap", choices=["ib-cap", "batch3d", "batch2d", "step3d"],
                     help="profile: the small case to run (see run_profile_mode)")
     ap.add_argument("--ib-grouped", type=int, default=0, help="profile ib-cap: grouped IB kernels")
     ap.add_argument("--tuning", default="",

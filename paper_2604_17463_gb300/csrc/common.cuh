@@ -96,9 +96,6 @@ struct StreamParams {
     unsigned* rng_out;
     float scale, inv_scale;  // binary16 storage scale (1 for other storage)
     int* err;
-    // bulk pass of the overlapped step, plain kernel: 32-cell segments to
-    // leave to the band pass (null: none)
-    const uint8_t* skip;
 };
 
 struct ForceParams {
@@ -207,16 +204,13 @@ cudaError_t launch_stream_collide_pipe(int Q, int storage, bool write_all, const
                                        const StreamParams& p, const PipeShape& ps, cudaStream_t s);
 
 // Band cells of the overlapped step (lbm.cu): after a bulk pass with
-// flags == nullptr (which left out the segments in `skip`, plain kernel
-// only), list the segments flagged or skipped (list: one int per segment at
-// most, count: one int, reset here) and update their cells from the same
-// sources: flagged ones with the force density and the moments, skipped
-// ones with the body force (moments too when write_all).  Afterwards skip =
-// this step's flags (the next bulk pass leaves those out) and the flags are
-// clear.  Three operations on stream s (a 4-byte memset and two kernels).
-void launch_band_cells(int Q, int storage, bool write_all, const void* fin, void* fout,
-                       void* moments, void* F, uint8_t* flags, uint8_t* skip, int* list,
-                       int* count, const StreamParams& p, int sm_count, cudaStream_t s);
+// flags == nullptr, list the flagged segments (list: one int per segment at
+// most) and update their cells again with the force density and the
+// moments; the flags are cleared.  count: one int, reset here.  Three
+// operations on stream s (a 4-byte memset and two kernels).
+void launch_band_cells(int Q, int storage, const void* fin, void* fout, void* moments, void* F,
+                       uint8_t* flags, int* list, int* count, const StreamParams& p,
+                       int sm_count, cudaStream_t s);
 constexpr int BAND_KERNELS = 2;
 
 // Host FP64 <-> device storage conversion of populations ([Q][ncell], f_i).

@@ -51,7 +51,6 @@ struct iblb_sim {
     cudaEvent_t ev_top = nullptr, ev_band = nullptr, ev_bulk = nullptr;  // overlapped step
     int* band_list = nullptr;    // flagged segments of the overlapped step [nflags]
     int* band_count = nullptr;
-    uint8_t* skip = nullptr;     // segments the next bulk pass leaves to the band pass [nflags]
     void* f[2] = {nullptr, nullptr};
     int cur = 0;
     void* mom = nullptr;       // drho [ncell], u [dim][ncell]
@@ -200,7 +199,6 @@ cudaError_t launch_sc(iblb_sim* h, cudaStream_t s, bool write_all, bool bulk = f
     uint8_t* flags = bulk ? nullptr : h->flags;
     // the step counter of the binary16 rounding follows the buffer parity
     StreamParams sp = h->sp;
-    sp.skip = bulk ? h->skip : nullptr;  // read by the plain kernel only
     sp.rng_in = h->rng + h->cur;
     sp.rng_out = h->rng + (h->cur ^ 1);
     if (h->two_tau || h->moving) {  // the plain kernel carries tau(x) and moving walls
@@ -266,8 +264,8 @@ void enqueue_step_overlapped(iblb_sim* h, cudaStream_t a, cudaStream_t b, bool w
     StreamParams sp = h->sp;
     sp.rng_in = h->rng + h->cur;
     sp.rng_out = nullptr;
-    launch_band_cells(h->Q, h->storage, write_all, h->f[h->cur], h->f[h->cur ^ 1], h->mom, h->F,
-                      h->flags, h->skip, h->band_list, h->band_count, sp, h->sm_count, a);
+    launch_band_cells(h->Q, h->storage, h->f[h->cur], h->f[h->cur ^ 1], h->mom, h->F, h->flags,
+                      h->band_list, h->band_count, sp, h->sm_count, a);
     cudaEventRecord(h->ev_band, a);
     enqueue_interp(h, a, h->mom, nullptr, true);
     h->cur ^= 1;
@@ -517,10 +515,8 @@ iblb_status iblb_create(const iblb_config* cfg, void* cuda_stream, iblb_handle* 
             if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess)
                 return bail(e, "events");
         if ((e = cudaMalloc(&h->band_list, sizeof(int) * (size_t)h->nflags)) != cudaSuccess ||
-            (e = cudaMalloc(&h->band_count, sizeof(int))) != cudaSuccess ||
-            (e = cudaMalloc(&h->skip, (size_t)h->nflags)) != cudaSuccess)
+            (e = cudaMalloc(&h->band_count, sizeof(int))) != cudaSuccess)
             return bail(e, "band list");
-        cudaMemsetAsync(h->skip, 0, (size_t)h->nflags, h->stream);
     }
     // rest state: deviations are zero in every storage form
     cudaMemsetAsync(h->f[0], 0, pop_bytes, h->stream);
@@ -590,7 +586,6 @@ void iblb_destroy(iblb_handle h)
         if (ev) cudaEventDestroy(ev);
     free_dev(h->band_list);
     free_dev(h->band_count);
-    free_dev(h->skip);
     delete h;
 }
 
@@ -629,7 +624,6 @@ iblb_status iblb_set_interface(iblb_handle h, const double* xyz, int n_nodes, co
     }
     CK(h, cudaStreamSynchronize(h->stream));
     clear_graphs(h);
-    CK(h, cudaMemsetAsync(h->skip, 0, (size_t)h->nflags, h->stream));
     free_dev(h->q);
     free_dev(h->phi);
     free_dev(h->tri);
@@ -1005,9 +999,8 @@ iblb_status iblb_step_profiled(iblb_handle h, int n_steps, double* kernel_ms)
             StreamParams sp = h->sp;
             sp.rng_in = h->rng + h->cur;
             sp.rng_out = nullptr;
-            launch_band_cells(h->Q, h->storage, last, h->f[h->cur], h->f[h->cur ^ 1], h->mom, h->F,
-                              h->flags, h->skip, h->band_list, h->band_count, sp, h->sm_count,
-                              h->stream);
+            launch_band_cells(h->Q, h->storage, h->f[h->cur], h->f[h->cur ^ 1], h->mom, h->F,
+                              h->flags, h->band_list, h->band_count, sp, h->sm_count, h->stream);
         }
         cudaEventRecord(ev[4], h->stream);
         if (ib) enqueue_interp(h, h->stream, h->mom, nullptr, true);

@@ -203,19 +203,14 @@ k_stream_collide(const typename StorageT<ST>::S* __restrict__ fin,
     }
     const int lane = threadIdx.x & 31;
     const long long seg = ((long long)z * p.g.ny + y) * p.g.nseg_x + (x >> 5);
-    // a warp is one 32-cell segment (BLOCK is a multiple of 32): its band
-    // flag and its skip mark are warp-uniform
     int band = 0;
-    if (lane == 0 && (x >> 5) < p.g.nseg_x) {
-        if (flags) band = flags[seg];
-        if (p.skip && p.skip[seg]) band = 2;
-    }
+    if (lane == 0 && flags && (x >> 5) < p.g.nseg_x) band = flags[seg];
     band = __shfl_sync(0xffffffffu, band, 0);
     unsigned step = 0;
     if constexpr (ST == ST_FP16)
         step = sr_step(p.rng_in, p.rng_out,
                        blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0);
-    if (x >= p.g.nx || band == 2) return;
+    if (x >= p.g.nx) return;
     sc_cell<Q, ST, WRITE_ALL, CS, EXT>(fin, fout, mom, F, p, x, y, z, band, step);
     if (lane == 0 && band) flags[seg] = 0;
 }
@@ -294,19 +289,18 @@ static void launch_sc_t(bool write_all, const void* fin, void* fout, void* mom, 
 
 // ------------------------------------------------------------------ band cells
 // Overlapped step: the bulk pass (any variant, flags == nullptr) updates
-// the cells with the body force only; the plain kernel leaves out the
-// segments marked in StreamParams::skip (the band of the previous step).
-// k_band_list then lists the segments that are flagged (this step's band)
-// or skipped, and k_band_sc updates their cells from the same sources, one
-// warp per segment: flagged ones with the force density and the moments,
-// skipped ones with the body force.  A segment flagged now but not skipped
-// was also done by the bulk pass and is overwritten.  The cell arithmetic
-// is the plain kernel's, so the result is that of one pass.
-__global__ void k_band_list(const uint8_t* __restrict__ flags, const uint8_t* __restrict__ skip,
-                            long long nseg, int* __restrict__ list, int* __restrict__ count)
+// every cell with the body force only; k_band_list then lists the flagged
+// 32-cell row segments and k_band_sc updates their cells again from the same
+// sources, with the force density and the moments, one warp per segment.
+// The cell arithmetic is the plain kernel's, so the result is that of one
+// pass with the band cells forced.  (A variant in which the bulk pass left out the previous step's band, and the
+// band pass took the union, measured no faster: the plain kernel then has to
+// read the mark before its loads.)
+__global__ void k_band_list(const uint8_t* __restrict__ flags, long long nseg,
+                            int* __restrict__ list, int* __restrict__ count)
 {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool set = s < nseg && (flags[s] | skip[s]) != 0;
+    const bool set = s < nseg && flags[s] != 0;
     const unsigned m = __ballot_sync(0xffffffffu, set);
     if (m == 0u) return;
     const int lane = threadIdx.x & 31;
@@ -316,13 +310,12 @@ __global__ void k_band_list(const uint8_t* __restrict__ flags, const uint8_t* __
     if (set) list[base + __popc(m & ((1u << lane) - 1u))] = (int)s;
 }
 
-template <int Q, int ST, bool WRITE_ALL, bool EXT>
+template <int Q, int ST, bool EXT>
 __global__ void __launch_bounds__(128)
 k_band_sc(const typename StorageT<ST>::S* __restrict__ fin,
           typename StorageT<ST>::S* __restrict__ fout, typename StorageT<ST>::R* __restrict__ mom,
           typename StorageT<ST>::R* __restrict__ F, uint8_t* __restrict__ flags,
-          uint8_t* __restrict__ skip, const int* __restrict__ list, const int* __restrict__ count,
-          const StreamParams p)
+          const int* __restrict__ list, const int* __restrict__ count, const StreamParams p)
 {
     constexpr int D = Stencil<Q>::D;
     const int lane = threadIdx.x & 31;
@@ -332,29 +325,25 @@ k_band_sc(const typename StorageT<ST>::S* __restrict__ fin,
     if constexpr (ST == ST_FP16) step = sr_step(p.rng_in, nullptr, false);
     for (int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < n; w += nw) {
         const int s = list[w];
-        const int band = flags[s];
         const int row = s / p.g.nseg_x;
         const int x = (s - row * p.g.nseg_x) * 32 + lane;
         const int y = (D == 2) ? row : row % p.g.ny;
         const int z = (D == 2) ? 0 : row / p.g.ny;
-        if (x < p.g.nx) sc_cell<Q, ST, WRITE_ALL, false, EXT>(fin, fout, mom, F, p, x, y, z, band, step);
+        if (x < p.g.nx) sc_cell<Q, ST, false, false, EXT>(fin, fout, mom, F, p, x, y, z, 1, step);
         __syncwarp();
-        if (lane == 0) {
-            skip[s] = band ? 1 : 0;
-            flags[s] = 0;
-        }
+        if (lane == 0) flags[s] = 0;
     }
 }
 
-template <int Q, int ST, bool WRITE_ALL>
-static void launch_band_w(const void* fin, void* fout, void* mom, void* F, uint8_t* flags,
-                          uint8_t* skip, int* list, int* count, const StreamParams& p,
-                          int sm_count, cudaStream_t s)
+template <int Q, int ST>
+static void launch_band_t(const void* fin, void* fout, void* mom, void* F, uint8_t* flags,
+                          int* list, int* count, const StreamParams& p, int sm_count,
+                          cudaStream_t s)
 {
     using T = StorageT<ST>;
     const long long nseg = (long long)p.g.ny * p.g.nz * p.g.nseg_x;
     cudaMemsetAsync(count, 0, sizeof(int), s);
-    k_band_list<<<(unsigned)((nseg + 255) / 256), 256, 0, s>>>(flags, skip, nseg, list, count);
+    k_band_list<<<(unsigned)((nseg + 255) / 256), 256, 0, s>>>(flags, nseg, list, count);
     auto* a = (const typename T::S*)fin;
     auto* b = (typename T::S*)fout;
     auto* m = (typename T::R*)mom;
@@ -363,28 +352,16 @@ static void launch_band_w(const void* fin, void* fout, void* mom, void* F, uint8
     // segments take one or two rounds of memory latency
     const int grid = 16 * sm_count;
     if (p.moving)
-        k_band_sc<Q, ST, WRITE_ALL, true><<<grid, 128, 0, s>>>(a, b, m, f, flags, skip, list, count, p);
+        k_band_sc<Q, ST, true><<<grid, 128, 0, s>>>(a, b, m, f, flags, list, count, p);
     else
-        k_band_sc<Q, ST, WRITE_ALL, false><<<grid, 128, 0, s>>>(a, b, m, f, flags, skip, list, count, p);
+        k_band_sc<Q, ST, false><<<grid, 128, 0, s>>>(a, b, m, f, flags, list, count, p);
 }
 
-template <int Q, int ST>
-static void launch_band_t(bool write_all, const void* fin, void* fout, void* mom, void* F,
-                          uint8_t* flags, uint8_t* skip, int* list, int* count,
-                          const StreamParams& p, int sm_count, cudaStream_t s)
+void launch_band_cells(int Q, int storage, const void* fin, void* fout, void* moments, void* F,
+                       uint8_t* flags, int* list, int* count, const StreamParams& p,
+                       int sm_count, cudaStream_t s)
 {
-    if (write_all)
-        launch_band_w<Q, ST, true>(fin, fout, mom, F, flags, skip, list, count, p, sm_count, s);
-    else
-        launch_band_w<Q, ST, false>(fin, fout, mom, F, flags, skip, list, count, p, sm_count, s);
-}
-
-void launch_band_cells(int Q, int storage, bool write_all, const void* fin, void* fout,
-                       void* moments, void* F, uint8_t* flags, uint8_t* skip, int* list,
-                       int* count, const StreamParams& p, int sm_count, cudaStream_t s)
-{
-#define IBLB_BAND(QQ, SS) \
-    launch_band_t<QQ, SS>(write_all, fin, fout, moments, F, flags, skip, list, count, p, sm_count, s)
+#define IBLB_BAND(QQ, SS) launch_band_t<QQ, SS>(fin, fout, moments, F, flags, list, count, p, sm_count, s)
     if (Q == 9) {
         if (storage == ST_FP64) IBLB_BAND(9, ST_FP64);
         else if (storage == ST_FP32) IBLB_BAND(9, ST_FP32);
