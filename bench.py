@@ -793,10 +793,11 @@ def run_profile_mode(args):
                batch; the profiled steps run inside the NVTX range "run"
       batch2d  the 256 D2Q9 drops of the batched workload in one FP32 batch,
                likewise inside the NVTX range "run"
-      step3d   the 3D benchmark drop at half the lattice (128 x 128 x 64,
-               R = 20, 2 562 nodes), FP32, the overlapped step's kernels
-               (bulk pass with the launch shape of --tuning, default the
-               x-pair kernel, then the band pass)
+      step3d   a 3D drop on a 192 x 192 x 96 lattice (R = 30, 10 242 nodes;
+               0.54 GB of FP32 populations, above L2), storage --storage,
+               the overlapped step's kernels (bulk pass with the launch
+               shape of --tuning, default the x-pair kernel for FP32 and
+               the row-pair kernel for binary16, then the band pass)
     """
     import dataclasses
     import torch
@@ -816,11 +817,13 @@ def run_profile_mode(args):
                    lattice=[wl.nx, wl.ny, wl.nz])
         sim.close()
     elif args.case == "step3d":
-        nodes, faces = W.icosphere(4, 20.0, (64.0 + 0.31, 64.0 - 0.22, W.WALL_PLANE + 22.0))
-        wl = W.Workload("step3d_128x128x64", 19, 128, 128, 64, 0.8, 1e-3, 1.0, 75.0, 9, 3, 100,
+        nodes, faces = W.icosphere(5, 30.0, (96.0 + 0.31, 96.0 - 0.22, W.WALL_PLANE + 32.0))
+        wl = W.Workload("step3d_192x192x96", 19, 192, 192, 96, 0.8, 1e-3, 1.0, 75.0, 9, 3, 100,
                         nodes, faces)
-        sim = iblb.Simulation.from_workload(wl, storage=iblb.FP32_DEV)
-        v, bx, rows, ctas, ncw = (int(x) for x in (args.tuning or "2,128,2,2,8").split(","))
+        storage = {"fp32": iblb.FP32_DEV, "fp16": iblb.FP16_DEV, "fp64": iblb.FP64}[args.storage]
+        sim = iblb.Simulation.from_workload(wl, storage=storage)
+        default = "3,128,2,2,8" if args.storage == "fp16" else "2,128,2,2,8"
+        v, bx, rows, ctas, ncw = (int(x) for x in (args.tuning or default).split(","))
         sim.set_tuning(v, bx, 0, rows, ctas, ncw, step_overlap=1)
         steps = 6
         kms = sim.step_profiled(steps) / steps

@@ -315,7 +315,8 @@ __global__ void __launch_bounds__(128)
 k_band_sc(const typename StorageT<ST>::S* __restrict__ fin,
           typename StorageT<ST>::S* __restrict__ fout, typename StorageT<ST>::R* __restrict__ mom,
           typename StorageT<ST>::R* __restrict__ F, uint8_t* __restrict__ flags,
-          const int* __restrict__ list, const int* __restrict__ count, const StreamParams p)
+          unsigned* __restrict__ fine, const int* __restrict__ list,
+          const int* __restrict__ count, const StreamParams p)
 {
     constexpr int D = Stencil<Q>::D;
     const int lane = threadIdx.x & 31;
@@ -325,21 +326,29 @@ k_band_sc(const typename StorageT<ST>::S* __restrict__ fin,
     if constexpr (ST == ST_FP16) step = sr_step(p.rng_in, nullptr, false);
     for (int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < n; w += nw) {
         const int s = list[w];
+        // the marked 8-cell quarters of the segment (all of it if none is
+        // marked); outside them F is zero and the bulk pass is exact
+        const unsigned fw = fine[s];
+        const bool mine = fw == 0u || ((fw >> (8 * (lane >> 3))) & 0xffu) != 0u;
         const int row = s / p.g.nseg_x;
         const int x = (s - row * p.g.nseg_x) * 32 + lane;
         const int y = (D == 2) ? row : row % p.g.ny;
         const int z = (D == 2) ? 0 : row / p.g.ny;
-        if (x < p.g.nx) sc_cell<Q, ST, false, false, EXT>(fin, fout, mom, F, p, x, y, z, 1, step);
+        if (mine && x < p.g.nx) sc_cell<Q, ST, false, false, EXT>(fin, fout, mom, F, p, x, y, z, 1, step);
         __syncwarp();
-        if (lane == 0) flags[s] = 0;
+        if (lane == 0) {
+            flags[s] = 0;
+            fine[s] = 0u;
+        }
     }
 }
 
 template <int Q, int ST>
 static void launch_band_t(const void* fin, void* fout, void* mom, void* F, uint8_t* flags,
-                          int* list, int* count, const StreamParams& p, int sm_count,
-                          cudaStream_t s)
+                          uint8_t* fine8, int* list, int* count, const StreamParams& p,
+                          int sm_count, cudaStream_t s)
 {
+    unsigned* fine = reinterpret_cast<unsigned*>(fine8);
     using T = StorageT<ST>;
     const long long nseg = (long long)p.g.ny * p.g.nz * p.g.nseg_x;
     cudaMemsetAsync(count, 0, sizeof(int), s);
@@ -352,16 +361,17 @@ static void launch_band_t(const void* fin, void* fout, void* mom, void* F, uint8
     // segments take one or two rounds of memory latency
     const int grid = 16 * sm_count;
     if (p.moving)
-        k_band_sc<Q, ST, true><<<grid, 128, 0, s>>>(a, b, m, f, flags, list, count, p);
+        k_band_sc<Q, ST, true><<<grid, 128, 0, s>>>(a, b, m, f, flags, fine, list, count, p);
     else
-        k_band_sc<Q, ST, false><<<grid, 128, 0, s>>>(a, b, m, f, flags, list, count, p);
+        k_band_sc<Q, ST, false><<<grid, 128, 0, s>>>(a, b, m, f, flags, fine, list, count, p);
 }
 
 void launch_band_cells(int Q, int storage, const void* fin, void* fout, void* moments, void* F,
-                       uint8_t* flags, int* list, int* count, const StreamParams& p,
-                       int sm_count, cudaStream_t s)
+                       uint8_t* flags, uint8_t* fine, int* list, int* count,
+                       const StreamParams& p, int sm_count, cudaStream_t s)
 {
-#define IBLB_BAND(QQ, SS) launch_band_t<QQ, SS>(fin, fout, moments, F, flags, list, count, p, sm_count, s)
+#define IBLB_BAND(QQ, SS) \
+    launch_band_t<QQ, SS>(fin, fout, moments, F, flags, fine, list, count, p, sm_count, s)
     if (Q == 9) {
         if (storage == ST_FP64) IBLB_BAND(9, ST_FP64);
         else if (storage == ST_FP32) IBLB_BAND(9, ST_FP32);
@@ -534,7 +544,7 @@ k_stream_collide2(const typename StorageT<ST>::S* __restrict__ fin,
     }
     if (!active) return;
 
-    float2 Fx = p2((float)p.body[0]), Fy = p2((float)p.body[1]), Fz = p2((float)p.body[2]);
+    float2 Fx = p2(p.body_f[0]), Fy = p2(p.body_f[1]), Fz = p2(p.body_f[2]);
     if (band) {  // float4 per cell: (Fx, Fy, Fz, 0)
         float4* F4 = reinterpret_cast<float4*>(F);
         const float4 a = F4[cell], b = F4[cell + 1];
@@ -545,7 +555,7 @@ k_stream_collide2(const typename StorageT<ST>::S* __restrict__ fin,
         F4[cell + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     const CellMoments2 mo = cell_moments2<Q>(g, Fx, Fy, Fz);
-    cell_collide2<Q>(g, mo, (float)p.omega, Fx, Fy, Fz);
+    cell_collide2<Q>(g, mo, p.omega_f, Fx, Fy, Fz);
     const unsigned seed = ST == ST_FP16 ? sr_seed(step, cell) : 0u;
 #pragma unroll
     for (int i = 0; i < Q; i++) P::store2(fout, (long long)i * nc + cell, g[i], p.scale, sr_bits(seed, i));

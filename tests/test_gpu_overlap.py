@@ -14,6 +14,7 @@ import numpy as np
 import pytest
 
 from paper_2604_17463_gb300 import iblb
+from paper_2604_17463_gb300 import workloads as W
 from helpers import fluid_mask, oracle_from_workload, rel_l2, small_2d, small_3d
 
 pytestmark = pytest.mark.gpu
@@ -79,6 +80,28 @@ def test_overlapped_atomic_spread_matches_oracle(which, steps):
     assert rel_l2(ug[:, m], uo[: wl.dim, m]) < 1e-10
     assert np.max(np.abs(qg - qo)) < 1e-11
     g.close()
+
+
+@pytest.mark.parametrize("storage", [iblb.FP64, iblb.FP32_DEV, iblb.FP16_DEV])
+def test_overlapped_quarter_marks_bitwise(storage):
+    # the atomic spread marks the 8-cell quarters it touches and the band
+    # pass redoes only those; with nodes 10 cells apart no two stencils
+    # share a cell, so the atomic sums are exact and both steps agree bitwise
+    nodes, faces = W.icosphere(0, 9.0, (16.3, 15.8, W.WALL_PLANE + 12.0))
+    wl = W.Workload("sparse3d", 19, 32, 32, 28, 0.8, 5e-3, 1.0, 75.0, 9, 3, 40, nodes, faces)
+    a = run(wl, storage, overlap=1, det=False)
+    b = run(wl, storage, overlap=2, det=False)
+    assert same(a, b)
+
+
+@pytest.mark.parametrize("storage,tol", [(iblb.FP64, 1e-12), (iblb.FP32_DEV, 1e-5)])
+def test_overlapped_atomic_spread_matches_serial(storage, tol):
+    wl = small_3d(n=30, nz=22, R=7.0, level=3)
+    a = run(wl, storage, overlap=1, det=False, steps=70)
+    b = run(wl, storage, overlap=2, det=False, steps=70)
+    m = fluid_mask(a[0].shape, 3)
+    assert rel_l2(a[1][:, m], b[1][:, m]) < tol
+    assert np.max(np.abs(a[2] - b[2])) < tol
 
 
 def test_overlapped_moving_walls_bitwise():
