@@ -362,7 +362,7 @@ k_b_spread(const SlotDev* __restrict__ slots, const int2* __restrict__ nodes, in
     if (t >= nnodes) return;
     const int2 nd = nodes[t];
     const SlotDev& sd = slots[nd.x];
-    spread_node<D, R>(sd.g, sd.q, sd.phi, nd.y, (R*)sd.F, sd.flags, nullptr);
+    spread_node<D, R>(sd.g, sd.q, sd.phi, nd.y, (R*)sd.F, sd.flags);
 }
 
 // One thread per (slot, node): interpolate and advect (interp_node).

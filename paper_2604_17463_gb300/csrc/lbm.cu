@@ -143,11 +143,11 @@ __device__ __forceinline__ void sc_cell(const typename StorageT<ST>::S* __restri
                 g[i] = T::load(fin, (long long)i * nc + src, p.inv_scale);
             }
         }
-        // the FP64 parameters converted per thread measured faster here than
-        // their FP32 copies
-        Fx = (R)p.body[0];
-        Fy = (R)p.body[1];
-        Fz = (R)p.body[2];
+        // FP32 copies of the parameters: no FP64 conversion per thread (the
+        // same values as converting the FP64 ones)
+        Fx = param_body<R>(p, 0);
+        Fy = param_body<R>(p, 1);
+        Fz = param_body<R>(p, 2);
     }
 
     if (band) take_band_force<D, R>(F, nc, cell, Fx, Fy, Fz);
@@ -156,7 +156,7 @@ __device__ __forceinline__ void sc_cell(const typename StorageT<ST>::S* __restri
         mo = cell_moments<Q, R>(g, Fx, Fy, Fz, (R)p.inv_scale);
     else
         mo = cell_moments<Q, R>(g, Fx, Fy, Fz);
-    R om = (D == 2) ? param_omega<R>(p) : (R)p.omega;
+    R om = param_omega<R>(p);
     if (EXT && p.two_tau) {  // viscosity ratio: outside the interface relax with omega_out
         const int col = (D == 2) ? x : x + nx * y;
         if (!inside_cell(p.col_cnt, p.col_z, col, a)) om = (R)p.omega_out;
@@ -296,18 +296,33 @@ static void launch_sc_t(bool write_all, const void* fin, void* fout, void* mom, 
 // pass with the band cells forced.  (A variant in which the bulk pass left out the previous step's band, and the
 // band pass took the union, measured no faster: the plain kernel then has to
 // read the mark before its loads.)
-__global__ void k_band_list(const uint8_t* __restrict__ flags, long long nseg,
-                            int* __restrict__ list, int* __restrict__ count)
+// One atomic per block of BAND_LIST_THREADS segments: the warps' ballots
+// are summed in shared memory, thread 0 reserves the block's range.
+constexpr int BAND_LIST_THREADS = 256;
+
+__global__ void __launch_bounds__(BAND_LIST_THREADS)
+k_band_list(const uint8_t* __restrict__ flags, long long nseg, int* __restrict__ list,
+            int* __restrict__ count)
 {
+    __shared__ int s_cnt[BAND_LIST_THREADS / 32];
+    __shared__ int s_base;
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool set = s < nseg && flags[s] != 0;
     const unsigned m = __ballot_sync(0xffffffffu, set);
-    if (m == 0u) return;
-    const int lane = threadIdx.x & 31;
-    int base = 0;
-    if (lane == 0) base = atomicAdd(count, __popc(m));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (set) list[base + __popc(m & ((1u << lane) - 1u))] = (int)s;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) s_cnt[wid] = __popc(m);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int w = 0; w < BAND_LIST_THREADS / 32; w++) {
+            const int c = s_cnt[w];
+            s_cnt[w] = tot;
+            tot += c;
+        }
+        s_base = tot ? atomicAdd(count, tot) : 0;
+    }
+    __syncthreads();
+    if (set) list[s_base + s_cnt[wid] + __popc(m & ((1u << lane) - 1u))] = (int)s;
 }
 
 template <int Q, int ST, bool EXT>
@@ -315,8 +330,7 @@ __global__ void __launch_bounds__(128)
 k_band_sc(const typename StorageT<ST>::S* __restrict__ fin,
           typename StorageT<ST>::S* __restrict__ fout, typename StorageT<ST>::R* __restrict__ mom,
           typename StorageT<ST>::R* __restrict__ F, uint8_t* __restrict__ flags,
-          unsigned* __restrict__ fine, const int* __restrict__ list,
-          const int* __restrict__ count, const StreamParams p)
+          const int* __restrict__ list, const int* __restrict__ count, const StreamParams p)
 {
     constexpr int D = Stencil<Q>::D;
     const int lane = threadIdx.x & 31;
@@ -326,33 +340,26 @@ k_band_sc(const typename StorageT<ST>::S* __restrict__ fin,
     if constexpr (ST == ST_FP16) step = sr_step(p.rng_in, nullptr, false);
     for (int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < n; w += nw) {
         const int s = list[w];
-        // the marked 8-cell quarters of the segment (all of it if none is
-        // marked); outside them F is zero and the bulk pass is exact
-        const unsigned fw = fine[s];
-        const bool mine = fw == 0u || ((fw >> (8 * (lane >> 3))) & 0xffu) != 0u;
         const int row = s / p.g.nseg_x;
         const int x = (s - row * p.g.nseg_x) * 32 + lane;
         const int y = (D == 2) ? row : row % p.g.ny;
         const int z = (D == 2) ? 0 : row / p.g.ny;
-        if (mine && x < p.g.nx) sc_cell<Q, ST, false, false, EXT>(fin, fout, mom, F, p, x, y, z, 1, step);
+        if (x < p.g.nx) sc_cell<Q, ST, false, false, EXT>(fin, fout, mom, F, p, x, y, z, 1, step);
         __syncwarp();
-        if (lane == 0) {
-            flags[s] = 0;
-            fine[s] = 0u;
-        }
+        if (lane == 0) flags[s] = 0;
     }
 }
 
 template <int Q, int ST>
 static void launch_band_t(const void* fin, void* fout, void* mom, void* F, uint8_t* flags,
-                          uint8_t* fine8, int* list, int* count, const StreamParams& p,
-                          int sm_count, cudaStream_t s)
+                          int* list, int* count, const StreamParams& p, int sm_count,
+                          cudaStream_t s)
 {
-    unsigned* fine = reinterpret_cast<unsigned*>(fine8);
     using T = StorageT<ST>;
     const long long nseg = (long long)p.g.ny * p.g.nz * p.g.nseg_x;
     cudaMemsetAsync(count, 0, sizeof(int), s);
-    k_band_list<<<(unsigned)((nseg + 255) / 256), 256, 0, s>>>(flags, nseg, list, count);
+    k_band_list<<<(unsigned)((nseg + BAND_LIST_THREADS - 1) / BAND_LIST_THREADS),
+                  BAND_LIST_THREADS, 0, s>>>(flags, nseg, list, count);
     auto* a = (const typename T::S*)fin;
     auto* b = (typename T::S*)fout;
     auto* m = (typename T::R*)mom;
@@ -361,17 +368,17 @@ static void launch_band_t(const void* fin, void* fout, void* mom, void* F, uint8
     // segments take one or two rounds of memory latency
     const int grid = 16 * sm_count;
     if (p.moving)
-        k_band_sc<Q, ST, true><<<grid, 128, 0, s>>>(a, b, m, f, flags, fine, list, count, p);
+        k_band_sc<Q, ST, true><<<grid, 128, 0, s>>>(a, b, m, f, flags, list, count, p);
     else
-        k_band_sc<Q, ST, false><<<grid, 128, 0, s>>>(a, b, m, f, flags, fine, list, count, p);
+        k_band_sc<Q, ST, false><<<grid, 128, 0, s>>>(a, b, m, f, flags, list, count, p);
 }
 
 void launch_band_cells(int Q, int storage, const void* fin, void* fout, void* moments, void* F,
-                       uint8_t* flags, uint8_t* fine, int* list, int* count,
-                       const StreamParams& p, int sm_count, cudaStream_t s)
+                       uint8_t* flags, int* list, int* count, const StreamParams& p,
+                       int sm_count, cudaStream_t s)
 {
 #define IBLB_BAND(QQ, SS) \
-    launch_band_t<QQ, SS>(fin, fout, moments, F, flags, fine, list, count, p, sm_count, s)
+    launch_band_t<QQ, SS>(fin, fout, moments, F, flags, list, count, p, sm_count, s)
     if (Q == 9) {
         if (storage == ST_FP64) IBLB_BAND(9, ST_FP64);
         else if (storage == ST_FP32) IBLB_BAND(9, ST_FP32);

@@ -83,10 +83,10 @@ def test_overlapped_atomic_spread_matches_oracle(which, steps):
 
 
 @pytest.mark.parametrize("storage", [iblb.FP64, iblb.FP32_DEV, iblb.FP16_DEV])
-def test_overlapped_quarter_marks_bitwise(storage):
-    # the atomic spread marks the 8-cell quarters it touches and the band
-    # pass redoes only those; with nodes 10 cells apart no two stencils
-    # share a cell, so the atomic sums are exact and both steps agree bitwise
+def test_overlapped_atomic_spread_bitwise_when_stencils_are_disjoint(storage):
+    # with nodes 9.5 cells apart no two stencils share a cell, so the atomic
+    # spread's sums are exact and the overlapped and serial steps agree
+    # bitwise
     nodes, faces = W.icosphere(0, 9.0, (16.3, 15.8, W.WALL_PLANE + 12.0))
     wl = W.Workload("sparse3d", 19, 32, 32, 28, 0.8, 5e-3, 1.0, 75.0, 9, 3, 40, nodes, faces)
     a = run(wl, storage, overlap=1, det=False)
