@@ -346,7 +346,9 @@ long long iblb_fluid_cells(iblb_handle h);
  * persistent kernel walking a (slot, tile) work list).  Slot state lives in
  * one device arena of hbm_budget_bytes allocated at creation; a request is
  * admitted when its footprint fits (first fit), else IBLB_EAGAIN.  Slots
- * must have walls, no body force, and the batch's lattice and storage.
+ * must have walls, no body force, no viscosity ratio (tau_out 0 or tau), and
+ * the batch's lattice and storage; the walls may move tangentially
+ * (wall_u_lo / wall_u_hi, Ladd's moving-wall bounce-back as in iblb_step).
  * Each slot's tile shape (32-cell row segments per stream-collide work item) is
  * chosen at admission by timing the candidates on that slot (cached per
  * lattice width).  Calls on one batch are not thread-safe. */

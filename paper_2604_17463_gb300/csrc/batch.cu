@@ -81,6 +81,8 @@ struct SlotDev {
     int* entry_pos;
     double* entry_rec;
     ForceParams fp;
+    double uw_lo[3], uw_hi[3];  // tangential velocities of the lower / upper wall
+    int moving;                 // either wall moves
 };
 
 namespace {
@@ -130,7 +132,7 @@ struct __align__(16) BItem {
     unsigned nc;           // cells of the slot's lattice
     int segs;              // segments in this item
     float omega_f;         // 1 / tau
-    int cur_base;          // current buffer = cur_base ^ batch parity
+    int cur_base;          // bit 0: current buffer = bit 0 ^ batch parity; bit 1: moving walls
     float scale, inv_scale;  // binary16 storage scale
     unsigned* rng;         // binary16 rounding step counter
 };
@@ -194,7 +196,8 @@ k_b_stream_collide(const SlotDev* __restrict__ slots, const BItem* __restrict__ 
         } else {
             item = load_item(items, it);
         }
-        const int cur = item.e.w ^ par;  // cur_base ^ parity
+        const int cur = (item.e.w & 1) ^ par;  // cur_base ^ parity
+        const bool moving = (item.e.w & 2) != 0;
         const S* __restrict__ fin =
             (const S*)(cur ? ptr_of(item.a.z, item.a.w) : ptr_of(item.a.x, item.a.y));
         S* __restrict__ fout =
@@ -237,6 +240,16 @@ k_b_stream_collide(const SlotDev* __restrict__ slots, const BItem* __restrict__ 
         }
         const unsigned dwm = (D == 2) ? 0u - (unsigned)nx : 0u - (unsigned)nx * (unsigned)ny;
         const bool solid_m = (a == 1), solid_p = (a == Lw - 2);
+        // moving walls (Ladd): a population bounced back at a wall of
+        // tangential velocity u_w gains 2 w_i rho_w (c_i . u_w) / c_s^2 with
+        // rho_w = 1, as in the single engine; only the rows next to a wall
+        // read the slot's wall velocities
+        double uwm[3] = {0.0, 0.0, 0.0}, uwp[3] = {0.0, 0.0, 0.0};
+        if (moving && (solid_m || solid_p))
+            for (int k = 0; k < 3; k++) {
+                uwm[k] = slots[slot].uw_lo[k];
+                uwp[k] = slots[slot].uw_hi[k];
+            }
         for (int j0 = 0; j0 < segs; j0 += ILP) {
             R g[ILP][Q];
             R fxk[ILP], fyk[ILP], fzk[ILP];
@@ -264,10 +277,17 @@ k_b_stream_collide(const SlotDev* __restrict__ slots, const BItem* __restrict__ 
                     unsigned off = (cx > 0 ? dxm : (cx < 0 ? dxp : 0u)) +
                                    (cw > 0 ? dwm : (cw < 0 ? 0u - dwm : 0u));
                     if (D == 3) off += (cy > 0 ? dym : (cy < 0 ? dyp : 0u));
-                    if (solid)
+                    if (solid) {
                         g[k][i] = T::load(fin, (unsigned)L::opp(i) * nc + cell, R(1));
-                    else
+                        if (moving) {
+                            const double* uw = cw > 0 ? uwm : uwp;
+                            const double cu = (D == 2) ? L::cx(i) * uw[0] + cy * uw[1]
+                                                       : L::cx(i) * uw[0] + cy * uw[1] + cw * uw[2];
+                            g[k][i] += (R)(6.0 * L::w(i) * cu) * gsc;
+                        }
+                    } else {
                         g[k][i] = T::load(fin, (unsigned)i * nc + cell + off, R(1));
+                    }
                 }
             }
 #pragma unroll
@@ -662,7 +682,7 @@ void slot_items(const SlotDev& d, int slot, int cpt, std::vector<BItem>& out)
     it.Lw = g.dim == 2 ? g.ny : g.nz;
     it.nc = (unsigned)g.ncell;
     it.omega_f = d.omega_f;
-    it.cur_base = d.cur_base;
+    it.cur_base = (d.cur_base & 1) | (d.moving ? 2 : 0);
     it.scale = d.scale;
     it.inv_scale = d.inv_scale;
     it.rng = d.rng;
@@ -911,9 +931,12 @@ iblb_status check_cfg(const iblb_batch_s* b, const iblb_config& c)
     if (!(c.shear_modulus >= 0.0) || !std::isfinite(c.shear_modulus) || !(c.skalak_c > -0.5) ||
         !std::isfinite(c.skalak_c))
         return IBLB_EINVAL;
-    for (int k = 0; k < 3; k++)
-        if (c.wall_u_lo[k] != 0.0 || c.wall_u_hi[k] != 0.0)
-            return IBLB_EINVAL;  // nor moving walls
+    for (int k = 0; k < 3; k++)  // as iblb_create: |u_w| <= 0.3
+        for (double u : {c.wall_u_lo[k], c.wall_u_hi[k]})
+            if (!std::isfinite(u) || std::fabs(u) > 0.3) return IBLB_EINVAL;
+    // moving walls are tangential: no velocity along the wall axis
+    if (c.wall_u_lo[dim - 1] != 0.0 || c.wall_u_hi[dim - 1] != 0.0) return IBLB_EINVAL;
+    if (dim == 2 && (c.wall_u_lo[2] != 0.0 || c.wall_u_hi[2] != 0.0)) return IBLB_EINVAL;
     return IBLB_OK;
 }
 
@@ -1093,6 +1116,12 @@ iblb_status iblb_batch_admit(iblb_batch b, const iblb_config* cfg, const double*
     d.fp.wall_plane = 0.5;
     d.fp.Gs = cfg->shear_modulus;
     d.fp.Cs = cfg->skalak_c;
+    d.moving = 0;
+    for (int k = 0; k < 3; k++) {
+        d.uw_lo[k] = k < dim ? cfg->wall_u_lo[k] : 0.0;
+        d.uw_hi[k] = k < dim ? cfg->wall_u_hi[k] : 0.0;
+        if (d.uw_lo[k] != 0.0 || d.uw_hi[k] != 0.0) d.moving = 1;
+    }
     d.fp.eref = elastic ? (const double*)(base + L.eref) : nullptr;
     if (dim == 3) {
         d.tri = (int*)(base + L.tri);

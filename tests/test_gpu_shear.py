@@ -111,8 +111,48 @@ def test_moving_wall_validation():
     with pytest.raises(iblb.IBLBError):   # too fast
         iblb.Simulation(19, 8, 8, 8, wall_u_hi=(0.5, 0.0, 0.0))
     b = iblb.Batch(iblb.D2Q9, iblb.FP32_DEV, 1 << 28, max_slots=4)
-    with pytest.raises(iblb.IBLBError):
-        b.admit_workload(small_2d(), wall_u_hi=(0.01, 0.0, 0.0))
+    with pytest.raises(iblb.IBLBError):   # wall-normal component
+        b.admit_workload(small_2d(), wall_u_hi=(0.0, 0.01, 0.0))
+    with pytest.raises(iblb.IBLBError):   # too fast
+        b.admit_workload(small_2d(), wall_u_hi=(0.4, 0.0, 0.0))
+    b.close()
+
+
+@pytest.mark.parametrize("which", ["2d", "3d"])
+@pytest.mark.parametrize("storage,tol", [(iblb.FP64, 1e-12), (iblb.FP32_DEV, 1e-5),
+                                         (iblb.FP16_DEV, 2e-3)])
+def test_batch_moving_walls_match_single_engine(which, storage, tol):
+    # a drop between moving walls in a batch with a slot at rest: the same
+    # fields and nodes as the single engine (from rest), and the resting slot
+    # is untouched by its neighbour's walls
+    if which == "2d":
+        wl, rest = small_2d(nx=48, ny=30), small_2d(nx=40, ny=26, R=5.0)
+        lo, hi = (-0.01, 0.0, 0.0), (0.012, 0.0, 0.0)
+        Q = iblb.D2Q9
+    else:
+        wl, rest = small_3d(n=24, nz=20), small_3d(n=20, nz=16, R=4.5)
+        lo, hi = (-0.01, 0.004, 0.0), (0.012, -0.006, 0.0)
+        Q = iblb.D3Q19
+    steps = 150 if which == "2d" else 40
+    b = iblb.Batch(Q, storage, 1 << 30, max_slots=4)
+    s = b.admit_workload(wl, n_steps=steps, wall_u_lo=lo, wall_u_hi=hi)
+    r = b.admit_workload(rest, n_steps=steps)
+    b.run(steps)
+    rb, ub, qb = b.fields(s)
+    g = iblb.Simulation.from_workload(wl, storage=storage, wall_u_lo=lo, wall_u_hi=hi)
+    g.step(steps)
+    rg, ug, qg = g.fields()
+    m = fluid_mask(rg.shape, wl.dim)
+    assert rel_l2(ub[:, m], ug[:, m]) < tol
+    assert np.max(np.abs(qb - qg)) < (1e-11 if storage == iblb.FP64 else 1e-4)
+    assert np.max(np.abs(ub[0][m])) > 1e-3   # the walls drive a flow
+    rr, ur, qr = b.fields(r)
+    g2 = iblb.Simulation.from_workload(rest, storage=storage)
+    g2.step(steps)
+    m2 = fluid_mask(rr.shape, rest.dim)
+    assert rel_l2(ur[:, m2], g2.fields()[1][:, m2]) < tol
+    g.close()
+    g2.close()
     b.close()
 
 
