@@ -242,14 +242,9 @@ k_b_stream_collide(const SlotDev* __restrict__ slots, const BItem* __restrict__ 
         const bool solid_m = (a == 1), solid_p = (a == Lw - 2);
         // moving walls (Ladd): a population bounced back at a wall of
         // tangential velocity u_w gains 2 w_i rho_w (c_i . u_w) / c_s^2 with
-        // rho_w = 1, as in the single engine; only the rows next to a wall
-        // read the slot's wall velocities
-        double uwm[3] = {0.0, 0.0, 0.0}, uwp[3] = {0.0, 0.0, 0.0};
-        if (moving && (solid_m || solid_p))
-            for (int k = 0; k < 3; k++) {
-                uwm[k] = slots[slot].uw_lo[k];
-                uwp[k] = slots[slot].uw_hi[k];
-            }
+        // rho_w = 1, as in the single engine; the wall velocities are read
+        // (from the slot descriptor, cached) only where that term is added,
+        // so they hold no registers through the segment loop
         for (int j0 = 0; j0 < segs; j0 += ILP) {
             R g[ILP][Q];
             R fxk[ILP], fyk[ILP], fzk[ILP];
@@ -280,7 +275,7 @@ k_b_stream_collide(const SlotDev* __restrict__ slots, const BItem* __restrict__ 
                     if (solid) {
                         g[k][i] = T::load(fin, (unsigned)L::opp(i) * nc + cell, R(1));
                         if (moving) {
-                            const double* uw = cw > 0 ? uwm : uwp;
+                            const double* uw = cw > 0 ? slots[slot].uw_lo : slots[slot].uw_hi;
                             const double cu = (D == 2) ? L::cx(i) * uw[0] + cy * uw[1]
                                                        : L::cx(i) * uw[0] + cy * uw[1] + cw * uw[2];
                             g[k][i] += (R)(6.0 * L::w(i) * cu) * gsc;
