@@ -298,7 +298,7 @@ typedef struct {
                                      additions.  Not changed by
                                      iblb_autotune. */
     int step_overlap;             /* iblb_step with an interface: 0 (default)
-                                     overlaps on lattices of at least 2^20
+                                     overlaps on 3D lattices of at least 2^20
                                      cells, 1 always, 2 never.  Overlapped, a
                                      step runs the stream-collide of every
                                      cell with the body force only on one

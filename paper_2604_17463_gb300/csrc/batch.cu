@@ -168,8 +168,10 @@ __device__ __forceinline__ void* ptr_of(int lo, int hi)
 // segments the force density is loaded right after the populations, so that
 // its latency overlaps theirs.  Populations are addressed by one 32-bit index
 // i * ncell + cell from the slot's buffer (Q * ncell < 2^32).  Arithmetic is
-// FP32 for the FP32 and binary16 forms, FP64 for FP64.
-template <int Q, int ST, bool WRITE_ALL>
+// FP32 for the FP32 and binary16 forms, FP64 for FP64.  MW: the
+// instantiation that adds the moving-wall term (launched only while some
+// active slot has moving walls; the other one carries no trace of it).
+template <int Q, int ST, bool WRITE_ALL, bool MW>
 __global__ void __launch_bounds__(BT, (BMinBlocks<Q, ST>::value))
 k_b_stream_collide(const SlotDev* __restrict__ slots, const BItem* __restrict__ items,
                    int nitems, int par)
@@ -197,7 +199,7 @@ k_b_stream_collide(const SlotDev* __restrict__ slots, const BItem* __restrict__ 
             item = load_item(items, it);
         }
         const int cur = (item.e.w & 1) ^ par;  // cur_base ^ parity
-        const bool moving = (item.e.w & 2) != 0;
+        const bool moving = MW && (item.e.w & 2) != 0;
         const S* __restrict__ fin =
             (const S*)(cur ? ptr_of(item.a.z, item.a.w) : ptr_of(item.a.x, item.a.y));
         S* __restrict__ fout =
@@ -242,9 +244,16 @@ k_b_stream_collide(const SlotDev* __restrict__ slots, const BItem* __restrict__ 
         const bool solid_m = (a == 1), solid_p = (a == Lw - 2);
         // moving walls (Ladd): a population bounced back at a wall of
         // tangential velocity u_w gains 2 w_i rho_w (c_i . u_w) / c_s^2 with
-        // rho_w = 1, as in the single engine; the wall velocities are read
-        // (from the slot descriptor, cached) only where that term is added,
-        // so they hold no registers through the segment loop
+        // rho_w = 1, as in the single engine; only the rows next to a wall
+        // read the slot's wall velocities
+        double uwm[3] = {0.0, 0.0, 0.0}, uwp[3] = {0.0, 0.0, 0.0};
+        if constexpr (MW) {
+            if (moving && (solid_m || solid_p))
+                for (int k = 0; k < 3; k++) {
+                    uwm[k] = slots[slot].uw_lo[k];
+                    uwp[k] = slots[slot].uw_hi[k];
+                }
+        }
         for (int j0 = 0; j0 < segs; j0 += ILP) {
             R g[ILP][Q];
             R fxk[ILP], fyk[ILP], fzk[ILP];
@@ -274,8 +283,8 @@ k_b_stream_collide(const SlotDev* __restrict__ slots, const BItem* __restrict__ 
                     if (D == 3) off += (cy > 0 ? dym : (cy < 0 ? dyp : 0u));
                     if (solid) {
                         g[k][i] = T::load(fin, (unsigned)L::opp(i) * nc + cell, R(1));
-                        if (moving) {
-                            const double* uw = cw > 0 ? slots[slot].uw_lo : slots[slot].uw_hi;
+                        if (MW && moving) {
+                            const double* uw = cw > 0 ? uwm : uwp;
                             const double cu = (D == 2) ? L::cx(i) * uw[0] + cy * uw[1]
                                                        : L::cx(i) * uw[0] + cy * uw[1] + cw * uw[2];
                             g[k][i] += (R)(6.0 * L::w(i) * cu) * gsc;
@@ -397,15 +406,22 @@ k_b_interp(const SlotDev* __restrict__ slots, const int2* __restrict__ nodes, in
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
-static void launch_b_sc(int Q, int storage, bool write_all, const SlotDev* slots,
+static void launch_b_sc(int Q, int storage, bool write_all, bool moving, const SlotDev* slots,
                         const BItem* tiles, int ntiles, int par, int grid, cudaStream_t s)
 {
-#define IBLB_BSC(QQ, SS)                                                                       \
-    do {                                                                                       \
-        if (write_all)                                                                         \
-            k_b_stream_collide<QQ, SS, true><<<grid, BT, 0, s>>>(slots, tiles, ntiles, par);   \
-        else                                                                                   \
-            k_b_stream_collide<QQ, SS, false><<<grid, BT, 0, s>>>(slots, tiles, ntiles, par);  \
+#define IBLB_BSC(QQ, SS)                                                                             \
+    do {                                                                                             \
+        if (moving) {                                                                                \
+            if (write_all)                                                                           \
+                k_b_stream_collide<QQ, SS, true, true><<<grid, BT, 0, s>>>(slots, tiles, ntiles, par);  \
+            else                                                                                     \
+                k_b_stream_collide<QQ, SS, false, true><<<grid, BT, 0, s>>>(slots, tiles, ntiles, par); \
+        } else {                                                                                     \
+            if (write_all)                                                                           \
+                k_b_stream_collide<QQ, SS, true, false><<<grid, BT, 0, s>>>(slots, tiles, ntiles, par); \
+            else                                                                                     \
+                k_b_stream_collide<QQ, SS, false, false><<<grid, BT, 0, s>>>(slots, tiles, ntiles, par);\
+        }                                                                                            \
     } while (0)
     if (Q == 9) {
         if (storage == ST_FP64) IBLB_BSC(9, ST_FP64);
@@ -425,7 +441,7 @@ static int b_sc_blocks_per_sm(int Q, int storage)
 {
     int n = 0;
     cudaError_t e = cudaErrorInvalidValue;
-#define IBLB_OCC(QQ, SS) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_b_stream_collide<QQ, SS, false>, BT, 0)
+#define IBLB_OCC(QQ, SS) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_b_stream_collide<QQ, SS, false, false>, BT, 0)
     if (Q == 9) {
         if (storage == ST_FP64) IBLB_OCC(9, ST_FP64);
         else if (storage == ST_FP32) IBLB_OCC(9, ST_FP32);
@@ -602,6 +618,7 @@ struct iblb_batch_s {
     int2* d_faces = nullptr;
     size_t cap_tiles = 0, cap_nodes = 0, cap_faces = 0;
     int ntiles = 0, nnodes = 0, nfaces = 0, nactive = 0;
+    bool any_moving = false;  // an active slot has moving walls
     double* d_partial = nullptr;
     double* d_obs = nullptr;
     int par = 0;
@@ -723,6 +740,9 @@ iblb_status rebuild(iblb_batch_s* b)
     b->ntiles = (int)tiles.size();
     b->nnodes = (int)nodes.size();
     b->nfaces = (int)faces.size();
+    b->any_moving = false;
+    for (auto& sl : b->slots)
+        if (sl.active && sl.dev.moving) b->any_moving = true;
     // deterministic spread: bins and cell tiles of the active slots, numbered
     // globally in slot order
     b->det = false;
@@ -800,7 +820,8 @@ void enqueue_step(iblb_batch_s* b, cudaStream_t s, int par, bool write_all)
         enqueue_spread(b, s);
     }
     const int grid = std::max(1, std::min(b->ntiles, b->sm_count * b->sc_blocks_per_sm));
-    launch_b_sc(b->Q, b->storage, write_all, b->d_slots, b->d_tiles, b->ntiles, par, grid, s);
+    launch_b_sc(b->Q, b->storage, write_all, b->any_moving, b->d_slots, b->d_tiles, b->ntiles, par,
+                grid, s);
     if (b->nnodes > 0)
         launch_b_ib(b->dim, b->storage, 2, b->d_slots, b->d_nodes, b->nnodes, b->d_faces,
                     b->nfaces, s);
@@ -882,10 +903,11 @@ iblb_status tune_slot(iblb_batch_s* b, int s)
         cudaMemcpy(d_one, &d, sizeof(SlotDev), cudaMemcpyHostToDevice);
         cudaMemcpy(d_t, tl.data(), sizeof(BItem) * tl.size(), cudaMemcpyHostToDevice);
         const int grid = std::max(1, std::min((int)tl.size(), b->sm_count * b->sc_blocks_per_sm));
-        launch_b_sc(b->Q, b->storage, false, d_one, d_t, (int)tl.size(), 0, grid, b->stream);
+        const bool mw = d.moving != 0;
+        launch_b_sc(b->Q, b->storage, false, mw, d_one, d_t, (int)tl.size(), 0, grid, b->stream);
         cudaEventRecord(e0, b->stream);
         for (int t = 0; t < trials; t++)
-            launch_b_sc(b->Q, b->storage, false, d_one, d_t, (int)tl.size(), 0, grid, b->stream);
+            launch_b_sc(b->Q, b->storage, false, mw, d_one, d_t, (int)tl.size(), 0, grid, b->stream);
         cudaEventRecord(e1, b->stream);
         b->launches += trials + 1;
         add_launches(trials + 1);
@@ -1235,8 +1257,8 @@ iblb_status batch_run(iblb_batch_s* b, int max_steps, int* n_completed, double* 
                 cudaEventRecord(ev[1], b->stream);
                 if (b->nnodes > 0) enqueue_spread(b, b->stream);
                 cudaEventRecord(ev[2], b->stream);
-                launch_b_sc(b->Q, b->storage, last, b->d_slots, b->d_tiles, b->ntiles, b->par,
-                            grid, b->stream);
+                launch_b_sc(b->Q, b->storage, last, b->any_moving, b->d_slots, b->d_tiles,
+                            b->ntiles, b->par, grid, b->stream);
                 cudaEventRecord(ev[3], b->stream);
                 if (b->nnodes > 0)
                     launch_b_ib(b->dim, b->storage, 2, b->d_slots, b->d_nodes, b->nnodes,

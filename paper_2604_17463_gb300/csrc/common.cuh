@@ -140,7 +140,7 @@ struct Tuning {
     long long wait_limit = 0;   // pipelined kernel: clock cycles a wait may take (0: ~2 s)
     int ib_grouped = 0;         // 3D interfaces: 1 spreads / interpolates by spatial groups of
                                 // nodes (ib_groups.cu) instead of one thread per node
-    int step_overlap = 0;       // 0: overlapped step on lattices of >= 2^20 cells; 1: always;
+    int step_overlap = 0;       // 0: overlapped step on 3D lattices of >= 2^20 cells; 1: always;
                                 // 2: never (see enqueue_step_overlapped)
 };
 
