@@ -206,11 +206,14 @@ cudaError_t launch_stream_collide_pipe(int Q, int storage, bool write_all, const
 // Band cells of the overlapped step (lbm.cu): after a bulk pass with
 // flags == nullptr, list the flagged segments (list: one int per segment at
 // most) and update their cells again with the force density and the
-// moments; the flags are cleared.  count: one int, reset here.  Three
-// operations on stream s (a 4-byte memset and two kernels).
+// moments, 8-cell quarter by quarter: the quarters marked in `fine` (4 bytes
+// per segment, 4-byte aligned), all four of a flagged segment without
+// marks.  Flags and marks are cleared.  list: one int per quarter at most;
+// count: one int, reset here.  Three operations on stream s (a 4-byte
+// memset and two kernels).
 void launch_band_cells(int Q, int storage, const void* fin, void* fout, void* moments, void* F,
-                       uint8_t* flags, int* list, int* count, const StreamParams& p,
-                       int sm_count, cudaStream_t s);
+                       uint8_t* flags, uint8_t* fine, int* list, int* count,
+                       const StreamParams& p, int sm_count, cudaStream_t s);
 constexpr int BAND_KERNELS = 2;
 
 // Host FP64 <-> device storage conversion of populations ([Q][ncell], f_i).
@@ -245,8 +248,10 @@ void launch_forces(int dim, const double* q, int N, int M, const int* tri, const
                    const int* entry_pos, double* entry_rec, const ForceParams& fp, double* phi,
                    double* normal, double* chi, int* err, cudaStream_t s);
 constexpr int ENTRY_RECORD_DOUBLES = 8;
+// fine (may be null): one byte per 8-cell quarter of each segment (4 per
+// segment), set where a stencil touches it, for the band pass.
 void launch_spread(int storage, int dim, const double* q, const double* phi, int N, void* F,
-                   uint8_t* flags, const GridParams& g, cudaStream_t s);
+                   uint8_t* flags, uint8_t* fine, const GridParams& g, cudaStream_t s);
 // qdot [N][dim] = sum u Delta; if advect, q += qdot.
 void launch_interp(int storage, int dim, double* q, const void* moments, int N, double* qdot,
                    bool advect, const GridParams& g, cudaStream_t s);

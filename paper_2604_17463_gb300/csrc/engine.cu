@@ -49,8 +49,9 @@ struct iblb_sim {
     cudaStream_t cap = nullptr;  // private stream used only for graph capture (IB chain)
     cudaStream_t cap2 = nullptr; // second capture stream: the bulk stream-collide pass
     cudaEvent_t ev_top = nullptr, ev_band = nullptr, ev_bulk = nullptr;  // overlapped step
-    int* band_list = nullptr;    // flagged segments of the overlapped step [nflags]
+    int* band_list = nullptr;    // band quarters of the overlapped step [4 nflags]
     int* band_count = nullptr;
+    uint8_t* fine = nullptr;     // 8-cell quarters the spread touched [4 nflags]
     void* f[2] = {nullptr, nullptr};
     int cur = 0;
     void* mom = nullptr;       // drho [ncell], u [dim][ncell]
@@ -165,8 +166,10 @@ void enqueue_regroup(iblb_sim* h, cudaStream_t s)
 
 // A2/A3: spread the nodal forces, with atomics (by spatial groups of nodes
 // for a 3D interface, else one thread per node) or (deterministic_spread)
-// as an ordered gather.
-void enqueue_spread(iblb_sim* h, cudaStream_t s)
+// as an ordered gather.  band_pass: the overlapped step's band pass
+// follows (the per-node spread then also marks the 8-cell quarters it
+// touches).
+void enqueue_spread(iblb_sim* h, cudaStream_t s, bool band_pass = false)
 {
     if (h->det)
         launch_spread_det(h->storage, h->dim, h->d_detslot, nullptr, h->N, h->detb, h->det_nbins,
@@ -174,7 +177,8 @@ void enqueue_spread(iblb_sim* h, cudaStream_t s)
     else if (use_groups(h))
         launch_spread_grouped(h->storage, h->q, h->phi, h->grp, h->F, h->flags, h->g, h->sm_count, s);
     else
-        launch_spread(h->storage, h->dim, h->q, h->phi, h->N, h->F, h->flags, h->g, s);
+        launch_spread(h->storage, h->dim, h->q, h->phi, h->N, h->F, h->flags,
+                      band_pass ? h->fine : nullptr, h->g, s);
 }
 
 // A5/A6: interpolate the velocity in `moments` to the nodes (qdot may be
@@ -261,13 +265,13 @@ void enqueue_step_overlapped(iblb_sim* h, cudaStream_t a, cudaStream_t b, bool w
     if (regroup) enqueue_regroup(h, a);
     launch_forces(h->dim, h->q, h->N, h->M, h->tri, h->csr_ptr, h->entry_pos, h->entry_rec, h->fp,
                   h->phi, nullptr, nullptr, h->err, a);
-    enqueue_spread(h, a);
+    enqueue_spread(h, a, true);
     cudaStreamWaitEvent(a, h->ev_bulk, 0);
     StreamParams sp = h->sp;
     sp.rng_in = h->rng + h->cur;
     sp.rng_out = nullptr;
     launch_band_cells(h->Q, h->storage, h->f[h->cur], h->f[h->cur ^ 1], h->mom, h->F, h->flags,
-                      h->band_list, h->band_count, sp, h->sm_count, a);
+                      h->fine, h->band_list, h->band_count, sp, h->sm_count, a);
     cudaEventRecord(h->ev_band, a);
     enqueue_interp(h, a, h->mom, nullptr, true);
     h->cur ^= 1;
@@ -516,9 +520,11 @@ iblb_status iblb_create(const iblb_config* cfg, void* cuda_stream, iblb_handle* 
         for (cudaEvent_t* ev : {&h->ev_top, &h->ev_band, &h->ev_bulk})
             if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess)
                 return bail(e, "events");
-        if ((e = cudaMalloc(&h->band_list, sizeof(int) * (size_t)h->nflags)) != cudaSuccess ||
-            (e = cudaMalloc(&h->band_count, sizeof(int))) != cudaSuccess)
+        if ((e = cudaMalloc(&h->band_list, sizeof(int) * 4 * (size_t)h->nflags)) != cudaSuccess ||
+            (e = cudaMalloc(&h->band_count, sizeof(int))) != cudaSuccess ||
+            (e = cudaMalloc(&h->fine, 4 * (size_t)h->nflags)) != cudaSuccess)
             return bail(e, "band list");
+        cudaMemsetAsync(h->fine, 0, 4 * (size_t)h->nflags, h->stream);
     }
     // rest state: deviations are zero in every storage form
     cudaMemsetAsync(h->f[0], 0, pop_bytes, h->stream);
@@ -588,6 +594,7 @@ void iblb_destroy(iblb_handle h)
         if (ev) cudaEventDestroy(ev);
     free_dev(h->band_list);
     free_dev(h->band_count);
+    free_dev(h->fine);
     delete h;
 }
 
@@ -992,7 +999,7 @@ iblb_status iblb_step_profiled(iblb_handle h, int n_steps, double* kernel_ms)
                           nullptr, nullptr, h->err, h->stream);
         cudaEventRecord(ev[1], h->stream);
         if (regroup) enqueue_regroup(h, h->stream);
-        if (ib) enqueue_spread(h, h->stream);
+        if (ib) enqueue_spread(h, h->stream, ov);
         enqueue_classify(h, h->stream);
         cudaEventRecord(ev[2], h->stream);
         launch_sc(h, h->stream, last, ov);
@@ -1002,7 +1009,8 @@ iblb_status iblb_step_profiled(iblb_handle h, int n_steps, double* kernel_ms)
             sp.rng_in = h->rng + h->cur;
             sp.rng_out = nullptr;
             launch_band_cells(h->Q, h->storage, h->f[h->cur], h->f[h->cur ^ 1], h->mom, h->F,
-                              h->flags, h->band_list, h->band_count, sp, h->sm_count, h->stream);
+                              h->flags, h->fine, h->band_list, h->band_count, sp, h->sm_count,
+                              h->stream);
         }
         cudaEventRecord(ev[4], h->stream);
         if (ib) enqueue_interp(h, h->stream, h->mom, nullptr, true);

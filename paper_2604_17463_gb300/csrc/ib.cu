@@ -97,23 +97,24 @@ void launch_forces(int dim, const double* q, int N, int M, const int* tri, const
 template <int D, typename R>
 __global__ void __launch_bounds__(128)
 k_spread_t(const double* __restrict__ q, const double* __restrict__ phi, int N,
-           R* __restrict__ F, uint8_t* __restrict__ flags, GridParams g)
+           R* __restrict__ F, uint8_t* __restrict__ flags, uint8_t* __restrict__ fine,
+           GridParams g)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < N) spread_node<D, R>(g, q, phi, j, F, flags);
+    if (j < N) spread_node<D, R>(g, q, phi, j, F, flags, fine);
 }
 
 void launch_spread(int storage, int dim, const double* q, const double* phi, int N, void* F,
-                   uint8_t* flags, const GridParams& g, cudaStream_t s)
+                   uint8_t* flags, uint8_t* fine, const GridParams& g, cudaStream_t s)
 {
     if (N <= 0) return;
     const int b = 128, grid = (N + b - 1) / b;
     if (storage == ST_FP64) {
-        if (dim == 2) k_spread_t<2, double><<<grid, b, 0, s>>>(q, phi, N, (double*)F, flags, g);
-        else k_spread_t<3, double><<<grid, b, 0, s>>>(q, phi, N, (double*)F, flags, g);
+        if (dim == 2) k_spread_t<2, double><<<grid, b, 0, s>>>(q, phi, N, (double*)F, flags, fine, g);
+        else k_spread_t<3, double><<<grid, b, 0, s>>>(q, phi, N, (double*)F, flags, fine, g);
     } else {
-        if (dim == 2) k_spread_t<2, float><<<grid, b, 0, s>>>(q, phi, N, (float*)F, flags, g);
-        else k_spread_t<3, float><<<grid, b, 0, s>>>(q, phi, N, (float*)F, flags, g);
+        if (dim == 2) k_spread_t<2, float><<<grid, b, 0, s>>>(q, phi, N, (float*)F, flags, fine, g);
+        else k_spread_t<3, float><<<grid, b, 0, s>>>(q, phi, N, (float*)F, flags, fine, g);
     }
 }
 

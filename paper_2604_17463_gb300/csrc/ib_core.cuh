@@ -87,11 +87,15 @@ __device__ __forceinline__ bool node_lines(const GridParams& g, const double* __
 // Spread of node j by one thread: its 16 (2D) / 64 (3D) stencil points in
 // turn, one fire-and-forget vector addition per point in FP32 (a thread
 // never waits on its additions, so many are in flight per SM); the band
-// segments of the stencil rows are flagged once per row and segment.
+// segments of the stencil rows are flagged once per row and segment, and,
+// when `fine` is given, the 8-cell quarters of them that the stencil touches
+// (fine[4 seg + quarter] = 1; the band pass of the overlapped step redoes
+// only those).
 template <int D, typename R>
 __device__ __forceinline__ void spread_node(const GridParams& g, const double* __restrict__ q,
                                             const double* __restrict__ phi, int j,
-                                            R* __restrict__ F, uint8_t* __restrict__ flags)
+                                            R* __restrict__ F, uint8_t* __restrict__ flags,
+                                            uint8_t* __restrict__ fine = nullptr)
 {
     R w[3][4];
     int ix[3][4];
@@ -108,7 +112,7 @@ __device__ __forceinline__ void spread_node(const GridParams& g, const double* _
             if (i1 < 0) continue;
             const long long row = (long long)i2 * g.ny + i1;
             const R w12 = w[1][o1] * w[2][o2];
-            int last_seg = -1;
+            int last_seg = -1, last_q = -1;
 #pragma unroll
             for (int o0 = 0; o0 < 4; o0++) {
                 const R ww = w[0][o0] * w12;
@@ -123,6 +127,10 @@ __device__ __forceinline__ void spread_node(const GridParams& g, const double* _
                 if ((i0 >> 5) != last_seg) {
                     last_seg = i0 >> 5;
                     flags[row * g.nseg_x + last_seg] = 1;
+                }
+                if (fine && (i0 >> 3) != last_q) {
+                    last_q = i0 >> 3;
+                    fine[row * g.nseg_x * 4 + last_q] = 1;
                 }
             }
         }

@@ -289,40 +289,63 @@ static void launch_sc_t(bool write_all, const void* fin, void* fout, void* mom, 
 
 // ------------------------------------------------------------------ band cells
 // Overlapped step: the bulk pass (any variant, flags == nullptr) updates
-// every cell with the body force only; k_band_list then lists the flagged
-// 32-cell row segments and k_band_sc updates their cells again from the same
-// sources, with the force density and the moments, one warp per segment.
-// The cell arithmetic is the plain kernel's, so the result is that of one
-// pass with the band cells forced.  (A variant in which the bulk pass left out the previous step's band, and the
+// every cell with the body force only; k_band_list then lists the 8-cell
+// quarters of the flagged 32-cell row segments that a stencil touched (all
+// four quarters of a flagged segment whose quarters carry no marks, as from
+// the ordered or the grouped spread), and k_band_sc updates their cells
+// again from the same sources, with the force density and the moments: each
+// warp takes four listed quarters, 8 lanes per quarter.  Outside the marked
+// quarters F is zero, so the bulk pass's result is already exact there.  The
+// cell arithmetic is the plain kernel's, so the result is that of one pass.
+// With whole segments, one warp each, the band kernel took 14.4 us per step
+// on the 256 x 256 x 128 drop (~16 600 segments, three to four rounds of
+// memory latency); a quarter-listed pass needs a quarter of the warps.  (A
+// variant in which the bulk pass left out the previous step's band, and the
 // band pass took the union, measured no faster: the plain kernel then has to
 // read the mark before its loads.)
-// One atomic per block of BAND_LIST_THREADS segments: the warps' ballots
+// One atomic per block of BAND_LIST_THREADS segments: the warps' counts
 // are summed in shared memory, thread 0 reserves the block's range.
 constexpr int BAND_LIST_THREADS = 256;
 
 __global__ void __launch_bounds__(BAND_LIST_THREADS)
-k_band_list(const uint8_t* __restrict__ flags, long long nseg, int* __restrict__ list,
-            int* __restrict__ count)
+k_band_list(const uint8_t* __restrict__ flags, const uint8_t* __restrict__ fine, long long nseg,
+            int* __restrict__ list, int* __restrict__ count)
 {
     __shared__ int s_cnt[BAND_LIST_THREADS / 32];
     __shared__ int s_base;
-    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool set = s < nseg && flags[s] != 0;
-    const unsigned m = __ballot_sync(0xffffffffu, set);
+    // one thread per segment: its marked quarters (all four when flagged
+    // without marks), written as quarter ids 4 s + k
+    const long long sg = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned qm = 0u;
+    if (sg < nseg && flags[sg] != 0) {
+        const unsigned fw = reinterpret_cast<const unsigned*>(fine)[sg];
+        qm = fw == 0u ? 0xfu
+                      : ((fw & 0xffu) ? 1u : 0u) | ((fw & 0xff00u) ? 2u : 0u) |
+                            ((fw & 0xff0000u) ? 4u : 0u) | ((fw & 0xff000000u) ? 8u : 0u);
+    }
+    const int c = __popc(qm);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) s_cnt[wid] = __popc(m);
+    int incl = c;  // inclusive warp scan of the counts
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) s_cnt[wid] = incl;
     __syncthreads();
     if (threadIdx.x == 0) {
         int tot = 0;
         for (int w = 0; w < BAND_LIST_THREADS / 32; w++) {
-            const int c = s_cnt[w];
+            const int t = s_cnt[w];
             s_cnt[w] = tot;
-            tot += c;
+            tot += t;
         }
         s_base = tot ? atomicAdd(count, tot) : 0;
     }
     __syncthreads();
-    if (set) list[s_base + s_cnt[wid] + __popc(m & ((1u << lane) - 1u))] = (int)s;
+    int pos = s_base + s_cnt[wid] + incl - c;
+    for (int k = 0; k < 4; k++)
+        if (qm & (1u << k)) list[pos++] = (int)(4 * sg + k);
 }
 
 template <int Q, int ST, bool EXT>
@@ -330,7 +353,8 @@ __global__ void __launch_bounds__(128)
 k_band_sc(const typename StorageT<ST>::S* __restrict__ fin,
           typename StorageT<ST>::S* __restrict__ fout, typename StorageT<ST>::R* __restrict__ mom,
           typename StorageT<ST>::R* __restrict__ F, uint8_t* __restrict__ flags,
-          const int* __restrict__ list, const int* __restrict__ count, const StreamParams p)
+          uint8_t* __restrict__ fine, const int* __restrict__ list,
+          const int* __restrict__ count, const StreamParams p)
 {
     constexpr int D = Stencil<Q>::D;
     const int lane = threadIdx.x & 31;
@@ -338,47 +362,52 @@ k_band_sc(const typename StorageT<ST>::S* __restrict__ fin,
     const int n = *count;
     unsigned step = 0;
     if constexpr (ST == ST_FP16) step = sr_step(p.rng_in, nullptr, false);
-    for (int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < n; w += nw) {
-        const int s = list[w];
-        const int row = s / p.g.nseg_x;
-        const int x = (s - row * p.g.nseg_x) * 32 + lane;
-        const int y = (D == 2) ? row : row % p.g.ny;
-        const int z = (D == 2) ? 0 : row / p.g.ny;
-        if (x < p.g.nx) sc_cell<Q, ST, false, false, EXT>(fin, fout, mom, F, p, x, y, z, 1, step);
-        __syncwarp();
-        if (lane == 0) flags[s] = 0;
+    for (int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); 4 * w < n; w += nw) {
+        const int e = 4 * w + (lane >> 3);
+        if (e < n) {
+            const int qd = list[e];
+            const int sg = qd >> 2;
+            const int row = sg / p.g.nseg_x;
+            const int x = (sg - row * p.g.nseg_x) * 32 + (qd & 3) * 8 + (lane & 7);
+            const int y = (D == 2) ? row : row % p.g.ny;
+            const int z = (D == 2) ? 0 : row / p.g.ny;
+            if (x < p.g.nx) sc_cell<Q, ST, false, false, EXT>(fin, fout, mom, F, p, x, y, z, 1, step);
+            if ((lane & 7) == 0) {
+                fine[qd] = 0;
+                flags[sg] = 0;
+            }
+        }
     }
 }
 
 template <int Q, int ST>
 static void launch_band_t(const void* fin, void* fout, void* mom, void* F, uint8_t* flags,
-                          int* list, int* count, const StreamParams& p, int sm_count,
-                          cudaStream_t s)
+                          uint8_t* fine, int* list, int* count, const StreamParams& p,
+                          int sm_count, cudaStream_t s)
 {
     using T = StorageT<ST>;
     const long long nseg = (long long)p.g.ny * p.g.nz * p.g.nseg_x;
     cudaMemsetAsync(count, 0, sizeof(int), s);
     k_band_list<<<(unsigned)((nseg + BAND_LIST_THREADS - 1) / BAND_LIST_THREADS),
-                  BAND_LIST_THREADS, 0, s>>>(flags, nseg, list, count);
+                  BAND_LIST_THREADS, 0, s>>>(flags, fine, nseg, list, count);
     auto* a = (const typename T::S*)fin;
     auto* b = (typename T::S*)fout;
     auto* m = (typename T::R*)mom;
     auto* f = (typename T::R*)F;
-    // one warp per listed segment: enough warps that a few thousand
-    // segments take one or two rounds of memory latency
+    // four listed quarters per warp, 16 blocks of 4 warps per SM
     const int grid = 16 * sm_count;
     if (p.moving)
-        k_band_sc<Q, ST, true><<<grid, 128, 0, s>>>(a, b, m, f, flags, list, count, p);
+        k_band_sc<Q, ST, true><<<grid, 128, 0, s>>>(a, b, m, f, flags, fine, list, count, p);
     else
-        k_band_sc<Q, ST, false><<<grid, 128, 0, s>>>(a, b, m, f, flags, list, count, p);
+        k_band_sc<Q, ST, false><<<grid, 128, 0, s>>>(a, b, m, f, flags, fine, list, count, p);
 }
 
 void launch_band_cells(int Q, int storage, const void* fin, void* fout, void* moments, void* F,
-                       uint8_t* flags, int* list, int* count, const StreamParams& p,
-                       int sm_count, cudaStream_t s)
+                       uint8_t* flags, uint8_t* fine, int* list, int* count,
+                       const StreamParams& p, int sm_count, cudaStream_t s)
 {
 #define IBLB_BAND(QQ, SS) \
-    launch_band_t<QQ, SS>(fin, fout, moments, F, flags, list, count, p, sm_count, s)
+    launch_band_t<QQ, SS>(fin, fout, moments, F, flags, fine, list, count, p, sm_count, s)
     if (Q == 9) {
         if (storage == ST_FP64) IBLB_BAND(9, ST_FP64);
         else if (storage == ST_FP32) IBLB_BAND(9, ST_FP32);
