@@ -346,9 +346,13 @@ long long iblb_fluid_cells(iblb_handle h);
  * persistent kernel walking a (slot, tile) work list).  Slot state lives in
  * one device arena of hbm_budget_bytes allocated at creation; a request is
  * admitted when its footprint fits (first fit), else IBLB_EAGAIN.  Slots
- * must have walls, no body force, no viscosity ratio (tau_out 0 or tau), and
- * the batch's lattice and storage; the walls may move tangentially
- * (wall_u_lo / wall_u_hi, Ladd's moving-wall bounce-back as in iblb_step).
+ * must have walls, no body force, and the batch's lattice and storage; the
+ * walls may move tangentially (wall_u_lo / wall_u_hi, Ladd's moving-wall
+ * bounce-back as in iblb_step), and a slot may have a viscosity ratio
+ * (tau_out: its inside / outside classification is rebuilt every step, as
+ * in iblb_step).  While some active slot has moving walls or a viscosity
+ * ratio the stream-collide launch is the instantiation that carries those
+ * terms.
  * Each slot's tile shape (32-cell row segments per stream-collide work item) is
  * chosen at admission by timing the candidates on that slot (cached per
  * lattice width).  Calls on one batch are not thread-safe. */

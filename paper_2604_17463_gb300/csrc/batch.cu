@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "../../include/iblb.h"
+#include "classify_core.cuh"
 #include "ib_core.cuh"
 #include "lbm_core.cuh"
 #include "spread_det.cuh"
@@ -83,6 +84,14 @@ struct SlotDev {
     ForceParams fp;
     double uw_lo[3], uw_hi[3];  // tangential velocities of the lower / upper wall
     int moving;                 // either wall moves
+    // viscosity ratio: cells outside the interface relax with omega_out;
+    // per-column crossing table of the inside / outside classification
+    int two_tau;
+    int ncol;                   // columns: nx (2D), nx * ny (3D)
+    double omega_out;
+    float omega_out_f;
+    int* col_cnt;               // [ncol]
+    double* col_z;              // [ncol][COL_MAX]
 };
 
 namespace {
@@ -132,7 +141,8 @@ struct __align__(16) BItem {
     unsigned nc;           // cells of the slot's lattice
     int segs;              // segments in this item
     float omega_f;         // 1 / tau
-    int cur_base;          // bit 0: current buffer = bit 0 ^ batch parity; bit 1: moving walls
+    int cur_base;          // bit 0: current buffer = bit 0 ^ batch parity; bit 1: moving
+                           // walls; bit 2: viscosity ratio
     float scale, inv_scale;  // binary16 storage scale
     unsigned* rng;         // binary16 rounding step counter
 };
@@ -168,10 +178,11 @@ __device__ __forceinline__ void* ptr_of(int lo, int hi)
 // segments the force density is loaded right after the populations, so that
 // its latency overlaps theirs.  Populations are addressed by one 32-bit index
 // i * ncell + cell from the slot's buffer (Q * ncell < 2^32).  Arithmetic is
-// FP32 for the FP32 and binary16 forms, FP64 for FP64.  MW: the
-// instantiation that adds the moving-wall term (launched only while some
-// active slot has moving walls; the other one carries no trace of it).
-template <int Q, int ST, bool WRITE_ALL, bool MW>
+// FP32 for the FP32 and binary16 forms, FP64 for FP64.  EXT: the
+// instantiation that adds the moving-wall term and the viscosity ratio
+// (per item, as its slot asks; launched only while some active slot has
+// either, the other instantiation carries no trace of them).
+template <int Q, int ST, bool WRITE_ALL, bool EXT>
 __global__ void __launch_bounds__(BT, (BMinBlocks<Q, ST>::value))
 k_b_stream_collide(const SlotDev* __restrict__ slots, const BItem* __restrict__ items,
                    int nitems, int par)
@@ -199,7 +210,8 @@ k_b_stream_collide(const SlotDev* __restrict__ slots, const BItem* __restrict__ 
             item = load_item(items, it);
         }
         const int cur = (item.e.w & 1) ^ par;  // cur_base ^ parity
-        const bool moving = MW && (item.e.w & 2) != 0;
+        const bool moving = EXT && (item.e.w & 2) != 0;
+        const bool two_tau = EXT && (item.e.w & 4) != 0;
         const S* __restrict__ fin =
             (const S*)(cur ? ptr_of(item.a.z, item.a.w) : ptr_of(item.a.x, item.a.y));
         S* __restrict__ fout =
@@ -217,6 +229,18 @@ k_b_stream_collide(const SlotDev* __restrict__ slots, const BItem* __restrict__ 
             omega = __int_as_float(item.e.z);
         else
             omega = slots[slot].omega;
+        // viscosity ratio: cells outside the interface (an even number of
+        // crossings of their column below them) relax with omega_out
+        R omega_out = omega;
+        const int* col_cnt = nullptr;
+        const double* col_z = nullptr;
+        if constexpr (EXT) {
+            if (two_tau) {
+                omega_out = sizeof(R) == 4 ? (R)slots[slot].omega_out_f : (R)slots[slot].omega_out;
+                col_cnt = slots[slot].col_cnt;
+                col_z = slots[slot].col_z;
+            }
+        }
         unsigned step = 0;
         if constexpr (ST == ST_FP16) {  // populations stay in their stored scale
             unsigned* rng = (unsigned*)ptr_of(item.f.z, item.f.w);
@@ -247,7 +271,7 @@ k_b_stream_collide(const SlotDev* __restrict__ slots, const BItem* __restrict__ 
         // rho_w = 1, as in the single engine; only the rows next to a wall
         // read the slot's wall velocities
         double uwm[3] = {0.0, 0.0, 0.0}, uwp[3] = {0.0, 0.0, 0.0};
-        if constexpr (MW) {
+        if constexpr (EXT) {
             if (moving && (solid_m || solid_p))
                 for (int k = 0; k < 3; k++) {
                     uwm[k] = slots[slot].uw_lo[k];
@@ -283,7 +307,7 @@ k_b_stream_collide(const SlotDev* __restrict__ slots, const BItem* __restrict__ 
                     if (D == 3) off += (cy > 0 ? dym : (cy < 0 ? dyp : 0u));
                     if (solid) {
                         g[k][i] = T::load(fin, (unsigned)L::opp(i) * nc + cell, R(1));
-                        if (MW && moving) {
+                        if (EXT && moving) {
                             const double* uw = cw > 0 ? uwm : uwp;
                             const double cu = (D == 2) ? L::cx(i) * uw[0] + cy * uw[1]
                                                        : L::cx(i) * uw[0] + cy * uw[1] + cw * uw[2];
@@ -329,7 +353,15 @@ k_b_stream_collide(const SlotDev* __restrict__ slots, const BItem* __restrict__ 
                     }
                 }
                 const CellMoments<Q, R> mo = cell_moments<Q, R>(g[k], Fx, Fy, Fz, ginv);
-                cell_collide<Q, R>(g[k], mo, omega, Fx, Fy, Fz, gsc);
+                R om = omega;
+                if constexpr (EXT) {
+                    if (two_tau) {
+                        const int xc = (int)(cell - rowbase);
+                        if (!inside_cell(col_cnt, col_z, D == 2 ? xc : xc + nx * y, a))
+                            om = omega_out;
+                    }
+                }
+                cell_collide<Q, R>(g[k], mo, om, Fx, Fy, Fz, gsc);
                 store_cell_flat<Q, ST>(fout, nc, cell, g[k],
                                        ST == ST_FP16 ? sr_seed(step, (long long)cell) : 0u);
                 if (WRITE_ALL || band) put_moments<D, R>(mom, nc, cell, mo.drho, mo.ux, mo.uy, mo.uz);
@@ -459,6 +491,30 @@ static int b_sc_blocks_per_sm(int Q, int storage)
     return n;
 }
 
+// Viscosity ratio: the column crossing tables of the slots that have one,
+// cleared and rebuilt from the current interface (classify_core.cuh), one
+// thread per (slot, column), then per (slot, segment) / (slot, face).
+__global__ void k_b_col_clear(const SlotDev* __restrict__ slots, const int* __restrict__ tt)
+{
+    const SlotDev& sd = slots[tt[blockIdx.y]];
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col < sd.ncol) sd.col_cnt[col] = 0;
+}
+
+__global__ void k_b_classify(const SlotDev* __restrict__ slots, const int2* __restrict__ items,
+                             int n, int dim)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int2 it = items[t];
+    const SlotDev& sd = slots[it.x];
+    if (!sd.two_tau) return;
+    if (dim == 2)
+        classify_segment(sd.q, sd.N, it.y, sd.g, sd.col_cnt, sd.col_z, sd.err);
+    else
+        classify_face(sd.q, sd.tri, it.y, sd.g, sd.col_cnt, sd.col_z, sd.err);
+}
+
 static void launch_b_ib(int dim, int storage, int phase, const SlotDev* slots, const int2* nodes,
                         int nnodes, const int2* faces, int nfaces, cudaStream_t s)
 {
@@ -550,11 +606,11 @@ struct Arena {
 };
 
 struct Layout {
-    size_t pop[2], mom, F, flags, err, rng, q, phi, tri, csr, epos, erec, eref, total;
+    size_t pop[2], mom, F, flags, err, rng, q, phi, tri, csr, epos, erec, eref, cols, colz, total;
 };
 
 Layout slot_layout(int Q, int dim, size_t elt, size_t relt, long long ncell, long long nfluid,
-                   int rowlen, int N, int M, bool elastic)
+                   int rowlen, int N, int M, bool elastic, int ncol)
 {
     Layout L{};
     size_t o = 0;
@@ -581,6 +637,10 @@ Layout slot_layout(int Q, int dim, size_t elt, size_t relt, long long ncell, lon
         L.erec = take(sizeof(double) * ENTRY_REC * 3 * (size_t)M);
     }
     if (elastic) L.eref = take(sizeof(double) * (dim == 3 ? 5 * (size_t)M : (size_t)N));
+    if (ncol > 0) {
+        L.cols = take(sizeof(int) * (size_t)ncol);
+        L.colz = take(sizeof(double) * COL_MAX * (size_t)ncol);
+    }
     L.total = o;
     return L;
 }
@@ -617,8 +677,11 @@ struct iblb_batch_s {
     int2* d_nodes = nullptr;
     int2* d_faces = nullptr;
     size_t cap_tiles = 0, cap_nodes = 0, cap_faces = 0;
+    int* d_tt = nullptr;      // active slots with a viscosity ratio
+    size_t cap_tt = 0;
+    int ntt = 0, max_ncol = 0;
     int ntiles = 0, nnodes = 0, nfaces = 0, nactive = 0;
-    bool any_moving = false;  // an active slot has moving walls
+    bool any_ext = false;     // an active slot has moving walls or a viscosity ratio
     double* d_partial = nullptr;
     double* d_obs = nullptr;
     int par = 0;
@@ -694,7 +757,7 @@ void slot_items(const SlotDev& d, int slot, int cpt, std::vector<BItem>& out)
     it.Lw = g.dim == 2 ? g.ny : g.nz;
     it.nc = (unsigned)g.ncell;
     it.omega_f = d.omega_f;
-    it.cur_base = (d.cur_base & 1) | (d.moving ? 2 : 0);
+    it.cur_base = (d.cur_base & 1) | (d.moving ? 2 : 0) | (d.two_tau ? 4 : 0);
     it.scale = d.scale;
     it.inv_scale = d.inv_scale;
     it.rng = d.rng;
@@ -740,9 +803,24 @@ iblb_status rebuild(iblb_batch_s* b)
     b->ntiles = (int)tiles.size();
     b->nnodes = (int)nodes.size();
     b->nfaces = (int)faces.size();
-    b->any_moving = false;
-    for (auto& sl : b->slots)
-        if (sl.active && sl.dev.moving) b->any_moving = true;
+    b->any_ext = false;
+    b->ntt = 0;
+    b->max_ncol = 0;
+    std::vector<int> tt;
+    for (size_t k = 0; k < b->slots.size(); k++) {
+        const Slot& sl = b->slots[k];
+        if (!sl.active) continue;
+        if (sl.dev.moving || sl.dev.two_tau) b->any_ext = true;
+        if (sl.dev.two_tau) {
+            tt.push_back((int)k);
+            b->max_ncol = std::max(b->max_ncol, sl.dev.ncol);
+        }
+    }
+    b->ntt = (int)tt.size();
+    if (!tt.empty()) {
+        BCK(b, ensure(&b->d_tt, &b->cap_tt, tt.size()));
+        BCK(b, cudaMemcpy(b->d_tt, tt.data(), sizeof(int) * tt.size(), cudaMemcpyHostToDevice));
+    }
     // deterministic spread: bins and cell tiles of the active slots, numbered
     // globally in slot order
     b->det = false;
@@ -797,7 +875,18 @@ iblb_status rebuild(iblb_batch_s* b)
 int kernels_per_step(const iblb_batch_s* b)
 {
     if (b->nnodes == 0) return 1;
-    return (b->dim == 3 ? 2 : 1) + 2 + (b->det ? DET_KERNELS : 1);
+    return (b->dim == 3 ? 2 : 1) + 2 + (b->det ? DET_KERNELS : 1) + (b->ntt > 0 ? 2 : 0);
+}
+
+// Viscosity ratio: inside / outside of every slot that has one, from the
+// interface at the start of the step (before its stream-collide).
+void enqueue_classify(iblb_batch_s* b, cudaStream_t s)
+{
+    if (b->ntt == 0 || b->nnodes == 0) return;
+    k_b_col_clear<<<dim3((b->max_ncol + 255) / 256, b->ntt), 256, 0, s>>>(b->d_slots, b->d_tt);
+    const int2* items = b->dim == 2 ? b->d_nodes : b->d_faces;
+    const int n = b->dim == 2 ? b->nnodes : b->nfaces;
+    k_b_classify<<<(n + 127) / 128, 128, 0, s>>>(b->d_slots, items, n, b->dim);
 }
 
 // A2/A3 over all active slots: atomics, or the ordered gather.
@@ -818,9 +907,10 @@ void enqueue_step(iblb_batch_s* b, cudaStream_t s, int par, bool write_all)
         launch_b_ib(b->dim, b->storage, 0, b->d_slots, b->d_nodes, b->nnodes, b->d_faces,
                     b->nfaces, s);
         enqueue_spread(b, s);
+        enqueue_classify(b, s);
     }
     const int grid = std::max(1, std::min(b->ntiles, b->sm_count * b->sc_blocks_per_sm));
-    launch_b_sc(b->Q, b->storage, write_all, b->any_moving, b->d_slots, b->d_tiles, b->ntiles, par,
+    launch_b_sc(b->Q, b->storage, write_all, b->any_ext, b->d_slots, b->d_tiles, b->ntiles, par,
                 grid, s);
     if (b->nnodes > 0)
         launch_b_ib(b->dim, b->storage, 2, b->d_slots, b->d_nodes, b->nnodes, b->d_faces,
@@ -903,7 +993,7 @@ iblb_status tune_slot(iblb_batch_s* b, int s)
         cudaMemcpy(d_one, &d, sizeof(SlotDev), cudaMemcpyHostToDevice);
         cudaMemcpy(d_t, tl.data(), sizeof(BItem) * tl.size(), cudaMemcpyHostToDevice);
         const int grid = std::max(1, std::min((int)tl.size(), b->sm_count * b->sc_blocks_per_sm));
-        const bool mw = d.moving != 0;
+        const bool mw = d.moving != 0 || d.two_tau != 0;
         launch_b_sc(b->Q, b->storage, false, mw, d_one, d_t, (int)tl.size(), 0, grid, b->stream);
         cudaEventRecord(e0, b->stream);
         for (int t = 0; t < trials; t++)
@@ -943,8 +1033,7 @@ iblb_status check_cfg(const iblb_batch_s* b, const iblb_config& c)
     if ((double)c.lattice * c.nx * c.ny * nz >= 4294967296.0) return IBLB_EINVAL;
     if (c.body_force[0] != 0.0 || c.body_force[1] != 0.0 || c.body_force[2] != 0.0)
         return IBLB_EINVAL;  // the batched kernel has no body force
-    if (c.tau_out != 0.0 && c.tau_out != c.tau)
-        return IBLB_EINVAL;  // nor a viscosity ratio
+    if (c.tau_out != 0.0 && !(c.tau_out > 0.5)) return IBLB_EINVAL;
     if (!(c.shear_modulus >= 0.0) || !std::isfinite(c.shear_modulus) || !(c.skalak_c > -0.5) ||
         !std::isfinite(c.skalak_c))
         return IBLB_EINVAL;
@@ -971,8 +1060,10 @@ size_t iblb_batch_footprint(const iblb_config* c, int n_nodes, int n_faces)
     const long long ncell = (long long)c->nx * c->ny * nz;
     const long long nfluid = dim == 2 ? (long long)c->nx * (c->ny - 2)
                                       : (long long)c->nx * c->ny * (nz - 2);
+    const bool two_tau = c->tau_out != 0.0 && c->tau_out != c->tau;
+    const int ncol = two_tau ? (dim == 2 ? c->nx : c->nx * c->ny) : 0;
     return slot_layout(c->lattice, dim, elt, relt, ncell, nfluid, c->nx, n_nodes, n_faces,
-                       c->shear_modulus != 0.0).total;
+                       c->shear_modulus != 0.0, ncol).total;
 }
 
 iblb_status iblb_batch_create(int lattice, int storage, size_t hbm_budget_bytes, int max_slots,
@@ -1021,6 +1112,7 @@ void iblb_batch_destroy(iblb_batch b)
     cudaFree(b->d_tiles);
     cudaFree(b->d_nodes);
     cudaFree(b->d_faces);
+    cudaFree(b->d_tt);
     cudaFree(b->d_detslots);
     cudaFree(b->detb.cnt);
     cudaFree(b->detb.start);
@@ -1089,8 +1181,10 @@ iblb_status iblb_batch_admit(iblb_batch b, const iblb_config* cfg, const double*
     const long long nfluid = dim == 2 ? (long long)cfg->nx * (cfg->ny - 2)
                                       : (long long)cfg->nx * cfg->ny * (nz - 2);
     const bool elastic = cfg->shear_modulus != 0.0;
+    const bool two_tau = cfg->tau_out != 0.0 && cfg->tau_out != cfg->tau;
+    const int ncol = two_tau ? (dim == 2 ? cfg->nx : cfg->nx * cfg->ny) : 0;
     const Layout L = slot_layout(b->Q, dim, b->elt, b->relt, g.ncell, nfluid, cfg->nx, n_nodes,
-                                 dim == 3 ? n_faces : 0, elastic);
+                                 dim == 3 ? n_faces : 0, elastic, ncol);
     size_t off = 0;
     if (!b->arena.alloc(L.total, &off)) return bfail(b, IBLB_EAGAIN, "no room in the HBM budget");
     Slot& sl = b->slots[s];
@@ -1133,6 +1227,12 @@ iblb_status iblb_batch_admit(iblb_batch b, const iblb_config* cfg, const double*
     d.fp.wall_plane = 0.5;
     d.fp.Gs = cfg->shear_modulus;
     d.fp.Cs = cfg->skalak_c;
+    d.two_tau = two_tau ? 1 : 0;
+    d.ncol = ncol;
+    d.omega_out = two_tau ? 1.0 / cfg->tau_out : d.omega;
+    d.omega_out_f = (float)d.omega_out;
+    d.col_cnt = two_tau ? (int*)(base + L.cols) : nullptr;
+    d.col_z = two_tau ? (double*)(base + L.colz) : nullptr;
     d.moving = 0;
     for (int k = 0; k < 3; k++) {
         d.uw_lo[k] = k < dim ? cfg->wall_u_lo[k] : 0.0;
@@ -1255,9 +1355,12 @@ iblb_status batch_run(iblb_batch_s* b, int max_steps, int* n_completed, double* 
                     launch_b_ib(b->dim, b->storage, 0, b->d_slots, b->d_nodes, b->nnodes,
                                 b->d_faces, b->nfaces, b->stream);
                 cudaEventRecord(ev[1], b->stream);
-                if (b->nnodes > 0) enqueue_spread(b, b->stream);
+                if (b->nnodes > 0) {
+                    enqueue_spread(b, b->stream);
+                    enqueue_classify(b, b->stream);
+                }
                 cudaEventRecord(ev[2], b->stream);
-                launch_b_sc(b->Q, b->storage, last, b->any_moving, b->d_slots, b->d_tiles,
+                launch_b_sc(b->Q, b->storage, last, b->any_ext, b->d_slots, b->d_tiles,
                             b->ntiles, b->par, grid, b->stream);
                 cudaEventRecord(ev[3], b->stream);
                 if (b->nnodes > 0)

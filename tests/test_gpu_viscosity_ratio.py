@@ -146,9 +146,42 @@ def test_two_tau_launch_count():
     g.close()
 
 
-def test_batch_rejects_viscosity_ratio():
+@pytest.mark.parametrize("which", ["2d", "3d"])
+@pytest.mark.parametrize("storage,tol", [(iblb.FP64, 1e-12), (iblb.FP32_DEV, 1e-5)])
+def test_batch_viscosity_ratio_matches_single_engine(which, storage, tol):
+    # a lambda = 4 slot and a lambda = 1 slot in one batch: each equals the
+    # single engine, and the lambda = 4 slot differs from the same drop at
+    # lambda = 1
+    wl = small_2d(nx=48, ny=30) if which == "2d" else small_3d(n=24, nz=20)
+    other = small_2d(nx=40, ny=26, R=5.0) if which == "2d" else small_3d(n=20, nz=16, R=4.5)
+    steps = 150 if which == "2d" else 40
+    tau_out = 0.5 + (wl.tau - 0.5) / 4.0
+    b = iblb.Batch(wl.lattice, storage, 1 << 30, max_slots=4)
+    s = b.admit_workload(wl, n_steps=steps, tau_out=tau_out)
+    r = b.admit_workload(other, n_steps=steps)
+    b.run(steps)
+    rb, ub, qb = b.fields(s)
+    g = iblb.Simulation.from_workload(wl, storage=storage, tau_out=tau_out)
+    g.step(steps)
+    rg, ug, qg = g.fields()
+    m = fluid_mask(rg.shape, wl.dim)
+    assert rel_l2(ub[:, m], ug[:, m]) < tol
+    assert np.max(np.abs(qb - qg)) < (1e-11 if storage == iblb.FP64 else 1e-4)
+    c = iblb.Simulation.from_workload(wl, storage=storage)
+    c.step(steps)
+    assert np.max(np.abs(c.fields()[2] - qb)) > 1e-6
+    rr, ur, qr = b.fields(r)
+    g2 = iblb.Simulation.from_workload(other, storage=storage)
+    g2.step(steps)
+    m2 = fluid_mask(rr.shape, other.dim)
+    assert rel_l2(ur[:, m2], g2.fields()[1][:, m2]) < tol
+    for x in (g, c, g2):
+        x.close()
+    b.close()
+
+
+def test_batch_rejects_bad_tau_out():
     b = iblb.Batch(iblb.D2Q9, iblb.FP32_DEV, 1 << 28, max_slots=4)
-    wl = small_2d()
     with pytest.raises(iblb.IBLBError):
-        b.admit_workload(wl, tau_out=1.2)
+        b.admit_workload(small_2d(), tau_out=0.4)
     b.close()
