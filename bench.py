@@ -790,10 +790,11 @@ def run_profile_mode(args):
       ib-cap   the paper-scale cap mesh (59 292 nodes, 118 580 faces) moved
                into a 128 x 128 x 64 lattice, FP32 storage, per-node IB
                kernels (--ib-grouped 1: grouped)
-      batch3d  the first 8 D3Q19 requests of the serving mix in one FP32
-               batch; the profiled steps run inside the NVTX range "run"
-      batch2d  the 256 D2Q9 drops of the batched workload in one FP32 batch,
-               likewise inside the NVTX range "run"
+      batch3d  the first 8 D3Q19 requests of the serving mix in one batch
+               of storage --storage (default FP32); the profiled steps run
+               inside the NVTX range "run"
+      batch2d  the 256 D2Q9 drops of the batched workload in one batch of
+               storage --storage, likewise inside the NVTX range "run"
       step3d   a 3D drop on a 192 x 192 x 96 lattice (R = 30, 10 242 nodes;
                0.54 GB of FP32 populations, above L2), storage --storage,
                the overlapped step's kernels (bulk pass with the launch
@@ -837,7 +838,8 @@ def run_profile_mode(args):
         else:
             reqs = W.config5(count=2000, rate_per_s=1.0)
             wls, lat = [r.work for r in reqs if r.work.lattice == 19][:8], iblb.D3Q19
-        b = iblb.Batch(lat, iblb.FP32_DEV, 8 << 30, max_slots=len(wls) + 8)
+        storage = {"fp32": iblb.FP32_DEV, "fp16": iblb.FP16_DEV, "fp64": iblb.FP64}[args.storage]
+        b = iblb.Batch(lat, storage, 8 << 30, max_slots=len(wls) + 8)
         for w in wls:
             if b.admit_workload(w, n_steps=100000) is None:
                 raise RuntimeError("batch3d: a request did not fit")
@@ -847,7 +849,8 @@ def run_profile_mode(args):
         b.sync()
         torch.cuda.nvtx.range_pop()
         kms = kms / steps
-        out.update(slots=len(wls), fluid_cells=int(sum(w.fluid_cells for w in wls)))
+        out.update(slots=len(wls), storage=args.storage,
+                   fluid_cells=int(sum(w.fluid_cells for w in wls)))
         b.close()
     out["phase_ms"] = {iblb.KERNEL_NAMES[k]: float(kms[k]) for k in range(iblb.K_COUNT)}
     print(json.dumps(out))
