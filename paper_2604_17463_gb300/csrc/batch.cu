@@ -30,50 +30,19 @@
 
 namespace iblb {
 
-// Division of a 32-bit unsigned integer by an invariant divisor d >= 1 with
-// one multiply-high (Granlund & Montgomery, "Division by invariant integers
-// using multiplication", PLDI 1994, Fig. 4.1): with l = ceil(log2 d) and
-// m = floor(2^32 (2^l - d) / d) + 1,
-//   n / d = (t + ((n - t) >> s1)) >> s2,  t = umulhi(m, n),
-//   s1 = min(l, 1), s2 = max(l - 1, 0),
-// exact for every 32-bit n.
-struct FastDiv {
-    unsigned m;
-    int s1, s2;
-};
-
-inline FastDiv make_fastdiv(unsigned d)
-{
-    int l = 0;
-    while ((1ull << l) < (unsigned long long)d) l++;
-    FastDiv f;
-    f.m = (unsigned)((((1ull << 32) * ((1ull << l) - d)) / d) + 1ull);
-    f.s1 = l < 1 ? l : 1;
-    f.s2 = l - 1 > 0 ? l - 1 : 0;
-    return f;
-}
-
-__device__ __forceinline__ unsigned fast_div(unsigned n, unsigned m, int s1, int s2)
-{
-    const unsigned t = __umulhi(m, n);
-    return (t + ((n - t) >> s1)) >> s2;
-}
-
 struct SlotDev {
     void* f[2];
     void* mom;
     void* F;
-    uint8_t* flags;        // one byte per 32 fluid cells (fluid-cell index)
+    uint8_t* flags;        // band flags, one byte per 32-cell row segment
     int* err;
     GridParams g;
     long long nfluid;      // fluid cells
-    long long fluid_off;   // cell index of the first fluid cell
     double omega;
     float omega_f, scale, inv_scale;
     int cur_base;          // current buffer = cur_base ^ batch parity
     unsigned* rng;         // two-entry step counter for binary16 stochastic rounding
     int cpt;               // 32-cell row segments per stream-collide work item
-    FastDiv div_nx, div_ny;  // fluid-cell index -> row -> (y, z)
     double* q;
     double* phi;
     int N, M;
@@ -609,8 +578,8 @@ struct Layout {
     size_t pop[2], mom, F, flags, err, rng, q, phi, tri, csr, epos, erec, eref, cols, colz, total;
 };
 
-Layout slot_layout(int Q, int dim, size_t elt, size_t relt, long long ncell, long long nfluid,
-                   int rowlen, int N, int M, bool elastic, int ncol)
+Layout slot_layout(int Q, int dim, size_t elt, size_t relt, long long ncell, int rowlen, int N,
+                   int M, bool elastic, int ncol)
 {
     Layout L{};
     size_t o = 0;
@@ -624,7 +593,6 @@ Layout slot_layout(int Q, int dim, size_t elt, size_t relt, long long ncell, lon
     const int storage = relt == 8 ? 0 : 1;
     L.mom = take(moments_bytes(storage, dim, ncell));
     L.F = take(force_bytes(storage, dim, ncell));
-    (void)nfluid;
     L.flags = take((size_t)(ncell / rowlen) * (size_t)((rowlen + 31) / 32));
     L.err = take(sizeof(int));
     L.rng = take(2 * sizeof(unsigned));
@@ -843,8 +811,6 @@ iblb_status rebuild(iblb_batch_s* b)
             d.phi = sl.dev.phi;
             d.F = sl.dev.F;
             d.flags = sl.dev.flags;
-            d.flags_by_fluid = 0;
-            d.fluid_off = sl.dev.fluid_off;
         }
         const size_t ni = nodes.size();
         BCK(b, ensure(&b->d_detslots, &b->cap_detslots, ds.size()));
@@ -1058,11 +1024,9 @@ size_t iblb_batch_footprint(const iblb_config* c, int n_nodes, int n_faces)
     const size_t elt = c->storage == IBLB_FP64 ? 8 : (c->storage == IBLB_FP32_DEV ? 4 : 2);
     const size_t relt = c->storage == IBLB_FP64 ? 8 : 4;
     const long long ncell = (long long)c->nx * c->ny * nz;
-    const long long nfluid = dim == 2 ? (long long)c->nx * (c->ny - 2)
-                                      : (long long)c->nx * c->ny * (nz - 2);
     const bool two_tau = c->tau_out != 0.0 && c->tau_out != c->tau;
     const int ncol = two_tau ? (dim == 2 ? c->nx : c->nx * c->ny) : 0;
-    return slot_layout(c->lattice, dim, elt, relt, ncell, nfluid, c->nx, n_nodes, n_faces,
+    return slot_layout(c->lattice, dim, elt, relt, ncell, c->nx, n_nodes, n_faces,
                        c->shear_modulus != 0.0, ncol).total;
 }
 
@@ -1183,7 +1147,7 @@ iblb_status iblb_batch_admit(iblb_batch b, const iblb_config* cfg, const double*
     const bool elastic = cfg->shear_modulus != 0.0;
     const bool two_tau = cfg->tau_out != 0.0 && cfg->tau_out != cfg->tau;
     const int ncol = two_tau ? (dim == 2 ? cfg->nx : cfg->nx * cfg->ny) : 0;
-    const Layout L = slot_layout(b->Q, dim, b->elt, b->relt, g.ncell, nfluid, cfg->nx, n_nodes,
+    const Layout L = slot_layout(b->Q, dim, b->elt, b->relt, g.ncell, cfg->nx, n_nodes,
                                  dim == 3 ? n_faces : 0, elastic, ncol);
     size_t off = 0;
     if (!b->arena.alloc(L.total, &off)) return bfail(b, IBLB_EAGAIN, "no room in the HBM budget");
@@ -1206,9 +1170,6 @@ iblb_status iblb_batch_admit(iblb_batch b, const iblb_config* cfg, const double*
     d.rng = (unsigned*)(base + L.rng);
     d.g = g;
     d.nfluid = nfluid;
-    d.fluid_off = dim == 2 ? (long long)cfg->nx : (long long)cfg->nx * cfg->ny;
-    d.div_nx = make_fastdiv((unsigned)cfg->nx);
-    d.div_ny = make_fastdiv((unsigned)cfg->ny);
     d.omega = 1.0 / cfg->tau;
     d.omega_f = (float)d.omega;
     const int sexp = cfg->fp16_scale_exp ? cfg->fp16_scale_exp : 16;

@@ -495,7 +495,6 @@ iblb_status iblb_create(const iblb_config* cfg, void* cuda_stream, iblb_handle* 
         h->det_ncelltiles = ds.ct[0] * ds.ct[1] * ds.ct[2];
         ds.F = h->F;
         ds.flags = h->flags;
-        ds.flags_by_fluid = 0;
         const size_t nbn = (size_t)h->det_nbins, nct = (size_t)h->det_ncelltiles;
         if ((e = cudaMalloc(&h->detb.cnt, sizeof(int) * nbn)) != cudaSuccess ||
             (e = cudaMalloc(&h->detb.start, sizeof(int) * nbn)) != cudaSuccess ||

@@ -287,12 +287,8 @@ k_det_gather(const DetSlot* __restrict__ slots, const int2* __restrict__ items,
             reinterpret_cast<float4*>(F)[cell] = make_float4(acc[0], acc[1], D == 3 ? acc[2] : 0.f, 0.f);
         else
             for (int k = 0; k < D; k++) F[(long long)k * g.ncell + cell] = acc[k];
-        if (d.flags_by_fluid) {
-            d.flags[(cell - d.fluid_off) >> 5] = 1;
-        } else {
-            const long long row = (long long)x[2] * g.ny + x[1];
-            d.flags[row * g.nseg_x + (x[0] >> 5)] = 1;
-        }
+        const long long row = (long long)x[2] * g.ny + x[1];
+        d.flags[row * g.nseg_x + (x[0] >> 5)] = 1;
     }
 }
 

@@ -19,10 +19,7 @@ struct DetSlot {
     const double* q;       // node positions [N][dim]
     const double* phi;     // nodal forces [N][dim]
     void* F;               // force density [dim][ncell], compute precision
-    uint8_t* flags;        // band flags
-    int flags_by_fluid;    // 1: one flag per 32 fluid cells (batched engine);
-                           // 0: per 32-cell row segment (single engine)
-    long long fluid_off;   // cell index of the first fluid cell
+    uint8_t* flags;        // band flags, one byte per 32-cell row segment
 };
 
 // Device work buffers (owned by the engine that launches).
