@@ -361,15 +361,15 @@ def run_ours(args, wl):
         cv, cdt = cpu_baseline_oracle(wl, cpu_steps, openmp=True)
         c1v, c1dt = cpu_baseline_oracle(wl, 2)
         from paper_2604_17463_gb300 import workloads as W
-        c1, _ = cpu_baseline_oracle(W.config1(), 200)
-        c2d, _ = cpu_baseline_oracle(W.config2(downscale=4), 50)
+        c1, _ = cpu_baseline_oracle(W.drop_2d_128x64(), 200)
+        c2d, _ = cpu_baseline_oracle(W.spreading_2d_2048x512(downscale=4), 50)
         cpu = {"value": cv, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                "sample": f"{cpu_steps} full time steps of the same workload in the FP64 oracle "
                          f"(stream-collide rows on {cores} OpenMP threads, {cdt:.1f} s)",
                "single_thread": {"value": c1v, "unit": "MLUPS", "cores": 1,
                                  "sample": f"2 full time steps, one thread, {c1dt:.1f} s"},
-               "other_workloads_mlups": {"c1_d2q9_128x64 (200 steps, 1 thread)": c1,
-                                         "c2_d2q9_512x128 downscaled (50 steps, 1 thread)": c2d}}
+               "other_workloads_mlups": {"d2q9_128x64 drop (200 steps, 1 thread)": c1,
+                                         "d2q9_512x128 spreading, 2048x512 downscaled 4x (50 steps, 1 thread)": c2d}}
     clocks = clk.summary()
     line = {
         "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
@@ -421,7 +421,7 @@ def batch_object(args):
     import torch
     from paper_2604_17463_gb300 import iblb, serve
     from paper_2604_17463_gb300 import workloads as W
-    wls = W.config4()
+    wls = W.batch_2d_drops()
     stream = torch.cuda.current_stream().cuda_stream
     peak, kind = hbm_peak()
     budget = 24 << 30
@@ -481,7 +481,7 @@ def run_batch_mode(args):
     from paper_2604_17463_gb300 import iblb, serve
     from paper_2604_17463_gb300 import workloads as W
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    wls = W.config4(count=args.count, steps_lo=5000 // args.step_div, steps_hi=50000 // args.step_div)
+    wls = W.batch_2d_drops(count=args.count, steps_lo=5000 // args.step_div, steps_hi=50000 // args.step_div)
     stream = torch.cuda.current_stream().cuda_stream
     n0 = iblb.iblb_kernel_launch_count()
     seq = serve.run_sequential(wls, iblb.FP32_DEV, stream=stream)
@@ -543,7 +543,7 @@ def run_serve_mode(args):
     from paper_2604_17463_gb300 import iblb, serve
     from paper_2604_17463_gb300 import workloads as W
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    reqs = W.config5(count=args.count, rate_per_s=args.rate, steps_lo=5000 // args.step_div,
+    reqs = W.serve_requests(count=args.count, rate_per_s=args.rate, steps_lo=5000 // args.step_div,
                      steps_hi=50000 // args.step_div)
     storage = {"fp32": iblb.FP32_DEV, "fp16": iblb.FP16_DEV, "fp64": iblb.FP64}[args.serve_storage]
     # seeded sample of the 2D requests for the oracle check (among those the
@@ -604,7 +604,7 @@ def _oracle_spread_trajectory(job):
     theta, tau, steps, checkpoints = job
     import oracle
     from paper_2604_17463_gb300 import workloads as W
-    wl = W.config2(theta_eq_deg=theta, tau=tau, downscale=4)
+    wl = W.spreading_2d_2048x512(theta_eq_deg=theta, tau=tau, downscale=4)
     o = oracle.Sim(9, wl.nx, wl.ny, tau=wl.tau, sigma=wl.sigma, xi=wl.xi,
                    theta_eq_deg=wl.theta_eq_deg, pi_n=wl.pi_n, pi_m=wl.pi_m)
     o.set_interface(wl.nodes)
@@ -669,7 +669,7 @@ def run_spread2d_mode(args):
     full, ds = [], []
     dev_s = {n: 0.0 for n in names.values()}
     for theta, tau in combos:
-        wl = W.config2(theta_eq_deg=theta, tau=tau)
+        wl = W.spreading_2d_2048x512(theta_eq_deg=theta, tau=tau)
         runs = {}
         for st in (iblb.FP64, iblb.FP32_DEV, iblb.FP16_DEV):
             runs[st], sec = traj(wl, st, steps_full)
@@ -685,7 +685,7 @@ def run_spread2d_mode(args):
                      "final": {n: {k: runs[st][-1][k] for k in ("theta_deg", "r_cl", "film")}
                                for st, n in names.items()},
                      "theta_t_fp16": [round(o["theta_deg"], 3) for o in runs[iblb.FP16_DEV]]})
-        wd = W.config2(theta_eq_deg=theta, tau=tau, downscale=4)
+        wd = W.spreading_2d_2048x512(theta_eq_deg=theta, tau=tau, downscale=4)
         ds.append({"theta_eq": theta, "tau": tau, "wl": wd,
                    "gpu": {st: traj(wd, st, steps_ds)[0] for st in (iblb.FP32_DEV, iblb.FP16_DEV)}})
     launches = iblb.iblb_kernel_launch_count() - n0
@@ -834,9 +834,9 @@ def run_profile_mode(args):
         sim.close()
     else:
         if args.case == "batch2d":
-            wls, lat = W.config4(), iblb.D2Q9
+            wls, lat = W.batch_2d_drops(), iblb.D2Q9
         else:
-            reqs = W.config5(count=2000, rate_per_s=1.0)
+            reqs = W.serve_requests(count=2000, rate_per_s=1.0)
             wls, lat = [r.work for r in reqs if r.work.lattice == 19][:8], iblb.D3Q19
         storage = {"fp32": iblb.FP32_DEV, "fp16": iblb.FP16_DEV, "fp64": iblb.FP64}[args.storage]
         b = iblb.Batch(lat, storage, 8 << 30, max_slots=len(wls) + 8)
@@ -1023,7 +1023,7 @@ def main():
     if args.mode == "profile":
         return run_profile_mode(args)
     from paper_2604_17463_gb300 import workloads as W
-    wl = W.config3()
+    wl = W.drop_3d_256x256x128()
     if args.impl == "reference":
         return run_reference(args, wl)
     return run_ours(args, wl)

@@ -152,16 +152,16 @@ class Workload:
         return self.nx * self.ny * (self.nz - 2)
 
 
-def config1() -> Workload:
+def drop_2d_128x64() -> Workload:
     """2D D2Q9 128x64, tau = 1, circle R = 20 with 200 nodes centred 22 lu
     above the wall, sigma = 1e-3, theta_eq = 60 deg, xi = 0.05 R, 2000 steps."""
     R = 20.0
     nodes = circle(200, R, (64.0, WALL_PLANE + 22.0))
-    return Workload("c1_d2q9_128x64_fp64", 9, 128, 64, 1, 1.0, 1e-3, 0.05 * R, 60.0, 9, 3,
+    return Workload("d2q9_128x64_fp64", 9, 128, 64, 1, 1.0, 1e-3, 0.05 * R, 60.0, 9, 3,
                     2000, nodes, None)
 
 
-def config2(theta_eq_deg: float = 60.0, tau: float = 1.0, downscale: int = 1) -> Workload:
+def spreading_2d_2048x512(theta_eq_deg: float = 60.0, tau: float = 1.0, downscale: int = 1) -> Workload:
     """2D D2Q9 2048x512 spreading, R = 200 with 2000 nodes, initial angle
     150 deg; optional downscaled copy (lattice, R, nodes / downscale)."""
     R = 200.0 / downscale
@@ -169,16 +169,16 @@ def config2(theta_eq_deg: float = 60.0, tau: float = 1.0, downscale: int = 1) ->
     n = 2000 // downscale
     nx, ny = 2048 // downscale, 512 // downscale
     nodes = truncated_circle(n, R, 150.0, WALL_PLANE + xi, nx / 2.0)
-    return Workload(f"c2_d2q9_{nx}x{ny}", 9, nx, ny, 1, tau, 1e-3, xi, theta_eq_deg, 9, 3,
+    return Workload(f"d2q9_spread_{nx}x{ny}", 9, nx, ny, 1, tau, 1e-3, xi, theta_eq_deg, 9, 3,
                     200000, nodes, None)
 
 
-def config3() -> Workload:
+def drop_3d_256x256x128() -> Workload:
     """3D D3Q19 256x256x128, icosphere R = 40 (20480 faces, 10242 nodes)
     centred 42 lu above the wall, theta_eq = 75 deg, tau = 0.8."""
     R = 40.0
     nodes, faces = icosphere(5, R, (128.0, 128.0, WALL_PLANE + 42.0))
-    return Workload("c3_d3q19_256x256x128", 19, 256, 256, 128, 0.8, 1e-3, 0.05 * R, 75.0, 9, 3,
+    return Workload("d3q19_256x256x128", 19, 256, 256, 128, 0.8, 1e-3, 0.05 * R, 75.0, 9, 3,
                     50000, nodes, faces)
 
 
@@ -209,7 +209,7 @@ def droplet_3d(nx: int, ny: int, nz: int, theta_eq_deg: float, tau: float, steps
                     steps, nodes, faces)
 
 
-def config4(count: int = 256, seed: int = BASE_SEED + 4, steps_lo: int = 5000,
+def batch_2d_drops(count: int = 256, seed: int = BASE_SEED + 4, steps_lo: int = 5000,
             steps_hi: int = 50000) -> List[Workload]:
     """256 uneven 2D droplets: width log-uniform in [64, 1024], theta_eq
     uniform in [30, 150], tau uniform in [0.55, 1.5]."""
@@ -220,7 +220,7 @@ def config4(count: int = 256, seed: int = BASE_SEED + 4, steps_lo: int = 5000,
         th = float(rng.uniform(30.0, 150.0))
         tau = float(rng.uniform(0.55, 1.5))
         st = int(rng.integers(steps_lo, steps_hi + 1))
-        out.append(droplet_2d(w, th, tau, st, name=f"c4_{k:03d}"))
+        out.append(droplet_2d(w, th, tau, st, name=f"drop{k:03d}"))
     return out
 
 
@@ -230,7 +230,7 @@ class Request:
     work: Workload
 
 
-def config5(count: int = 2000, rate_per_s: float = 50.0, seed: int = BASE_SEED + 5,
+def serve_requests(count: int = 2000, rate_per_s: float = 50.0, seed: int = BASE_SEED + 5,
             steps_lo: int = 5000, steps_hi: int = 50000, frac_3d: float = 0.2) -> List[Request]:
     """Poisson stream of wetting requests: 80% 2D (sizes as in the batched
     workload), 20% 3D D3Q19 between 64^3 and 192x192x96."""
@@ -246,10 +246,10 @@ def config5(count: int = 2000, rate_per_s: float = 50.0, seed: int = BASE_SEED +
             s = float(rng.uniform(0.0, 1.0))
             nx = int(round(64 + s * (192 - 64)))
             nz = int(round(64 + s * (96 - 64)))
-            out.append(Request(t, droplet_3d(nx, nx, nz, th, tau, st, name=f"c5_{k:04d}")))
+            out.append(Request(t, droplet_3d(nx, nx, nz, th, tau, st, name=f"req{k:04d}")))
         else:
             w = int(round(math.exp(rng.uniform(math.log(64), math.log(1024)))))
-            out.append(Request(t, droplet_2d(w, th, tau, st, name=f"c5_{k:04d}")))
+            out.append(Request(t, droplet_2d(w, th, tau, st, name=f"req{k:04d}")))
     return out
 
 

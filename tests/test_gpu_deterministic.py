@@ -78,10 +78,10 @@ def test_bitwise_repeatable_and_matches_oracle(which, steps):
     assert np.max(np.abs(q0 - qo)) < 1e-11
 
 
-def test_config1_deterministic_2000_steps():
+def test_drop_2d_128x64_deterministic_2000_steps():
     # the 128x64 drop of the first workload, 2000 steps, twice: bitwise equal,
     # and within the FP64 tolerances of the oracle
-    wl = W.config1()
+    wl = W.drop_2d_128x64()
     out = []
     for _ in range(2):
         g = iblb.Simulation.from_workload(wl, deterministic_spread=True)

@@ -33,7 +33,7 @@ def compare(wl, storage, steps, tol_u, tol_drho, tol_q):
 
 
 def test_3d_benchmark_workload_fp32():
-    compare(W.config3(), iblb.FP32_DEV, 3, 1e-5, 1e-5, 1e-9)
+    compare(W.drop_3d_256x256x128(), iblb.FP32_DEV, 3, 1e-5, 1e-5, 1e-9)
 
 
 # binary16 keeps about three significant digits of each population deviation
@@ -41,4 +41,4 @@ def test_3d_benchmark_workload_fp32():
 @pytest.mark.parametrize("storage,tol,tol_q", [(iblb.FP32_DEV, 1e-5, 1e-8),
                                                (iblb.FP16_DEV, 2e-3, 1e-5)])
 def test_2d_spreading_workload(storage, tol, tol_q):
-    compare(W.config2(theta_eq_deg=30.0, tau=0.6), storage, 20, tol, tol, tol_q)
+    compare(W.spreading_2d_2048x512(theta_eq_deg=30.0, tau=0.6), storage, 20, tol, tol, tol_q)

@@ -114,8 +114,8 @@ def test_full_step_fp64(which, steps):
     g.close()
 
 
-def test_config1_fp64_2000_steps():
-    wl = W.config1()
+def test_drop_2d_128x64_fp64_2000_steps():
+    wl = W.drop_2d_128x64()
     o = oracle_from_workload(wl)
     g = iblb.Simulation.from_workload(wl)
     assert o.step(wl.steps) == 0
@@ -127,7 +127,7 @@ def test_config1_fp64_2000_steps():
     e_drho = rel_l2(rg[m] - 1.0, ro[m] - 1.0)
     e_u = rel_l2(ug[:, m], uo[:2, m])
     e_q = rel_l2(qg, qo)
-    print(f"config1 fp64: rel-L2 rho {e_rho:.2e} rho-1 {e_drho:.2e} u {e_u:.2e} q {e_q:.2e}")
+    print(f"d2q9 128x64 drop fp64: rel-L2 rho {e_rho:.2e} rho-1 {e_drho:.2e} u {e_u:.2e} q {e_q:.2e}")
     assert e_rho < 1e-10 and e_u < 1e-10
     # rho - 1 ~ 3e-5 here: the oracle stores raw f ~ 0.1-0.4 in FP64, whose
     # rounding (~1e-16 absolute per operation) bounds the agreement on the
@@ -144,8 +144,8 @@ def test_config1_fp64_2000_steps():
     g.close()
 
 
-def test_config1_fp32_2000_steps():
-    wl = W.config1()
+def test_drop_2d_128x64_fp32_2000_steps():
+    wl = W.drop_2d_128x64()
     o = oracle_from_workload(wl)
     g = iblb.Simulation.from_workload(wl, storage=iblb.FP32_DEV)
     assert o.step(wl.steps) == 0
@@ -156,7 +156,7 @@ def test_config1_fp32_2000_steps():
     e_rho = rel_l2(rg[m], ro[m])
     e_drho = rel_l2(rg[m] - 1.0, ro[m] - 1.0)
     e_u = rel_l2(ug[:, m], uo[:2, m])
-    print(f"config1 fp32: rel-L2 rho {e_rho:.2e} rho-1 {e_drho:.2e} u {e_u:.2e}")
+    print(f"d2q9 128x64 drop fp32: rel-L2 rho {e_rho:.2e} rho-1 {e_drho:.2e} u {e_u:.2e}")
     assert e_rho < 1e-5 and e_u < 1e-5
     assert e_drho < 1e-5
     g.close()

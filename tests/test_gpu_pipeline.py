@@ -97,7 +97,7 @@ def test_pipeline_full_step_3d_drop(storage, tol, variant):
 
 
 def test_pipeline_used_by_default_on_benchmark_shape():
-    wl = W.config3()
+    wl = W.drop_3d_256x256x128()
     g = iblb.Simulation.from_workload(wl, storage=iblb.FP32_DEV)
     assert g.variant == 1
     g.step(3)

@@ -34,12 +34,12 @@ def trajectory(wl, storage):
 
 @pytest.fixture(scope="module")
 def runs():
-    wl = W.config2(theta_eq_deg=60.0, tau=1.0, downscale=4)
+    wl = W.spreading_2d_2048x512(theta_eq_deg=60.0, tau=1.0, downscale=4)
     return {s: trajectory(wl, s) for s in (iblb.FP64, iblb.FP32_DEV, iblb.FP16_DEV)}
 
 
 def test_fp64_matches_oracle_on_downscaled_spreading():
-    wl = W.config2(theta_eq_deg=60.0, tau=1.0, downscale=4)
+    wl = W.spreading_2d_2048x512(theta_eq_deg=60.0, tau=1.0, downscale=4)
     o = oracle_from_workload(wl)
     g = iblb.Simulation.from_workload(wl)
     assert o.step(300) == 0
@@ -72,13 +72,13 @@ def test_reduced_precision_contact_angle(runs, storage):
 
 
 def wl_xi():
-    return W.config2(downscale=4).xi
+    return W.spreading_2d_2048x512(downscale=4).xi
 
 
 def test_full_size_spreading_fp16_vs_fp64():
     # the full 2048 x 512 spreading drop, the most-spreading corner of the
     # sweep (theta_eq = 30 deg, tau = 0.6), all 200k steps
-    wl = W.config2(theta_eq_deg=30.0, tau=0.6)
+    wl = W.spreading_2d_2048x512(theta_eq_deg=30.0, tau=0.6)
     runs = {}
     for st in (iblb.FP64, iblb.FP16_DEV):
         g = iblb.Simulation.from_workload(wl, storage=st)

@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 
 
 def test_serving_completes_and_matches_alone():
-    reqs = W.config5(count=24, rate_per_s=60.0, steps_lo=200, steps_hi=800, frac_3d=0.2)
+    reqs = W.serve_requests(count=24, rate_per_s=60.0, steps_lo=200, steps_hi=800, frac_3d=0.2)
     out = serve.serve(reqs, iblb.FP32_DEV, budget_2d=2 << 30, budget_3d=8 << 30, chunk=200)
     assert out["completed"] == len(reqs)
     assert out["p99_s"] >= out["p50_s"] > 0

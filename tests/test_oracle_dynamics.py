@@ -251,8 +251,8 @@ def test_contact_angle_follows_theta_eq():
     assert all(0.0 < m - t < 12.0 for m, t in zip(th, (60.0, 90.0, 120.0))), th
 
 
-def test_config1_volume_drift_and_wall():
-    wl = W.config1()
+def test_drop_2d_128x64_volume_drift_and_wall():
+    wl = W.drop_2d_128x64()
     s = oracle.Sim(9, wl.nx, wl.ny, tau=wl.tau, walls=True, wetting=True, sigma=wl.sigma,
                    xi=wl.xi, theta_eq_deg=wl.theta_eq_deg, pi_n=wl.pi_n, pi_m=wl.pi_m)
     s.set_interface(wl.nodes)

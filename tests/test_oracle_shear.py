@@ -71,7 +71,7 @@ def test_walls_moving_together_give_plug_flow():
 
 
 def test_moving_walls_conserve_mass_with_a_drop():
-    wl = W.config1()
+    wl = W.drop_2d_128x64()
     s = oracle.Sim(9, wl.nx, wl.ny, tau=1.0, sigma=wl.sigma, xi=wl.xi, wetting=False,
                    wall_u_lo=(-0.002, 0.0), wall_u_hi=(0.002, 0.0))
     s.set_interface(wl.nodes)

@@ -109,7 +109,7 @@ def test_relaxation_times_by_region(tau_in, tau_out):
 
 
 def test_equal_relaxation_times_reduce_to_single_tau():
-    wl = W.config1()
+    wl = W.drop_2d_128x64()
     a = oracle.Sim(9, wl.nx, wl.ny, tau=1.0, sigma=wl.sigma, xi=wl.xi, theta_eq_deg=60.0)
     b = oracle.Sim(9, wl.nx, wl.ny, tau=1.0, sigma=wl.sigma, xi=wl.xi, theta_eq_deg=60.0,
                    tau_out=1.0)
